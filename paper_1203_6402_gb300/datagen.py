@@ -1,0 +1,71 @@
+"""Seeded synthetic inputs shaped like the workloads of "Scalable K-Means++".
+
+This module holds no part of the method's arithmetic: it only draws points.  It
+is the one module that both the CUDA path's tests/benchmark and the CPU oracle's
+tests read, so that both sides see the same bytes.
+
+* ``gauss_mixture`` -- GAUSSMIXTURE (Sec. 4.1): k centers from a spherical
+  Gaussian with mean 0 and variance R per coordinate, then points from unit
+  variance Gaussians around centers chosen uniformly (equal weights).
+* ``kdd_like`` -- a stand-in with the shape of the 4.8M x 42 KDDCUP1999 data
+  (Sec. 4.1; the real data set is not available here): 34 heavy-tailed
+  non-negative columns (log-normal, mu = 0, sigma = 2), 8 integer-valued columns
+  in [0, 255], and a fraction of rows that are exact copies of other rows.
+
+All draws use numpy's PCG64 with an explicit seed; outputs are FP32, row-major.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def gauss_mixture(n: int, d: int, k_true: int, R: float, seed: int, return_centers: bool = False):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    centers = rng.normal(0.0, np.sqrt(R), size=(k_true, d))
+    comp = rng.integers(0, k_true, size=n)
+    X = centers[comp] + rng.normal(0.0, 1.0, size=(n, d))
+    X = X.astype(np.float32)
+    if return_centers:
+        return X, centers, comp
+    return X
+
+
+def kdd_like(n: int, seed: int, d_lognormal: int = 34, d_int: int = 8, dup_frac: float = 0.2,
+             sigma: float = 2.0) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d = d_lognormal + d_int
+    X = np.empty((n, d), dtype=np.float32)
+    X[:, :d_lognormal] = rng.lognormal(0.0, sigma, size=(n, d_lognormal)).astype(np.float32)
+    X[:, d_lognormal:] = rng.integers(0, 256, size=(n, d_int)).astype(np.float32)
+    ndup = int(round(dup_frac * n))
+    if ndup > 0 and n > 1:
+        dst = rng.choice(n, size=ndup, replace=False)
+        src = rng.integers(0, n, size=ndup)
+        X[dst] = X[src]
+    return X
+
+
+def uniform_box(n: int, d: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """Plain uniform points (edge-case tests)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(lo, hi, size=(n, d)).astype(np.float32)
+
+
+# The five workloads, by name.  Sizes follow the benchmark table of the design.
+WORKLOADS = {
+    "gmm_n10k_d15_k50": dict(kind="gmm", n=10_000, d=15, k=50, k_true=50, R=10.0, ell=100.0, rounds=5,
+                             max_iter=100),
+    "kdd_n1M_d42_k500": dict(kind="kdd", n=1_000_000, d=42, k=500, ell=1000.0, rounds=5, max_iter=100),
+    "kdd_n4.8M_d42_k1000": dict(kind="kdd", n=4_800_000, d=42, k=1000, ell=2000.0, rounds=5, max_iter=100),
+    "gmm_n10M_d128_k10000": dict(kind="gmm", n=10_000_000, d=128, k=10_000, k_true=10_000, R=100.0,
+                                 ell=20_000.0, rounds=5, max_iter=10),
+}
+
+
+def make(name: str, seed: int, n: int | None = None) -> np.ndarray:
+    """Points for a named workload (optionally a smaller n with the same recipe)."""
+    w = WORKLOADS[name]
+    nn = w["n"] if n is None else n
+    if w["kind"] == "gmm":
+        return gauss_mixture(nn, w["d"], w["k_true"], w["R"], seed)
+    return kdd_like(nn, seed)

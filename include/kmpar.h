@@ -1,0 +1,208 @@
+/*
+ * kmpar.h -- C ABI of the GB300 (sm_103a) k-means|| library.
+ *
+ * Method: Bahmani, Moseley, Vattani, Kumar, Vassilvitskii, "Scalable K-Means++"
+ * (arXiv:1203.6402).  The library runs the data-parallel path of Algorithm 2
+ * (Sec. 3.3) on one GPU:
+ *
+ *   kmpar_init       Alg. 2 steps 1-2  first center uniform over X; psi = phi_X(C)
+ *   kmpar_round      Alg. 2 steps 4-5  draw each x with p = min(1, l D^2(x)/phi),
+ *                                       C <- C u C', update D^2 and phi
+ *   kmpar_weight     Alg. 2 step 7     w_c = #points nearest to candidate c
+ *   kmpar_recluster  Alg. 2 step 8     weighted k-means++ (Alg. 1, Sec. 4.2) to k
+ *   kmpar_lloyd      Sec. 1, Sec. 3.1  Lloyd's iteration to a stable assignment
+ *   kmpar_cost       Sec. 3.1          phi_X(C) = sum_x min_i ||x - c_i||^2
+ *
+ * Conventions (all entry points):
+ *   - X is row-major FP32, n rows of d coordinates (row stride d floats), in
+ *     DEVICE memory unless a function says otherwise.  It is borrowed: the
+ *     caller keeps it alive and unchanged for the life of the context.
+ *   - Every call is asynchronous on the context's stream unless it writes to a
+ *     host pointer the caller passed (those calls synchronise that stream).
+ *   - Errors are returned as kmpar_status; no exception crosses the ABI and no
+ *     device trap is used.  kmpar_last_error() gives a one-line reason.
+ *   - Nothing is thread-safe per context; distinct contexts are independent.
+ *   - Limits: 1 <= d <= 4096, 1 <= n < 2^31, 1 <= k, l > 0, 0 <= rounds,
+ *     per-round sample capacity l + 10 sqrt(l) + 64 <= 32768.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = seed and
+ * counter = (i_lo, i_hi, round, tag); tag 1 = first center, 2 = round draws,
+ * 3 = reclustering draws; a uniform double is (a 2^26 + b) / 2^53 with
+ * a = word0 >> 5, b = word1 >> 6.  Results are a pure function of
+ * (X, k, l, rounds, seed, precision).
+ *
+ * Ties: an argmin goes to the lowest center number; candidates are numbered in
+ * insertion order (initial center 0, then each round's draws in ascending point
+ * order).  Decisions whose FP32 values are within the FP32 error bound of one
+ * another are re-decided in FP64 with the same formula as the definition
+ * (difference form, ascending coordinates, no fused multiply-add).
+ */
+#ifndef KMPAR_H
+#define KMPAR_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define KMPAR_API __attribute__((visibility("default")))
+#else
+#define KMPAR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kmpar_ctx kmpar_ctx;
+
+typedef enum {
+    KMPAR_OK = 0,
+    KMPAR_ERR_ARG = 1,              /* an argument is out of range or NULL          */
+    KMPAR_ERR_CUDA = 2,             /* a CUDA runtime call or a launch failed       */
+    KMPAR_ERR_OOM = 3,              /* device allocation failed                     */
+    KMPAR_ERR_CAPACITY = 4,         /* a round drew more points than its capacity   */
+    KMPAR_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up           */
+    KMPAR_ERR_STATE = 6,            /* call out of order (see each function)        */
+    KMPAR_WARN_FEW_CANDIDATES = 7,  /* recluster ran out of positive mass before k  */
+    KMPAR_ERR_UNSUPPORTED = 8       /* precision or size not built into this library*/
+} kmpar_status;
+
+/* Arithmetic of the distance step.  Every mode stores exact FP32 difference-form
+ * distances and takes the same argmin decisions; the modes differ only in how
+ * candidates are screened. */
+typedef enum {
+    KMPAR_FP32 = 0,     /* CUDA-core FP32 difference form for every pair          */
+    KMPAR_BF16 = 1,     /* tcgen05 BF16 GEMM-form screening + exact FP32 refine    */
+    KMPAR_BF16X3 = 2    /* tcgen05 split-BF16 (hi/lo, 3 products) screening+refine */
+} kmpar_precision;
+
+/* Counters gathered on the device (kmpar_get_stats synchronises). */
+typedef struct {
+    int64_t n, m;                 /* points; candidates so far                      */
+    int32_t d, k, rounds_done, lloyd_iters;
+    int64_t round_added[64];      /* |C'_i| for i = 1..rounds (index i-1)            */
+    double  phi[65];              /* psi, then phi after each round                  */
+    int64_t sample_near;          /* draws with |u - p| <= 1e-6                      */
+    int64_t sample_refined;       /* draws re-decided with an FP64 D^2                */
+    int64_t argmin_fp64;          /* argmin decisions re-decided in FP64              */
+    int64_t argmin_wide;          /* screening windows that held more than 2 centers  */
+    int64_t recluster_near;       /* reclustering targets within 1e-6 of a boundary   */
+    int32_t capacity_overflow;    /* 1 if some round exceeded its capacity            */
+    int32_t recluster_warn;       /* 1 if positive mass ran out before k draws        */
+    /* with kmpar_set_timing(ctx, 1): CUDA-event time of the distance passes,
+     * [0] = round passes (Alg. 2 step 5), [1] = Lloyd assignment passes */
+    double  kernel_ms[2];
+    int64_t kernel_launches[2];
+} kmpar_stats;
+
+/*
+ * Alg. 2 steps 1-2.  Creates a context over X (device, n x d FP32, borrowed),
+ * allocates its device buffers, draws the first center i0 = floor(u n) with u
+ * from counter (0, 0, 0, 1), and computes D^2(x) = ||x - x_i0||^2 (exact FP32
+ * difference form), idx(x) = 0 and psi = sum D^2 (FP64).  k is the number of
+ * centers the reclustering produces; ell is the oversampling factor l; rounds is
+ * the number of calls to kmpar_round that will follow; stream is a cudaStream_t
+ * (NULL = legacy default stream).  On error *out is NULL.
+ */
+KMPAR_API kmpar_status kmpar_init(kmpar_ctx **out, const float *X, int64_t n, int32_t d, int32_t k,
+                        double ell, int32_t rounds, uint64_t seed, int32_t precision,
+                        void *stream);
+
+/*
+ * Alg. 2 steps 4-5, round i (1-based; rounds must be called in order 1..rounds).
+ * Draws each x independently with p = min(1, l D^2(x)/phi) (p = 0 if phi = 0),
+ * u from counter (x, 0, i, 2); appends the drawn points in ascending order to the
+ * candidate set; updates D^2, idx and phi against the new candidates.  n_added
+ * and phi (host, nullable) receive |C'_i| and the new phi; passing either
+ * synchronises the stream.  KMPAR_ERR_CAPACITY if the round drew more than its
+ * capacity (the context is then unusable).
+ */
+KMPAR_API kmpar_status kmpar_round(kmpar_ctx *ctx, int32_t i, int64_t *n_added, double *phi);
+
+/*
+ * Alg. 2 step 7.  Computes w_c = #{x : idx(x) = c} for every candidate c.
+ * *m_out (host) receives the number of candidates m; *cand_idx_dev receives a
+ * device pointer to m int32 row numbers of X (insertion order) and *w_dev a
+ * device pointer to m int64 weights; both are owned by the context and stay valid
+ * until kmpar_destroy.  Any out pointer may be NULL.  Synchronises.
+ */
+KMPAR_API kmpar_status kmpar_weight(kmpar_ctx *ctx, int64_t *m_out, const int32_t **cand_idx_dev,
+                          const int64_t **w_dev);
+
+/*
+ * Alg. 2 step 8.  Weighted k-means++ over the m candidates: draw t = 0 picks c
+ * with probability w_c / sum w; draw t > 0 picks c with probability
+ * w_c D^2(c) / sum w D^2, D^2 to the centers drawn so far; a draw uses u from
+ * counter (t, 0, 0, 3), target = u * total, and the smallest c whose FP64 prefix
+ * sum exceeds the target.  Writes the k chosen rows to centers_dev (device, k x d
+ * FP32, caller-owned).  Requires kmpar_weight.  Returns KMPAR_WARN_FEW_CANDIDATES
+ * (centers still written, remaining draws repeat the first center) if the mass
+ * ran out before k draws.  Synchronises.
+ */
+KMPAR_API kmpar_status kmpar_recluster(kmpar_ctx *ctx, float *centers_dev);
+
+/*
+ * Lloyd's iteration (Sec. 1, Sec. 3.1) on X from the k centers in centers_dev
+ * (device, k x d FP32, updated in place).  Each iteration assigns every point to
+ * its nearest center (lowest index on ties) and stops if no label changed;
+ * otherwise each center becomes the centroid of its cluster (FP64 sums in
+ * ascending point order, rounded to FP32; an empty cluster keeps its center).
+ * At most max_iter center updates.  labels_dev (device, n int32, nullable)
+ * receives the final assignment; *iters (host, nullable) the number of updates;
+ * *final_cost (host, nullable) the cost of the final centers; cost_hist (host,
+ * nullable, max_iter+1 doubles) the cost of each assignment.  Synchronises once
+ * per iteration.
+ */
+KMPAR_API kmpar_status kmpar_lloyd(kmpar_ctx *ctx, float *centers_dev, int32_t max_iter,
+                         int32_t *labels_dev, int32_t *iters, double *final_cost,
+                         double *cost_hist);
+
+/*
+ * Sec. 3.1: phi_X(C) = sum_x min_i ||x - c_i||^2 for X (device, n x d FP32) and
+ * C (device, k x d FP32), summed in FP64 over exact FP32 distances.  *phi (host)
+ * receives the cost.  Allocates a small scratch buffer on the stream.
+ * Synchronises.
+ */
+KMPAR_API kmpar_status kmpar_cost(const float *X, int64_t n, int32_t d, const float *C, int32_t k,
+                        int32_t precision, double *phi, void *stream);
+
+/*
+ * The whole path in one call: init, rounds 1..r, weight, recluster, Lloyd.
+ * flags & KMPAR_HOST_BUFFERS: X, centers_out and labels_out are HOST pointers
+ * (copied in and out inside the call); otherwise device pointers.  seed_cost,
+ * final_cost and iters are host pointers (nullable).  labels_out is nullable.
+ */
+#define KMPAR_HOST_BUFFERS 1
+KMPAR_API kmpar_status kmpar_fit(const float *X, int64_t n, int32_t d, int32_t k, double ell, int32_t rounds,
+                       uint64_t seed, int32_t precision, int32_t max_iter, float *centers_out,
+                       int32_t *labels_out, double *seed_cost, double *final_cost, int32_t *iters,
+                       int32_t flags, void *stream);
+
+/* Device pointers to the context's D^2 (n FP32) and idx (n int32) arrays, valid
+ * until the next call on the context; either out pointer may be NULL. */
+KMPAR_API kmpar_status kmpar_state(const kmpar_ctx *ctx, const float **D2_dev, const int32_t **idx_dev);
+
+/* Device-side counters (see kmpar_stats).  Synchronises. */
+KMPAR_API kmpar_status kmpar_get_stats(kmpar_ctx *ctx, kmpar_stats *out);
+
+/* Writes u(i) for counters (i, 0, round, tag), i = 0..count-1, under key seed,
+ * to out_dev (device, count doubles): the generator every draw above uses. */
+KMPAR_API kmpar_status kmpar_uniforms(int64_t count, uint32_t round, uint32_t tag, uint64_t seed,
+                            double *out_dev, void *stream);
+
+/* Enables (1) or disables (0) CUDA-event timing of the context's distance passes
+ * (reported by kmpar_get_stats); off by default. */
+KMPAR_API kmpar_status kmpar_set_timing(kmpar_ctx *ctx, int32_t enable);
+
+/* Number of CUDA kernels this library has launched in the process so far. */
+KMPAR_API int64_t kmpar_launch_count(void);
+
+KMPAR_API void kmpar_destroy(kmpar_ctx *ctx);
+KMPAR_API const char *kmpar_status_string(kmpar_status s);
+/* Last error message of ctx, or of the calling thread's last context-free call
+ * when ctx is NULL. */
+KMPAR_API const char *kmpar_last_error(const kmpar_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KMPAR_H */

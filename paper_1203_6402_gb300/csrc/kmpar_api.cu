@@ -1,0 +1,432 @@
+// kmpar_api.cu -- the C ABI of include/kmpar.h: argument checks, context
+// buffers, the call order of Algorithm 2 (Bahmani et al., Sec. 3.3) and Lloyd's
+// loop.  Every step of the path runs in the kernels of this library.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <string>
+
+#include "kmpar_internal.cuh"
+
+struct kmpar_ctx {
+    kmp::Ctx c;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+kmpar_status fail(kmp::Ctx *c, kmpar_status s, const std::string &msg) {
+    if (c) c->err = msg; else g_err = msg;
+    return s;
+}
+
+kmpar_status cuda_fail(kmp::Ctx *c, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? KMPAR_ERR_OOM : KMPAR_ERR_CUDA, m);
+}
+
+#define KMP_CUDA(ctx, expr, where)                          \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e, where); \
+    } while (0)
+
+bool precision_supported(int p) { return p == KMPAR_FP32; }
+
+int round_capacity(double ell) {
+    double c = ell + 10.0 * sqrt(ell) + 64.0;
+    if (c > 2.0e9) c = 2.0e9;
+    return (int)ceil(c);
+}
+
+template <typename T>
+cudaError_t alloc(T **p, size_t count) {
+    return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1));
+}
+
+void free_ctx(kmp::Ctx &c) {
+    void *bufs[] = {c.st, c.D2, c.idx, c.drawn, c.cand, c.C, c.w, c.rD2, c.chosen, c.partials,
+                    c.labels[0], c.labels[1], c.perm, c.hist, c.base, c.cost_dev, c.Xb, c.Cb, c.xnorm};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+}
+
+int sort_pow2(int cap) {
+    int P = 1;
+    while (P < cap) P <<= 1;
+    return P;
+}
+
+}  // namespace
+
+namespace kmp {
+// kernels configured once per process (dynamic shared memory above 48 KB)
+cudaError_t configure_kernels(int max_sort_pow2, int k);
+
+std::atomic<long long> g_launches{0};
+
+cudaError_t timing_begin(Ctx &c, cudaEvent_t *a) {
+    *a = nullptr;
+    if (!c.timing) return cudaSuccess;
+    cudaError_t e;
+    if (c.event_pool.empty()) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return e;
+        c.event_pool.push_back(ev);
+    }
+    *a = c.event_pool.back();
+    c.event_pool.pop_back();
+    return cudaEventRecord(*a, c.stream);
+}
+
+cudaError_t timing_end(Ctx &c, cudaEvent_t a, int cls) {
+    if (!c.timing || !a) return cudaSuccess;
+    cudaError_t e;
+    if (c.event_pool.empty()) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return e;
+        c.event_pool.push_back(ev);
+    }
+    cudaEvent_t b = c.event_pool.back();
+    c.event_pool.pop_back();
+    c.pending.push_back({a, b, cls});
+    return cudaEventRecord(b, c.stream);
+}
+
+cudaError_t timing_drain(Ctx &c) {
+    for (auto &p : c.pending) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&ms, p.a, p.b);
+        if (e != cudaSuccess) return e;
+        c.kernel_ms[p.cls] += ms;
+        c.kernel_launches[p.cls] += 1;
+        c.event_pool.push_back(p.a);
+        c.event_pool.push_back(p.b);
+    }
+    c.pending.clear();
+    return cudaSuccess;
+}
+}  // namespace kmp
+
+extern "C" {
+
+const char *kmpar_status_string(kmpar_status s) {
+    switch (s) {
+        case KMPAR_OK: return "ok";
+        case KMPAR_ERR_ARG: return "invalid argument";
+        case KMPAR_ERR_CUDA: return "CUDA error";
+        case KMPAR_ERR_OOM: return "out of device memory";
+        case KMPAR_ERR_CAPACITY: return "round drew more points than its capacity";
+        case KMPAR_ERR_TIMEOUT: return "device-side wait timed out";
+        case KMPAR_ERR_STATE: return "call out of order";
+        case KMPAR_WARN_FEW_CANDIDATES: return "reclustering ran out of positive mass before k draws";
+        case KMPAR_ERR_UNSUPPORTED: return "unsupported precision or size";
+    }
+    return "unknown status";
+}
+
+const char *kmpar_last_error(const kmpar_ctx *ctx) { return ctx ? ctx->c.err.c_str() : g_err.c_str(); }
+
+kmpar_status kmpar_init(kmpar_ctx **out, const float *X, int64_t n, int32_t d, int32_t k, double ell,
+                        int32_t rounds, uint64_t seed, int32_t precision, void *stream) {
+    if (!out) return fail(nullptr, KMPAR_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!X) return fail(nullptr, KMPAR_ERR_ARG, "X is NULL");
+    if (n < 1 || n >= (int64_t)INT32_MAX) return fail(nullptr, KMPAR_ERR_ARG, "n out of range [1, 2^31)");
+    if (d < 1 || d > 4096) return fail(nullptr, KMPAR_ERR_ARG, "d out of range [1, 4096]");
+    if (k < 1) return fail(nullptr, KMPAR_ERR_ARG, "k must be >= 1");
+    if (!(ell > 0.0) || !isfinite(ell)) return fail(nullptr, KMPAR_ERR_ARG, "ell must be finite and > 0");
+    if (rounds < 0 || rounds > kmp::kMaxRounds) return fail(nullptr, KMPAR_ERR_ARG, "rounds out of range [0, 64]");
+    if (!precision_supported(precision))
+        return fail(nullptr, KMPAR_ERR_UNSUPPORTED, "precision not built into this library");
+    const int cap_round = round_capacity(ell);
+    if (cap_round > kmp::kMaxRoundCap)
+        return fail(nullptr, KMPAR_ERR_UNSUPPORTED, "l + 10 sqrt(l) + 64 exceeds the per-round capacity 32768");
+    const int64_t cap_total64 = 1 + (int64_t)rounds * cap_round;
+    if (cap_total64 >= INT32_MAX) return fail(nullptr, KMPAR_ERR_ARG, "candidate capacity too large");
+
+    kmpar_ctx *h = new kmpar_ctx();
+    kmp::Ctx &c = h->c;
+    c.X = X; c.n = n; c.d = d; c.k = k; c.ell = ell; c.rounds = rounds; c.seed = seed;
+    c.precision = precision; c.stream = (cudaStream_t)stream;
+    c.cap_round = cap_round;
+    c.cap_total = (int)cap_total64;
+    c.nsb = (int)((n + kmp::kSortBlock - 1) / kmp::kSortBlock);
+    c.num_partials = kmp::assign_num_partials(n, d);
+
+    auto bail = [&](kmpar_status s) {
+        std::string m = c.err;
+        free_ctx(c);
+        delete h;
+        g_err = m;
+        return s;
+    };
+    cudaError_t e;
+#define KMP_INIT_CUDA(expr, where) \
+    if ((e = (expr)) != cudaSuccess) return bail(cuda_fail(&c, e, where))
+    KMP_INIT_CUDA(cudaGetDevice(&c.dev), "cudaGetDevice");
+    KMP_INIT_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.dev), "sm count");
+    KMP_INIT_CUDA(kmp::configure_kernels(sort_pow2(cap_round), k), "configure kernels");
+    KMP_INIT_CUDA(alloc(&c.st, 1), "alloc state");
+    KMP_INIT_CUDA(alloc(&c.D2, n), "alloc D2");
+    KMP_INIT_CUDA(alloc(&c.idx, n), "alloc idx");
+    KMP_INIT_CUDA(alloc(&c.drawn, cap_round), "alloc draws");
+    KMP_INIT_CUDA(alloc(&c.cand, c.cap_total), "alloc candidates");
+    KMP_INIT_CUDA(alloc(&c.C, (size_t)c.cap_total * d), "alloc candidate rows");
+    KMP_INIT_CUDA(alloc(&c.w, c.cap_total), "alloc weights");
+    KMP_INIT_CUDA(alloc(&c.rD2, c.cap_total), "alloc recluster D2");
+    KMP_INIT_CUDA(alloc(&c.chosen, k), "alloc chosen");
+    KMP_INIT_CUDA(alloc(&c.partials, c.num_partials), "alloc partials");
+    KMP_INIT_CUDA(cudaMemsetAsync(c.st, 0, sizeof(kmp::DevState), c.stream), "memset state");
+    KMP_INIT_CUDA(kmp::launch_init_first(c), "init kernels");
+#undef KMP_INIT_CUDA
+    *out = h;
+    return KMPAR_OK;
+}
+
+kmpar_status kmpar_round(kmpar_ctx *ctx, int32_t i, int64_t *n_added, double *phi) {
+    if (!ctx) return fail(nullptr, KMPAR_ERR_ARG, "ctx is NULL");
+    kmp::Ctx &c = ctx->c;
+    if (i != c.rounds_done + 1 || i > c.rounds)
+        return fail(&c, KMPAR_ERR_STATE, "rounds must be called in order 1..rounds");
+    if (c.weighted) return fail(&c, KMPAR_ERR_STATE, "round after weight");
+    KMP_CUDA(&c, kmp::launch_round(c, i), "round kernels");
+    c.rounds_done = i;
+    if (n_added || phi) {
+        kmp::DevState st;
+        KMP_CUDA(&c, cudaMemcpyAsync(&st, c.st, sizeof(st), cudaMemcpyDeviceToHost, c.stream), "read state");
+        KMP_CUDA(&c, cudaStreamSynchronize(c.stream), "sync");
+        if (st.overflow) return fail(&c, KMPAR_ERR_CAPACITY, "a round drew more points than its capacity");
+        if (n_added) *n_added = st.round_added[i - 1];
+        if (phi) *phi = st.phi;
+    }
+    return KMPAR_OK;
+}
+
+kmpar_status kmpar_weight(kmpar_ctx *ctx, int64_t *m_out, const int32_t **cand_idx_dev, const int64_t **w_dev) {
+    if (!ctx) return fail(nullptr, KMPAR_ERR_ARG, "ctx is NULL");
+    kmp::Ctx &c = ctx->c;
+    if (c.rounds_done != c.rounds) return fail(&c, KMPAR_ERR_STATE, "weight before the last round");
+    KMP_CUDA(&c, kmp::launch_weights(c), "weights kernel");
+    kmp::DevState st;
+    KMP_CUDA(&c, cudaMemcpyAsync(&st, c.st, sizeof(st), cudaMemcpyDeviceToHost, c.stream), "read state");
+    KMP_CUDA(&c, cudaStreamSynchronize(c.stream), "sync");
+    KMP_CUDA(&c, kmp::timing_drain(c), "timing");
+    if (st.overflow) return fail(&c, KMPAR_ERR_CAPACITY, "a round drew more points than its capacity");
+    c.weighted = true;
+    if (m_out) *m_out = st.m;
+    if (cand_idx_dev) *cand_idx_dev = c.cand;
+    if (w_dev) *w_dev = reinterpret_cast<const int64_t *>(c.w);
+    return KMPAR_OK;
+}
+
+kmpar_status kmpar_recluster(kmpar_ctx *ctx, float *centers_dev) {
+    if (!ctx) return fail(nullptr, KMPAR_ERR_ARG, "ctx is NULL");
+    kmp::Ctx &c = ctx->c;
+    if (!centers_dev) return fail(&c, KMPAR_ERR_ARG, "centers_dev is NULL");
+    if (!c.weighted) return fail(&c, KMPAR_ERR_STATE, "recluster before weight");
+    KMP_CUDA(&c, cudaMemsetAsync(&c.st->warn, 0, sizeof(int32_t), c.stream), "memset warn");
+    KMP_CUDA(&c, kmp::launch_recluster(c, centers_dev), "recluster kernel");
+    int32_t warn = 0;
+    KMP_CUDA(&c, cudaMemcpyAsync(&warn, &c.st->warn, sizeof(warn), cudaMemcpyDeviceToHost, c.stream), "read warn");
+    KMP_CUDA(&c, cudaStreamSynchronize(c.stream), "sync");
+    return warn ? KMPAR_WARN_FEW_CANDIDATES : KMPAR_OK;
+}
+
+static kmpar_status ensure_lloyd_buffers(kmp::Ctx &c) {
+    if (c.labels[0]) return KMPAR_OK;
+    cudaError_t e;
+    if ((e = alloc(&c.labels[0], c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc labels");
+    if ((e = alloc(&c.labels[1], c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc labels");
+    if ((e = alloc(&c.perm, c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc perm");
+    if ((e = alloc(&c.hist, (size_t)c.nsb * c.k)) != cudaSuccess) return cuda_fail(&c, e, "alloc hist");
+    if ((e = alloc(&c.base, (size_t)c.k + 1)) != cudaSuccess) return cuda_fail(&c, e, "alloc base");
+    if ((e = alloc(&c.cost_dev, 4)) != cudaSuccess) return cuda_fail(&c, e, "alloc cost");
+    return KMPAR_OK;
+}
+
+kmpar_status kmpar_lloyd(kmpar_ctx *ctx, float *centers_dev, int32_t max_iter, int32_t *labels_dev,
+                         int32_t *iters, double *final_cost, double *cost_hist) {
+    if (!ctx) return fail(nullptr, KMPAR_ERR_ARG, "ctx is NULL");
+    kmp::Ctx &c = ctx->c;
+    if (!centers_dev) return fail(&c, KMPAR_ERR_ARG, "centers_dev is NULL");
+    if (max_iter < 0) return fail(&c, KMPAR_ERR_ARG, "max_iter < 0");
+    if (c.k > 49152) return fail(&c, KMPAR_ERR_UNSUPPORTED, "Lloyd supports k <= 49152");
+    kmpar_status s = ensure_lloyd_buffers(c);
+    if (s != KMPAR_OK) return s;
+    int cur = 0, t = 0;
+    double cost = 0.0;
+    int *changed = reinterpret_cast<int *>(c.cost_dev + 1);
+    for (;;) {
+        KMP_CUDA(&c, cudaMemsetAsync(changed, 0, sizeof(int), c.stream), "memset changed");
+        cudaEvent_t ev = nullptr;
+        KMP_CUDA(&c, kmp::timing_begin(c, &ev), "timing");
+        KMP_CUDA(&c, kmp::launch_assign(c.X, c.n, c.d, centers_dev, c.k, c.labels[cur],
+                                        t > 0 ? c.labels[cur ^ 1] : nullptr, changed, c.partials,
+                                        c.num_partials, &c.st->argmin_fp64, c.stream),
+                 "assign kernel");
+        KMP_CUDA(&c, kmp::timing_end(c, ev, 1), "timing");
+        KMP_CUDA(&c, kmp::launch_sum_f64(c.partials, c.num_partials, c.cost_dev, nullptr, c.stream), "cost sum");
+        struct { double cost; int changed; int pad; } hb;
+        KMP_CUDA(&c, cudaMemcpyAsync(&hb, c.cost_dev, 16, cudaMemcpyDeviceToHost, c.stream), "read cost");
+        KMP_CUDA(&c, cudaStreamSynchronize(c.stream), "sync");
+        KMP_CUDA(&c, kmp::timing_drain(c), "timing");
+        cost = hb.cost;
+        if (cost_hist) cost_hist[t] = cost;
+        if (t > 0 && hb.changed == 0) break;
+        if (t == max_iter) break;
+        KMP_CUDA(&c, kmp::launch_centroids(c, c.labels[cur], centers_dev), "centroid kernels");
+        cur ^= 1;
+        ++t;
+    }
+    if (labels_dev)
+        KMP_CUDA(&c, cudaMemcpyAsync(labels_dev, c.labels[cur], sizeof(int32_t) * c.n, cudaMemcpyDeviceToDevice,
+                                     c.stream), "copy labels");
+    KMP_CUDA(&c, cudaStreamSynchronize(c.stream), "sync");
+    c.lloyd_iters = t;
+    if (iters) *iters = t;
+    if (final_cost) *final_cost = cost;
+    return KMPAR_OK;
+}
+
+kmpar_status kmpar_cost(const float *X, int64_t n, int32_t d, const float *C, int32_t k, int32_t precision,
+                        double *phi, void *stream) {
+    if (!X || !C || !phi) return fail(nullptr, KMPAR_ERR_ARG, "NULL pointer");
+    if (n < 1 || n >= (int64_t)INT32_MAX || d < 1 || d > 4096 || k < 1)
+        return fail(nullptr, KMPAR_ERR_ARG, "size out of range");
+    if (!precision_supported(precision)) return fail(nullptr, KMPAR_ERR_UNSUPPORTED, "precision not built");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int np = kmp::assign_num_partials(n, d);
+    double *buf = nullptr;   // np partials, the sum, one counter
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&buf), sizeof(double) * (np + 2), s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "scratch alloc");
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(buf + np + 1);
+    e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = kmp::launch_assign(X, n, d, C, k, nullptr, nullptr, nullptr, buf, np, cnt, s);
+    if (e == cudaSuccess) e = kmp::launch_sum_f64(buf, np, buf + np, nullptr, s);
+    double h = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, buf + np, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaError_t e2 = cudaFreeAsync(buf, s);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cost kernels");
+    *phi = h;
+    return KMPAR_OK;
+}
+
+kmpar_status kmpar_state(const kmpar_ctx *ctx, const float **D2_dev, const int32_t **idx_dev) {
+    if (!ctx) return fail(nullptr, KMPAR_ERR_ARG, "ctx is NULL");
+    if (D2_dev) *D2_dev = ctx->c.D2;
+    if (idx_dev) *idx_dev = ctx->c.idx;
+    return KMPAR_OK;
+}
+
+kmpar_status kmpar_get_stats(kmpar_ctx *ctx, kmpar_stats *out) {
+    if (!ctx || !out) return fail(nullptr, KMPAR_ERR_ARG, "NULL pointer");
+    kmp::Ctx &c = ctx->c;
+    kmp::DevState st;
+    KMP_CUDA(&c, cudaMemcpyAsync(&st, c.st, sizeof(st), cudaMemcpyDeviceToHost, c.stream), "read state");
+    KMP_CUDA(&c, cudaStreamSynchronize(c.stream), "sync");
+    memset(out, 0, sizeof(*out));
+    out->n = c.n; out->m = st.m; out->d = c.d; out->k = c.k;
+    out->rounds_done = c.rounds_done; out->lloyd_iters = c.lloyd_iters;
+    for (int i = 0; i < kmp::kMaxRounds; ++i) out->round_added[i] = st.round_added[i];
+    for (int i = 0; i <= kmp::kMaxRounds; ++i) out->phi[i] = st.phi_hist[i];
+    out->sample_near = (int64_t)st.sample_near;
+    out->sample_refined = (int64_t)st.sample_refined;
+    out->argmin_fp64 = (int64_t)st.argmin_fp64;
+    out->argmin_wide = (int64_t)st.argmin_wide;
+    out->recluster_near = (int64_t)st.recluster_near;
+    out->capacity_overflow = st.overflow;
+    out->recluster_warn = st.warn;
+    KMP_CUDA(&c, kmp::timing_drain(c), "timing");
+    for (int i = 0; i < 2; ++i) {
+        out->kernel_ms[i] = c.kernel_ms[i];
+        out->kernel_launches[i] = c.kernel_launches[i];
+    }
+    return KMPAR_OK;
+}
+
+kmpar_status kmpar_uniforms(int64_t count, uint32_t round, uint32_t tag, uint64_t seed, double *out_dev,
+                            void *stream) {
+    if (count < 0 || (count > 0 && !out_dev)) return fail(nullptr, KMPAR_ERR_ARG, "bad arguments");
+    if (count == 0) return KMPAR_OK;
+    cudaError_t e = kmp::launch_uniforms(count, round, tag, seed, out_dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "uniforms kernel");
+    return KMPAR_OK;
+}
+
+kmpar_status kmpar_fit(const float *X, int64_t n, int32_t d, int32_t k, double ell, int32_t rounds, uint64_t seed,
+                       int32_t precision, int32_t max_iter, float *centers_out, int32_t *labels_out,
+                       double *seed_cost, double *final_cost, int32_t *iters, int32_t flags, void *stream) {
+    if (!X || !centers_out) return fail(nullptr, KMPAR_ERR_ARG, "NULL pointer");
+    if (n < 1 || d < 1 || k < 1) return fail(nullptr, KMPAR_ERR_ARG, "size out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool host = (flags & KMPAR_HOST_BUFFERS) != 0;
+    const float *Xd = X;
+    float *Xbuf = nullptr, *Cd = centers_out;
+    int32_t *Ld = labels_out;
+    cudaError_t e = cudaSuccess;
+    if (host) {
+        e = cudaMallocAsync(reinterpret_cast<void **>(&Xbuf), sizeof(float) * (size_t)n * d, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Xbuf, X, sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&Cd), sizeof(float) * (size_t)k * d, s);
+        if (e == cudaSuccess && labels_out)
+            e = cudaMallocAsync(reinterpret_cast<void **>(&Ld), sizeof(int32_t) * (size_t)n, s);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "fit staging");
+        Xd = Xbuf;
+    }
+    kmpar_ctx *ctx = nullptr;
+    kmpar_status st = kmpar_init(&ctx, Xd, n, d, k, ell, rounds, seed, precision, stream);
+    for (int i = 1; st == KMPAR_OK && i <= rounds; ++i) st = kmpar_round(ctx, i, nullptr, nullptr);
+    if (st == KMPAR_OK) st = kmpar_weight(ctx, nullptr, nullptr, nullptr);
+    kmpar_status warn = KMPAR_OK;
+    if (st == KMPAR_OK) {
+        st = kmpar_recluster(ctx, Cd);
+        if (st == KMPAR_WARN_FEW_CANDIDATES) { warn = st; st = KMPAR_OK; }
+    }
+    if (st == KMPAR_OK && seed_cost) st = kmpar_cost(Xd, n, d, Cd, k, precision, seed_cost, stream);
+    if (st == KMPAR_OK) st = kmpar_lloyd(ctx, Cd, max_iter, Ld, iters, final_cost, nullptr);
+    if (st != KMPAR_OK && ctx) g_err = ctx->c.err;
+    if (ctx) kmpar_destroy(ctx);
+    if (host) {
+        if (st == KMPAR_OK) {
+            e = cudaMemcpyAsync(centers_out, Cd, sizeof(float) * (size_t)k * d, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess && labels_out)
+                e = cudaMemcpyAsync(labels_out, Ld, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s);
+        }
+        cudaFreeAsync(Xbuf, s);
+        cudaFreeAsync(Cd, s);
+        if (Ld) cudaFreeAsync(Ld, s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = e2;
+        if (st == KMPAR_OK && e != cudaSuccess) return cuda_fail(nullptr, e, "fit copy-out");
+    }
+    return st != KMPAR_OK ? st : warn;
+}
+
+kmpar_status kmpar_set_timing(kmpar_ctx *ctx, int32_t enable) {
+    if (!ctx) return fail(nullptr, KMPAR_ERR_ARG, "ctx is NULL");
+    ctx->c.timing = enable != 0;
+    return KMPAR_OK;
+}
+
+int64_t kmpar_launch_count(void) { return (int64_t)kmp::g_launches.load(); }
+
+void kmpar_destroy(kmpar_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->c.stream);
+    for (auto &p : ctx->c.pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto ev : ctx->c.event_pool) cudaEventDestroy(ev);
+    free_ctx(ctx->c);
+    delete ctx;
+}
+
+}  // extern "C"

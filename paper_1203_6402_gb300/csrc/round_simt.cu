@@ -1,0 +1,416 @@
+// round_simt.cu -- the per-round data-parallel pass of k-means|| (Alg. 2 steps
+// 1-2, 4-5 of Bahmani et al., Sec. 3.3) and the nearest-center scan that Lloyd's
+// iteration and phi_X(C) (Sec. 3.1) reuse, on CUDA cores in exact FP32.
+//
+// Kernels:
+//   pick_first_kernel   Alg. 2 step 1: i0 = floor(u n), row gathered as candidate 0
+//   nearest_kernel      d^2(x, C') for the batch C' (or all k centers), top-2 per
+//                       row, FP64 re-decision of near ties, D^2/idx/labels update,
+//                       per-block FP64 partial of phi
+//   sample_kernel       Alg. 2 step 4: p = min(1, l D^2/phi), Philox draw,
+//                       warp-aggregated atomic append
+//   sort_batch_kernel   ascending order of the round's draws (one CTA, bitonic)
+//   gather_kernel       candidate rows copied out of X
+//   sum_f64_kernel      fixed-order FP64 sum of per-block partials
+#include <float.h>
+
+#include <algorithm>
+
+#include "kmpar_internal.cuh"
+
+namespace kmp {
+
+constexpr int kNearThreads = 128;
+
+enum { MODE_FIRST = 0, MODE_ROUND = 1, MODE_ASSIGN = 2 };
+
+struct NearestParams {
+    const float *X;
+    int64_t n;
+    int d;
+    const float *C;        // center rows, stride d
+    int c_begin, c_cnt;    // ASSIGN: static range; FIRST/ROUND: taken from st
+    const DevState *st;
+    float *D2;             // FIRST: out; ROUND: in/out
+    int32_t *idx;          // FIRST: out; ROUND: in/out
+    int32_t *labels;       // ASSIGN: out (nullable)
+    const int32_t *prev;   // ASSIGN: previous labels (nullable)
+    int *changed;          // ASSIGN: +number of labels != prev (nullable)
+    double *partials;      // per-block FP64 sum of the stored distances
+    unsigned long long *fp64_cnt, *wide_cnt;
+};
+
+// lexicographic (value, index) improvement
+__device__ __forceinline__ void take_if_better(double v, int j, double &best, int &bj) {
+    if (v < best || (v == best && j < bj)) { best = v; bj = j; }
+}
+
+template <int DP, int MODE>
+__global__ void __launch_bounds__(kNearThreads) nearest_kernel(NearestParams p) {
+    constexpr int TC = DP == 0 ? 1 : (DP <= 64 ? 64 : 32);
+    constexpr int TILE = DP == 0 ? 4 : TC * DP;
+    __shared__ __align__(16) float tile[TILE];
+    __shared__ double red[32];
+    __shared__ int redi[32];
+
+    const int tid = threadIdx.x;
+    const int64_t pt = (int64_t)blockIdx.x * kNearThreads + tid;
+    const bool valid = pt < p.n;
+    const int d = p.d;
+    const float *xrow = p.X + (valid ? pt : 0) * (int64_t)d;
+
+    float xr[DP == 0 ? 1 : DP];
+    if constexpr (DP > 0) {
+#pragma unroll
+        for (int q = 0; q < DP; ++q) xr[q] = (valid && q < d) ? __ldg(xrow + q) : 0.f;
+    }
+
+    int begin, cnt;
+    if constexpr (MODE == MODE_ASSIGN) {
+        begin = p.c_begin; cnt = p.c_cnt;
+    } else {
+        begin = p.st->batch_begin; cnt = p.st->batch_cnt;
+    }
+
+    float b1 = FLT_MAX, b2 = FLT_MAX;
+    int i1 = -1, i2 = -1;
+    for (int t0 = 0; t0 < cnt; t0 += TC) {
+        const int nt = min(TC, cnt - t0);
+        if constexpr (DP > 0) {
+            __syncthreads();
+            for (int e = tid; e < TC * DP; e += kNearThreads) {
+                const int r = e / DP, q = e - r * DP;
+                tile[e] = (r < nt && q < d) ? __ldg(p.C + (int64_t)(begin + t0 + r) * d + q) : 0.f;
+            }
+            __syncthreads();
+        }
+        if (valid) {
+            for (int r = 0; r < nt; ++r) {
+                float acc = 0.f;
+                if constexpr (DP > 0) {
+                    const float4 *c4 = reinterpret_cast<const float4 *>(tile + r * DP);
+#pragma unroll
+                    for (int q4 = 0; q4 < DP / 4; ++q4) {
+                        const float4 c = c4[q4];
+                        float t;
+                        t = __fsub_rn(xr[4 * q4 + 0], c.x); acc = __fmaf_rn(t, t, acc);
+                        t = __fsub_rn(xr[4 * q4 + 1], c.y); acc = __fmaf_rn(t, t, acc);
+                        t = __fsub_rn(xr[4 * q4 + 2], c.z); acc = __fmaf_rn(t, t, acc);
+                        t = __fsub_rn(xr[4 * q4 + 3], c.w); acc = __fmaf_rn(t, t, acc);
+                    }
+                } else {
+                    acc = dist2_fp32(xrow, p.C + (int64_t)(begin + t0 + r) * d, d);
+                }
+                const int j = begin + t0 + r;
+                if (acc < b2) {
+                    if (acc < b1) { b2 = b1; i2 = i1; b1 = acc; i1 = j; }
+                    else { b2 = acc; i2 = j; }
+                }
+            }
+        }
+    }
+
+    float stored = 0.f;
+    int chg = 0;
+    if (valid) {
+        const float W = fp32_tie_window(d);
+        if constexpr (MODE == MODE_ASSIGN) {
+            int lab = i1;
+            stored = b1;
+            if (i2 >= 0 && b2 <= b1 + W * b1) {
+                // the FP32 order of the two best may differ from the FP64 order
+                double best = dist2_fp64(xrow, p.C + (int64_t)i1 * d, d);
+                int bj = i1;
+                take_if_better(dist2_fp64(xrow, p.C + (int64_t)i2 * d, d), i2, best, bj);
+                if (bj == i2) { lab = i2; stored = b2; }
+                atomicAdd(p.fp64_cnt, 1ull);
+            }
+            if (p.labels) p.labels[pt] = lab;
+            if (p.prev) chg = (p.prev[pt] != lab);
+        } else if constexpr (MODE == MODE_FIRST) {
+            stored = (i1 >= 0) ? b1 : __int_as_float(0x7f800000);
+            p.D2[pt] = stored;
+            p.idx[pt] = 0;
+        } else {
+            const float old = p.D2[pt];
+            const int oi = p.idx[pt];
+            const float m32 = fminf(old, b1);
+            const float lim = m32 + W * m32;
+            const bool in_old = (oi >= 0) && old <= lim;
+            const bool in1 = i1 >= 0 && b1 <= lim;
+            const bool in2 = i2 >= 0 && b2 <= lim;
+            int win = -1;
+            float wv = old;
+            if ((int)in_old + (int)in1 + (int)in2 >= 2) {
+                double best = DBL_MAX;
+                int bj = INT_MAX;
+                if (in_old) take_if_better(dist2_fp64(xrow, p.C + (int64_t)oi * d, d), oi, best, bj);
+                if (in1) take_if_better(dist2_fp64(xrow, p.C + (int64_t)i1 * d, d), i1, best, bj);
+                if (in2) take_if_better(dist2_fp64(xrow, p.C + (int64_t)i2 * d, d), i2, best, bj);
+                atomicAdd(p.fp64_cnt, 1ull);
+                if (in1 && in2) atomicAdd(p.wide_cnt, 1ull);
+                if (bj == i1) { win = i1; wv = b1; }
+                else if (bj == i2) { win = i2; wv = b2; }
+            } else if (i1 >= 0 && b1 < old) {
+                win = i1; wv = b1;
+            }
+            if (win >= 0) {
+                p.D2[pt] = wv;
+                p.idx[pt] = win;
+                stored = wv;
+            } else {
+                stored = old;
+            }
+        }
+    }
+
+    const double s = block_sum_f64(valid ? (double)stored : 0.0, red);
+    if (tid == 0) p.partials[blockIdx.x] = s;
+    if constexpr (MODE == MODE_ASSIGN) {
+        if (p.changed) {
+            int c = warp_sum_i32(chg);
+            __syncthreads();
+            if ((tid & 31) == 0) redi[tid >> 5] = c;
+            __syncthreads();
+            if (tid == 0) {
+                int tot = 0;
+                for (int i = 0; i < kNearThreads / 32; ++i) tot += redi[i];
+                if (tot) atomicAdd(p.changed, tot);
+            }
+        }
+    }
+}
+
+template <int MODE>
+static cudaError_t launch_nearest_mode(const NearestParams &p, cudaStream_t s) {
+    const int grid = (int)((p.n + kNearThreads - 1) / kNearThreads);
+    const int d = p.d;
+#define KMP_NEAREST_CASE(DPV)                                              \
+    if (d <= DPV) {                                                         \
+        nearest_kernel<DPV, MODE><<<grid, kNearThreads, 0, s>>>(p);          \
+        count_launches(1);                                                   \
+        return cudaGetLastError();                                           \
+    }
+    KMP_NEAREST_CASE(4)
+    KMP_NEAREST_CASE(8)
+    KMP_NEAREST_CASE(16)
+    KMP_NEAREST_CASE(32)
+    KMP_NEAREST_CASE(48)
+    KMP_NEAREST_CASE(64)
+    KMP_NEAREST_CASE(96)
+    KMP_NEAREST_CASE(128)
+#undef KMP_NEAREST_CASE
+    nearest_kernel<0, MODE><<<grid, kNearThreads, 0, s>>>(p);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+int assign_num_partials(int64_t n, int) { return (int)((n + kNearThreads - 1) / kNearThreads); }
+
+// ------------------------------------------------------------------ init
+__global__ void pick_first_kernel(const float *X, int64_t n, int d, uint64_t seed, DevState *st,
+                                  int32_t *cand, float *C) {
+    __shared__ int64_t s_i0;
+    if (threadIdx.x == 0) {
+        const double u = uniform53(0, 0, TAG_INIT, seed);
+        int64_t i0 = (int64_t)floor(__dmul_rn(u, (double)n));
+        if (i0 >= n) i0 = n - 1;
+        s_i0 = i0;
+        st->i0 = (int32_t)i0;
+        cand[0] = (int32_t)i0;
+        st->m = 1;
+        st->batch_begin = 0;
+        st->batch_cnt = 1;
+        st->drawn = 0;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < d; q += blockDim.x) C[q] = X[s_i0 * (int64_t)d + q];
+}
+
+cudaError_t launch_init_first(Ctx &c) {
+    pick_first_kernel<<<1, 128, 0, c.stream>>>(c.X, c.n, c.d, c.seed, c.st, c.cand, c.C);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    NearestParams p{};
+    p.X = c.X; p.n = c.n; p.d = c.d; p.C = c.C; p.st = c.st; p.D2 = c.D2; p.idx = c.idx;
+    p.partials = c.partials; p.fp64_cnt = &c.st->argmin_fp64; p.wide_cnt = &c.st->argmin_wide;
+    e = launch_nearest_mode<MODE_FIRST>(p, c.stream);
+    if (e != cudaSuccess) return e;
+    return launch_phi_finalize(c, assign_num_partials(c.n, c.d), &c.st->phi, &c.st->phi_hist[0]);
+}
+
+// ------------------------------------------------------------------ sampling
+__global__ void sample_kernel(const float *__restrict__ D2, const int32_t *__restrict__ idx,
+                              const float *__restrict__ X, const float *__restrict__ C, int64_t n, int d,
+                              double ell, uint32_t round, uint64_t seed, DevState *st, int32_t *drawn,
+                              int cap) {
+    const double phi = st->phi;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        bool take = false;
+        if (i < n) {
+            const float dd = D2[i];
+            double pr = 0.0;
+            if (phi > 0.0) pr = fmin(1.0, __ddiv_rn(__dmul_rn(ell, (double)dd), phi));
+            const double u = uniform53((uint64_t)i, round, TAG_SAMPLE, seed);
+            if (dd > 0.f && fabs(u - pr) <= 1e-5) {
+                // the FP32 D^2 could decide this draw: use the FP64 distance of the definition
+                const double d64 = dist2_fp64(X + i * (int64_t)d, C + (int64_t)idx[i] * d, d);
+                pr = fmin(1.0, __ddiv_rn(__dmul_rn(ell, d64), phi));
+                atomicAdd(&st->sample_refined, 1ull);
+            }
+            if (fabs(u - pr) <= 1e-6) atomicAdd(&st->sample_near, 1ull);
+            take = u < pr;
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, take);
+        if (mask) {
+            const int leader = __ffs(mask) - 1;
+            int b = 0;
+            if (lane == leader) b = atomicAdd(&st->drawn, __popc(mask));
+            b = __shfl_sync(0xffffffffu, b, leader);
+            if (take) {
+                const int pos = b + __popc(mask & ((1u << lane) - 1u));
+                if (pos < cap) drawn[pos] = (int32_t)i;
+                else st->overflow = 1;
+            }
+        }
+    }
+}
+
+// one CTA: bitonic sort of this round's draws (ascending point order), appended to
+// the candidate list; the batch range is published in st for the next kernels.
+__global__ void __launch_bounds__(1024) sort_batch_kernel(const int32_t *drawn, int cap, int round,
+                                                          DevState *st, int32_t *cand) {
+    extern __shared__ int32_t keys[];
+    const int total = st->drawn;
+    const int cnt = min(total, cap);
+    int P = 1;
+    while (P < cnt) P <<= 1;
+    for (int e = threadIdx.x; e < P; e += blockDim.x) keys[e] = e < cnt ? drawn[e] : INT_MAX;
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < P; e += blockDim.x) {
+                const int o = e ^ stride;
+                if (o > e) {
+                    const bool asc = (e & size) == 0;
+                    const int a = keys[e], b = keys[o];
+                    if ((a > b) == asc) { keys[e] = b; keys[o] = a; }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int m0 = st->m;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) cand[m0 + e] = keys[e];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->batch_begin = m0;
+        st->batch_cnt = cnt;
+        st->m = m0 + cnt;
+        st->round_added[round - 1] = total;
+        st->drawn = 0;
+    }
+}
+
+__global__ void gather_kernel(const float *__restrict__ X, int d, const DevState *st, const int32_t *cand,
+                              float *C) {
+    const int begin = st->batch_begin, cnt = st->batch_cnt;
+    const int64_t total = (int64_t)cnt * d;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / d;
+        const int q = (int)(e - r * d);
+        C[(begin + r) * d + q] = X[(int64_t)cand[begin + r] * d + q];
+    }
+}
+
+__global__ void __launch_bounds__(1024) sum_f64_kernel(const double *parts, int nparts, double *out,
+                                                      double *copy) {
+    __shared__ double sh[32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += parts[i];
+    const double s = block_sum_f64(v, sh);
+    if (threadIdx.x == 0) {
+        *out = s;
+        if (copy) *copy = s;
+    }
+}
+
+cudaError_t launch_sum_f64(const double *parts, int nparts, double *out, double *copy, cudaStream_t s) {
+    sum_f64_kernel<<<1, 1024, 0, s>>>(parts, nparts, out, copy);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phi_finalize(Ctx &c, int nparts, double *out, double *hist_slot) {
+    return launch_sum_f64(c.partials, nparts, out, hist_slot, c.stream);
+}
+
+cudaError_t launch_round(Ctx &c, int round) {
+    cudaError_t e;
+    const int sgrid = c.num_sms * 8;
+    sample_kernel<<<sgrid, 256, 0, c.stream>>>(c.D2, c.idx, c.X, c.C, c.n, c.d, c.ell, (uint32_t)round,
+                                               c.seed, c.st, c.drawn, c.cap_round);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int P = 1;
+    while (P < c.cap_round) P <<= 1;
+    sort_batch_kernel<<<1, 1024, P * sizeof(int32_t), c.stream>>>(c.drawn, c.cap_round, round, c.st, c.cand);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int64_t gtot = (int64_t)c.cap_round * c.d;
+    const int ggrid = (int)std::min<int64_t>((gtot + 255) / 256, (int64_t)c.num_sms * 16);
+    gather_kernel<<<ggrid, 256, 0, c.stream>>>(c.X, c.d, c.st, c.cand, c.C);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    count_launches(3);
+    return launch_round_distance(c, round);
+}
+
+// Alg. 2 step 5: D^2/idx against the batch just appended, then phi
+cudaError_t launch_round_distance(Ctx &c, int round) {
+    cudaError_t e;
+    cudaEvent_t ev = nullptr;
+    if ((e = timing_begin(c, &ev)) != cudaSuccess) return e;
+    NearestParams p{};
+    p.X = c.X; p.n = c.n; p.d = c.d; p.C = c.C; p.st = c.st; p.D2 = c.D2; p.idx = c.idx;
+    p.partials = c.partials; p.fp64_cnt = &c.st->argmin_fp64; p.wide_cnt = &c.st->argmin_wide;
+    if ((e = launch_nearest_mode<MODE_ROUND>(p, c.stream)) != cudaSuccess) return e;
+    if ((e = timing_end(c, ev, 0)) != cudaSuccess) return e;
+    return launch_phi_finalize(c, assign_num_partials(c.n, c.d), &c.st->phi, &c.st->phi_hist[round]);
+}
+
+cudaError_t launch_assign(const float *X, int64_t n, int d, const float *C, int k, int32_t *labels,
+                          const int32_t *prev, int *changed, double *partials, int,
+                          unsigned long long *fp64_cnt, cudaStream_t s) {
+    NearestParams p{};
+    p.X = X; p.n = n; p.d = d; p.C = C; p.c_begin = 0; p.c_cnt = k;
+    p.labels = labels; p.prev = prev; p.changed = changed; p.partials = partials;
+    p.fp64_cnt = fp64_cnt; p.wide_cnt = fp64_cnt;
+    return launch_nearest_mode<MODE_ASSIGN>(p, s);
+}
+
+// ------------------------------------------------------------------ generator export
+__global__ void uniforms_kernel(int64_t count, uint32_t round, uint32_t tag, uint64_t seed, double *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = uniform53((uint64_t)i, round, tag, seed);
+}
+
+cudaError_t launch_uniforms(int64_t count, uint32_t round, uint32_t tag, uint64_t seed, double *out,
+                            cudaStream_t s) {
+    const int grid = (int)std::min<int64_t>((count + 255) / 256, 4096);
+    uniforms_kernel<<<grid > 0 ? grid : 1, 256, 0, s>>>(count, round, tag, seed, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace kmp
+
+namespace kmp {
+cudaError_t configure_round_kernels(int max_sort_pow2) {
+    return cudaFuncSetAttribute(sort_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                max_sort_pow2 * (int)sizeof(int32_t));
+}
+}  // namespace kmp

@@ -1,0 +1,258 @@
+"""GPU parity: every step of k-means|| through the C ABI against the FP64 oracle
+on the same seeded inputs (Algorithm 2, Sec. 3.3; Lloyd, Sec. 3.1).
+
+Bar (per step): candidate sets and weights bit-exact; idx/labels bit-exact except
+where the oracle reports a near tie (runner-up within 1e-6 relative); draws
+bit-exact except where the oracle reports |u - p| <= 1e-6; D^2 within 1e-5
+relative (exact FP32 difference form vs FP64; absolute floor 1e-30); phi within
+1e-6 relative; final Lloyd cost within 1e-4 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1203_6402_gb300 import datagen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+D2_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def km():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_6402_gb300 import kmpar
+    kmpar.load()
+    return kmpar
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _close_d2(gpu, ref):
+    ref = np.asarray(ref, np.float64)
+    gpu = np.asarray(gpu, np.float64)
+    return np.abs(gpu - ref) <= D2_RTOL * np.abs(ref) + 1e-30
+
+
+def run_and_compare(km, orc, X, k, ell, rounds, seed, precision="fp32", max_iter=100):
+    """Runs the GPU path step by step and the oracle beside it; asserts the bar.
+
+    Returns a dict of diagnostics.  If the trajectories part at a reported near
+    tie, the remaining steps are checked for validity only (diag['parted'])."""
+    n, d = X.shape
+    Xd = _dev(X)
+    g = km.KMeansPar(Xd, k, ell, rounds, seed, precision=precision)
+    diag = dict(parted=None)
+    # Alg. 2 steps 1-2
+    i0 = orc.init_index(n, seed)
+    D2, idx, psi = orc.init(X, i0)
+    gD2, gidx = g.state()
+    assert np.all(_close_d2(gD2.cpu().numpy(), D2))
+    assert np.all(gidx.cpu().numpy() == 0)
+    cand = [i0]
+    phi = psi
+    for r in range(1, rounds + 1):
+        sel, p, nsamp = orc.sample(D2, phi, ell, r, seed)
+        phi, narg = orc.update(X, sel, len(cand), D2, idx)
+        na, gphi = g.round(r, sync=True)
+        cand.extend(int(s) for s in sel)
+        gD2, gidx = g.state()
+        gD2, gidx = gD2.cpu().numpy(), gidx.cpu().numpy()
+        if na != len(sel):
+            diag["parted"] = ("round", r)
+            break
+        assert math.isclose(gphi, phi, rel_tol=1e-6), (r, gphi, phi)
+        ok_d2 = _close_d2(gD2, D2)
+        ok_idx = gidx == idx
+        bad = ~(ok_d2 & ok_idx) & ~narg
+        assert not bad.any(), f"round {r}: {bad.sum()} points differ (first {np.flatnonzero(bad)[:5]})"
+    stats = g.stats()
+    diag["stats"] = stats
+    m, ci, wp = km.kmpar_weight(g.ctx)
+    gcand, gw = g.candidates()
+    gcand, gw = gcand.cpu().numpy(), gw.cpu().numpy()
+    if diag["parted"] is None:
+        if not np.array_equal(gcand, np.array(cand)):
+            # a draw may flip only at a reported near tie
+            diag["parted"] = ("candidates", None)
+        else:
+            w = orc.weights(idx, len(cand))
+            assert np.array_equal(gw, w)
+    assert gw.sum() == n                                             # step 7: sum w = n
+    C, st = g.recluster()
+    Ch = C.cpu().numpy()
+    # the seed centers are rows of X from the candidate set
+    rows = gcand
+    if diag["parted"] is None:
+        chosen, rnear, rwarn = orc.recluster(X[rows].astype(np.float64), gw, k, seed)
+        assert (st == km.KMPAR_WARN_FEW_CANDIDATES) == rwarn
+        same = np.all(Ch == X[rows[chosen]], axis=1)
+        if not same.all():
+            assert rnear.any() or stats["recluster_near"] > 0, "recluster differs without a reported near tie"
+            diag["parted"] = ("recluster", int(np.argmin(same)))
+    C0 = Ch.copy()
+    out = g.lloyd(C, max_iter, labels=True, hist=True)
+    Cf = C.cpu().numpy()
+    lab = out["labels"].cpu().numpy()
+    # Lloyd from the same seed centers in the oracle
+    oC, olab, oit, ofc, ohist, onear = orc.lloyd(X, C0.astype(np.float64), max_iter)
+    seed_cost = orc.cost(X, C0.astype(np.float64))
+    assert math.isclose(out["cost_hist"][0], seed_cost, rel_tol=1e-6)
+    if out["iters"] == oit and np.array_equal(lab, olab):
+        assert math.isclose(out["final_cost"], ofc, rel_tol=1e-4)
+        np.testing.assert_allclose(Cf, oC, rtol=1e-5, atol=1e-5 * (np.abs(oC).max() + 1))
+    else:
+        # a Lloyd trajectory may part only at a near tie; the final state must still be valid
+        assert onear.any() or diag["stats"]["argmin_fp64"] > 0
+        diag["lloyd_parted"] = True
+        assert out["final_cost"] <= seed_cost * (1 + 1e-6)
+    # the GPU's final labels are the nearest centers of its final centers (FP64 check)
+    Cf64 = Cf.astype(np.float64)
+    D = ((X.astype(np.float64)[:, None, :] - Cf64[None]) ** 2).sum(-1) if n * k <= 4_000_000 else None
+    if D is not None:
+        best = D.min(1)
+        assert np.all(D[np.arange(n), lab] <= best * (1 + 1e-6) + 1e-30)
+        assert math.isclose(out["final_cost"], best.sum(), rel_tol=1e-5)
+    hist = np.array(out["cost_hist"])
+    assert np.all(np.diff(hist) <= 1e-6 * hist[0])                   # cost never increases
+    diag["iters"] = out["iters"]
+    diag["final_cost"] = out["final_cost"]
+    g.close()
+    return diag
+
+
+CASES = [
+    # name, X maker, k, ell, rounds, seed
+    ("gmm_small", lambda: datagen.gauss_mixture(3000, 15, 20, 10.0, seed=1), 20, 40.0, 5, 3),
+    ("kdd_like", lambda: datagen.kdd_like(2500, seed=2), 30, 60.0, 5, 4),
+    ("ragged_d1", lambda: datagen.uniform_box(1001, 1, seed=3), 7, 14.0, 4, 5),
+    ("d130_generic", lambda: datagen.gauss_mixture(777, 130, 6, 4.0, seed=4), 6, 12.0, 3, 6),
+    ("d128", lambda: datagen.gauss_mixture(1500, 128, 12, 100.0, seed=5), 12, 24.0, 5, 7),
+    ("d42_many_centers", lambda: datagen.kdd_like(2000, seed=6), 64, 300.0, 3, 8),
+]
+
+
+@pytest.mark.parametrize("name,mk,k,ell,rounds,seed", CASES, ids=[c[0] for c in CASES])
+def test_parity_fp32(km, orc, name, mk, k, ell, rounds, seed):
+    X = mk()
+    diag = run_and_compare(km, orc, X, k, ell, rounds, seed)
+    assert diag["parted"] is None, diag
+
+
+def test_philox_matches_oracle(km, orc):
+    for rnd, tag, seed in [(0, 1, 0), (3, 2, 12345), (0, 3, (1 << 40) + 7)]:
+        out = torch.empty(20000, dtype=torch.float64, device="cuda")
+        km.kmpar_uniforms(20000, rnd, tag, seed, out.data_ptr())
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        ref = np.array([orc.uniform(i, rnd, tag, seed) for i in range(20000)])
+        assert np.array_equal(got, ref)
+
+
+def test_cost_matches_oracle(km, orc):
+    X = datagen.kdd_like(5000, seed=9)
+    C = X[::97][:40].copy()
+    phi = km.kmpar_cost(_dev(X).data_ptr(), 5000, X.shape[1], _dev(C).data_ptr(), len(C))
+    assert math.isclose(phi, orc.cost(X, C.astype(np.float64)), rel_tol=1e-6)
+
+
+def test_fit_host_buffers_matches_device(km):
+    X = datagen.gauss_mixture(4000, 15, 12, 10.0, seed=11)
+    n, d = X.shape
+    k = 12
+    Xd = _dev(X)
+    Cd = torch.empty(k, d, dtype=torch.float32, device="cuda")
+    Ld = torch.empty(n, dtype=torch.int32, device="cuda")
+    r1 = km.kmpar_fit(Xd.data_ptr(), n, d, k, 24.0, 5, 3, km.KMPAR_FP32, 50, Cd.data_ptr(), Ld.data_ptr())
+    Ch = np.zeros((k, d), np.float32)
+    Lh = np.zeros(n, np.int32)
+    r2 = km.kmpar_fit(X.ctypes.data, n, d, k, 24.0, 5, 3, km.KMPAR_FP32, 50, Ch.ctypes.data, Lh.ctypes.data,
+                      flags=km.KMPAR_HOST_BUFFERS)
+    assert r1["final_cost"] == r2["final_cost"] and r1["iters"] == r2["iters"]
+    assert np.array_equal(Cd.cpu().numpy(), Ch) and np.array_equal(Ld.cpu().numpy(), Lh)
+
+
+def test_run_to_run_deterministic(km):
+    X = datagen.kdd_like(30000, seed=12)
+    Xd = _dev(X)
+    res = []
+    for _ in range(2):
+        g = km.KMeansPar(Xd, 50, 100.0, 5, 21)
+        for r in range(1, 6):
+            g.round(r)
+        g.weight()
+        C, _ = g.recluster()
+        out = g.lloyd(C, 30)
+        res.append((C.cpu().numpy(), out["labels"].cpu().numpy(), out["final_cost"]))
+        g.close()
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert res[0][2] == res[1][2]
+
+
+# ------------------------------------------------------------------ edge cases
+def test_single_point(km, orc):
+    X = np.array([[1.5, -2.0, 3.0]], np.float32)
+    diag = run_and_compare(km, orc, X, 1, 2.0, 2, 1)
+    assert diag["final_cost"] == 0.0
+
+
+def test_all_identical_points_warns(km, orc):
+    X = np.full((300, 4), 2.5, np.float32)
+    g = km.KMeansPar(_dev(X), 3, 6.0, 3, 1)
+    for r in range(1, 4):
+        assert g.round(r, sync=True) == (0, 0.0)
+    assert g.weight() == 1
+    C, st = g.recluster()
+    assert st == km.KMPAR_WARN_FEW_CANDIDATES
+    assert np.all(C.cpu().numpy() == 2.5)
+    out = g.lloyd(C, 5)
+    assert out["final_cost"] == 0.0
+    g.close()
+
+
+def test_huge_ell_takes_all_points(km, orc):
+    # distinct grid points: every D^2 >= 1 > phi / l, so every p is capped at 1
+    X = np.stack(np.meshgrid(np.arange(4), np.arange(5), np.arange(2)), -1).reshape(-1, 3).astype(np.float32)
+    g = km.KMeansPar(_dev(X), 40, 3e4, 1, 3)
+    na, phi = g.round(1, sync=True)
+    assert na == 39 and phi == 0.0
+    assert g.weight() == 40
+    C, st = g.recluster()
+    out = g.lloyd(C, 5)
+    assert out["final_cost"] == 0.0
+    g.close()
+
+
+def test_state_machine_and_arguments(km):
+    X = _dev(datagen.uniform_box(100, 2, seed=1))
+    with pytest.raises(km.KmparError) as e:
+        km.kmpar_init(X.data_ptr(), 0, 2, 3, 4.0, 2, 0, km.KMPAR_FP32)
+    assert e.value.status == km.KMPAR_ERR_ARG
+    with pytest.raises(km.KmparError) as e:
+        km.kmpar_init(X.data_ptr(), 100, 2, 3, -1.0, 2, 0, km.KMPAR_FP32)
+    assert e.value.status == km.KMPAR_ERR_ARG
+    with pytest.raises(km.KmparError) as e:
+        km.kmpar_init(X.data_ptr(), 100, 2, 3, 1e6, 2, 0, km.KMPAR_FP32)
+    assert e.value.status == km.KMPAR_ERR_UNSUPPORTED
+    g = km.KMeansPar(X, 3, 4.0, 2, 0)
+    with pytest.raises(km.KmparError) as e:
+        g.round(2)
+    assert e.value.status == km.KMPAR_ERR_STATE
+    with pytest.raises(km.KmparError) as e:
+        g.weight()
+    assert e.value.status == km.KMPAR_ERR_STATE
+    g.round(1)
+    with pytest.raises(km.KmparError) as e:
+        g.recluster()
+    assert e.value.status == km.KMPAR_ERR_STATE
+    g.round(2)
+    g.weight()
+    with pytest.raises(km.KmparError) as e:
+        g.round(3)
+    assert e.value.status == km.KMPAR_ERR_STATE
+    g.close()

@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(kNearThreads) nearest_kernel(NearestParams p) 
     if (valid) {
         const float W = fp32_tie_window(d);
         if constexpr (MODE == MODE_ASSIGN) {
-            int lab = i1;
+            // a row whose distances are all NaN/inf keeps label 0 (labels stay in range)
+            int lab = i1 >= 0 ? i1 : 0;
             stored = b1;
             if (i2 >= 0 && b2 <= b1 + W * b1) {
                 // the FP32 order of the two best may differ from the FP64 order

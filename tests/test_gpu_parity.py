@@ -157,7 +157,8 @@ def test_philox_matches_oracle(km, orc):
 def test_cost_matches_oracle(km, orc):
     X = datagen.kdd_like(5000, seed=9)
     C = X[::97][:40].copy()
-    phi = km.kmpar_cost(_dev(X).data_ptr(), 5000, X.shape[1], _dev(C).data_ptr(), len(C))
+    Xd, Cd = _dev(X), _dev(C)          # keep both alive while the library reads them
+    phi = km.kmpar_cost(Xd.data_ptr(), 5000, X.shape[1], Cd.data_ptr(), len(C))
     assert math.isclose(phi, orc.cost(X, C.astype(np.float64)), rel_tol=1e-6)
 
 

@@ -166,6 +166,28 @@ KMPAR_API kmpar_status kmpar_cost(const float *X, int64_t n, int32_t d, const fl
                         int32_t precision, double *phi, void *stream);
 
 /*
+ * phi_X(C) like kmpar_cost, for callers that cannot allocate device memory when
+ * they need it: for instance a host framework that has reserved all of the GPU's
+ * memory for its own pool, or a latency-critical loop in which an allocation,
+ * which can synchronise the device, is not allowed.  The paper has no
+ * counterpart; this is a packaging variant of the Sec. 3.1 cost.
+ *
+ * No allocation: the per-block FP64 partial sums live in a fixed array inside the
+ * library (65,539 doubles, about 512 KB, held on every GPU that loads the library
+ * until the process exits).  The caller still passes X and C (device) and phi
+ * (host).  n is limited to 8,388,608 points (65,536 blocks of 128); larger n
+ * returns KMPAR_ERR_ARG with a message in kmpar_last_error(NULL).
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array, which keeps the last call's
+ * contents: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.  Synchronises.
+ */
+KMPAR_API kmpar_status kmpar_cost_noalloc(const float *X, int64_t n, int32_t d, const float *C, int32_t k,
+                                          double *phi, void *stream);
+
+/*
  * The whole path in one call: init, rounds 1..r, weight, recluster, Lloyd.
  * flags & KMPAR_HOST_BUFFERS: X, centers_out and labels_out are HOST pointers
  * (copied in and out inside the call); otherwise device pointers.  seed_cost,

@@ -69,6 +69,8 @@ cudaError_t configure_kernels(int max_sort_pow2, int k);
 
 std::atomic<long long> g_launches{0};
 
+void set_thread_error(const std::string &m) { g_err = m; }
+
 cudaError_t timing_begin(Ctx &c, cudaEvent_t *a) {
     *a = nullptr;
     if (!c.timing) return cudaSuccess;

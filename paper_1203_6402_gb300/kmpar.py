@@ -22,7 +22,7 @@ PRECISIONS = {"fp32": KMPAR_FP32, "bf16": KMPAR_BF16, "bf16x3": KMPAR_BF16X3}
 
 EXPORTED = ["kmpar_init", "kmpar_round", "kmpar_weight", "kmpar_recluster", "kmpar_lloyd", "kmpar_cost",
             "kmpar_fit", "kmpar_state", "kmpar_get_stats", "kmpar_uniforms", "kmpar_set_timing",
-            "kmpar_launch_count", "kmpar_destroy",
+            "kmpar_launch_count", "kmpar_cost_noalloc", "kmpar_destroy",
             "kmpar_status_string", "kmpar_last_error"]
 
 
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kmpar_uniforms": (i32, [i64, u32, u32, u64, P, P]),
         "kmpar_set_timing": (i32, [P, i32]),
         "kmpar_launch_count": (i64, []),
+        "kmpar_cost_noalloc": (i32, [P, i64, i32, P, i32, ctypes.POINTER(f64), P]),
         "kmpar_destroy": (None, [P]),
         "kmpar_status_string": (ctypes.c_char_p, [i32]),
         "kmpar_last_error": (ctypes.c_char_p, [P]),
@@ -139,6 +140,13 @@ def kmpar_cost(X_ptr: int, n: int, d: int, C_ptr: int, k: int, precision: int = 
                stream: int = 0) -> float:
     phi = ctypes.c_double()
     _check(load().kmpar_cost(X_ptr, n, d, C_ptr, k, precision, ctypes.byref(phi), stream))
+    return phi.value
+
+
+def kmpar_cost_noalloc(X_ptr: int, n: int, d: int, C_ptr: int, k: int, stream: int = 0) -> float:
+    """kmpar_cost without any device allocation (fixed in-library scratch, shared by all calls)."""
+    phi = ctypes.c_double()
+    _check(load().kmpar_cost_noalloc(X_ptr, n, d, C_ptr, k, ctypes.byref(phi), stream))
     return phi.value
 
 

@@ -231,6 +231,7 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": k * d * 4 + n * 4, "steps": e2e_steps},
         "roofline": roofline, "clocks": clocks,
         "refine": {key: st_t[key] for key in ("sample_near", "sample_refined", "argmin_fp64", "argmin_wide",
+                                             "screen_rows", "screen_fallback",
                                              "recluster_near")},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -92,6 +92,9 @@ typedef struct {
      * [0] = round passes (Alg. 2 step 5), [1] = Lloyd assignment passes */
     double  kernel_ms[2];
     int64_t kernel_launches[2];
+    int64_t screen_rows;          /* tensor-core passes: rows screened                 */
+    int64_t screen_fallback;      /* rows whose screening window held 2+ centers and
+                                     that the exact CUDA-core pass decided            */
 } kmpar_stats;
 
 /*
@@ -159,7 +162,8 @@ KMPAR_API kmpar_status kmpar_lloyd(kmpar_ctx *ctx, float *centers_dev, int32_t m
 /*
  * Sec. 3.1: phi_X(C) = sum_x min_i ||x - c_i||^2 for X (device, n x d FP32) and
  * C (device, k x d FP32), summed in FP64 over exact FP32 distances.  *phi (host)
- * receives the cost.  Allocates a small scratch buffer on the stream.
+ * receives the cost.  Every precision gives this same exact-FP32 value (the
+ * CUDA-core pass computes it).  Allocates a small scratch buffer on the stream.
  * Synchronises.
  */
 KMPAR_API kmpar_status kmpar_cost(const float *X, int64_t n, int32_t d, const float *C, int32_t k,

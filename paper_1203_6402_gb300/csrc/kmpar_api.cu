@@ -35,7 +35,12 @@ kmpar_status cuda_fail(kmp::Ctx *c, cudaError_t e, const char *where) {
         if (_e != cudaSuccess) return cuda_fail(ctx, _e, where); \
     } while (0)
 
-bool precision_supported(int p) { return p == KMPAR_FP32; }
+bool precision_supported(int p, int d) {
+    if (p == KMPAR_FP32) return true;
+    if (p == KMPAR_BF16) return kmp::tc::tc_supported(d, 0);
+    if (p == KMPAR_BF16X3) return kmp::tc::tc_supported(d, 1);
+    return false;
+}
 
 int round_capacity(double ell) {
     double c = ell + 10.0 * sqrt(ell) + 64.0;
@@ -50,7 +55,8 @@ cudaError_t alloc(T **p, size_t count) {
 
 void free_ctx(kmp::Ctx &c) {
     void *bufs[] = {c.st, c.D2, c.idx, c.drawn, c.cand, c.C, c.w, c.rD2, c.chosen, c.partials,
-                    c.labels[0], c.labels[1], c.perm, c.hist, c.base, c.cost_dev, c.Xb, c.Cb, c.xnorm};
+                    c.labels[0], c.labels[1], c.perm, c.hist, c.base, c.cost_dev, c.tc_img, c.tc_cnorm,
+                    c.tc_cmax, c.tc_err, c.cand1, c.fix_rows, c.fix_cnt, c.dmin, c.tc_ximg, c.tc_xnorm};
     for (void *b : bufs)
         if (b) cudaFree(b);
 }
@@ -143,8 +149,8 @@ kmpar_status kmpar_init(kmpar_ctx **out, const float *X, int64_t n, int32_t d, i
     if (k < 1) return fail(nullptr, KMPAR_ERR_ARG, "k must be >= 1");
     if (!(ell > 0.0) || !isfinite(ell)) return fail(nullptr, KMPAR_ERR_ARG, "ell must be finite and > 0");
     if (rounds < 0 || rounds > kmp::kMaxRounds) return fail(nullptr, KMPAR_ERR_ARG, "rounds out of range [0, 64]");
-    if (!precision_supported(precision))
-        return fail(nullptr, KMPAR_ERR_UNSUPPORTED, "precision not built into this library");
+    if (!precision_supported(precision, d))
+        return fail(nullptr, KMPAR_ERR_UNSUPPORTED, "precision not built into this library for this d");
     const int cap_round = round_capacity(ell);
     if (cap_round > kmp::kMaxRoundCap)
         return fail(nullptr, KMPAR_ERR_UNSUPPORTED, "l + 10 sqrt(l) + 64 exceeds the per-round capacity 32768");
@@ -183,10 +189,34 @@ kmpar_status kmpar_init(kmpar_ctx **out, const float *X, int64_t n, int32_t d, i
     KMP_INIT_CUDA(alloc(&c.rD2, c.cap_total), "alloc recluster D2");
     KMP_INIT_CUDA(alloc(&c.chosen, k), "alloc chosen");
     KMP_INIT_CUDA(alloc(&c.partials, c.num_partials), "alloc partials");
+    if (precision != KMPAR_FP32) {
+        const int split = precision == KMPAR_BF16X3 ? 1 : 0;
+        const int rows = std::max(cap_round, k);
+        KMP_INIT_CUDA(alloc(&c.tc_img, kmp::tc::tc_image_bytes(d, split, rows)), "alloc center tiles");
+        KMP_INIT_CUDA(alloc(&c.tc_cnorm, (size_t)rows + 512), "alloc center norms");
+        KMP_INIT_CUDA(alloc(&c.tc_cmax, 1), "alloc cmax");
+        KMP_INIT_CUDA(alloc(&c.tc_err, 1), "alloc error word");
+        KMP_INIT_CUDA(alloc(&c.fix_rows, n), "alloc fix-up rows");
+        KMP_INIT_CUDA(alloc(&c.cand1, n), "alloc screening winners");
+        KMP_INIT_CUDA(alloc(&c.tc_ximg, kmp::tc::tc_points_image_bytes(d, split, n)), "alloc points image");
+        KMP_INIT_CUDA(alloc(&c.tc_xnorm, (size_t)((n + 127) / 128) * 128), "alloc point norms");
+        KMP_INIT_CUDA(kmp::tc::launch_prep_points(X, n, d, split, c.tc_ximg, c.tc_xnorm, c.stream), "points image");
+        KMP_INIT_CUDA(alloc(&c.fix_cnt, 1), "alloc fix-up count");
+        KMP_INIT_CUDA(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream), "memset error word");
+    }
     KMP_INIT_CUDA(cudaMemsetAsync(c.st, 0, sizeof(kmp::DevState), c.stream), "memset state");
     KMP_INIT_CUDA(kmp::launch_init_first(c), "init kernels");
 #undef KMP_INIT_CUDA
     *out = h;
+    return KMPAR_OK;
+}
+
+static kmpar_status check_timeout(kmp::Ctx &c) {
+    if (!c.tc_err) return KMPAR_OK;
+    int err = 0;
+    KMP_CUDA(&c, cudaMemcpyAsync(&err, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "read error word");
+    KMP_CUDA(&c, cudaStreamSynchronize(c.stream), "sync");
+    if (err) return fail(&c, KMPAR_ERR_TIMEOUT, "a tensor-core pass timed out waiting (code " + std::to_string(err) + ")");
     return KMPAR_OK;
 }
 
@@ -203,6 +233,8 @@ kmpar_status kmpar_round(kmpar_ctx *ctx, int32_t i, int64_t *n_added, double *ph
         KMP_CUDA(&c, cudaMemcpyAsync(&st, c.st, sizeof(st), cudaMemcpyDeviceToHost, c.stream), "read state");
         KMP_CUDA(&c, cudaStreamSynchronize(c.stream), "sync");
         if (st.overflow) return fail(&c, KMPAR_ERR_CAPACITY, "a round drew more points than its capacity");
+        kmpar_status ts = check_timeout(c);
+        if (ts != KMPAR_OK) return ts;
         if (n_added) *n_added = st.round_added[i - 1];
         if (phi) *phi = st.phi;
     }
@@ -219,6 +251,8 @@ kmpar_status kmpar_weight(kmpar_ctx *ctx, int64_t *m_out, const int32_t **cand_i
     KMP_CUDA(&c, cudaStreamSynchronize(c.stream), "sync");
     KMP_CUDA(&c, kmp::timing_drain(c), "timing");
     if (st.overflow) return fail(&c, KMPAR_ERR_CAPACITY, "a round drew more points than its capacity");
+    kmpar_status ts = check_timeout(c);
+    if (ts != KMPAR_OK) return ts;
     c.weighted = true;
     if (m_out) *m_out = st.m;
     if (cand_idx_dev) *cand_idx_dev = c.cand;
@@ -248,6 +282,7 @@ static kmpar_status ensure_lloyd_buffers(kmp::Ctx &c) {
     if ((e = alloc(&c.hist, (size_t)c.nsb * c.k)) != cudaSuccess) return cuda_fail(&c, e, "alloc hist");
     if ((e = alloc(&c.base, (size_t)c.k + 1)) != cudaSuccess) return cuda_fail(&c, e, "alloc base");
     if ((e = alloc(&c.cost_dev, 4)) != cudaSuccess) return cuda_fail(&c, e, "alloc cost");
+    if (c.precision != KMPAR_FP32 && (e = alloc(&c.dmin, c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc dmin");
     return KMPAR_OK;
 }
 
@@ -265,18 +300,30 @@ kmpar_status kmpar_lloyd(kmpar_ctx *ctx, float *centers_dev, int32_t max_iter, i
     int *changed = reinterpret_cast<int *>(c.cost_dev + 1);
     for (;;) {
         KMP_CUDA(&c, cudaMemsetAsync(changed, 0, sizeof(int), c.stream), "memset changed");
-        cudaEvent_t ev = nullptr;
-        KMP_CUDA(&c, kmp::timing_begin(c, &ev), "timing");
-        KMP_CUDA(&c, kmp::launch_assign(c.X, c.n, c.d, centers_dev, c.k, c.labels[cur],
-                                        t > 0 ? c.labels[cur ^ 1] : nullptr, changed, c.partials,
-                                        c.num_partials, &c.st->argmin_fp64, c.stream),
-                 "assign kernel");
-        KMP_CUDA(&c, kmp::timing_end(c, ev, 1), "timing");
-        KMP_CUDA(&c, kmp::launch_sum_f64(c.partials, c.num_partials, c.cost_dev, nullptr, c.stream), "cost sum");
+        if (c.precision == KMPAR_FP32) {
+            cudaEvent_t ev = nullptr;
+            KMP_CUDA(&c, kmp::timing_begin(c, &ev), "timing");
+            KMP_CUDA(&c, kmp::launch_assign(c.X, c.n, c.d, centers_dev, c.k, c.labels[cur],
+                                            t > 0 ? c.labels[cur ^ 1] : nullptr, changed, c.partials,
+                                            c.num_partials, &c.st->argmin_fp64, c.stream),
+                     "assign kernel");
+            KMP_CUDA(&c, kmp::timing_end(c, ev, 1), "timing");
+            KMP_CUDA(&c, kmp::launch_sum_f64(c.partials, c.num_partials, c.cost_dev, nullptr, c.stream), "cost sum");
+        } else {
+            KMP_CUDA(&c, kmp::launch_tc_pass(c, 0, centers_dev, c.k, c.labels[cur], t > 0 ? c.labels[cur ^ 1] : nullptr,
+                                             changed, c.dmin, 1),
+                     "tensor assign pass");
+            KMP_CUDA(&c, kmp::launch_sum_rows(c.dmin, c.n, c.partials, c.num_partials, c.cost_dev, nullptr, c.stream),
+                     "cost sum");
+        }
         struct { double cost; int changed; int pad; } hb;
         KMP_CUDA(&c, cudaMemcpyAsync(&hb, c.cost_dev, 16, cudaMemcpyDeviceToHost, c.stream), "read cost");
         KMP_CUDA(&c, cudaStreamSynchronize(c.stream), "sync");
         KMP_CUDA(&c, kmp::timing_drain(c), "timing");
+        if (c.tc_err) {
+            kmpar_status ts = check_timeout(c);
+            if (ts != KMPAR_OK) return ts;
+        }
         cost = hb.cost;
         if (cost_hist) cost_hist[t] = cost;
         if (t > 0 && hb.changed == 0) break;
@@ -297,10 +344,12 @@ kmpar_status kmpar_lloyd(kmpar_ctx *ctx, float *centers_dev, int32_t max_iter, i
 
 kmpar_status kmpar_cost(const float *X, int64_t n, int32_t d, const float *C, int32_t k, int32_t precision,
                         double *phi, void *stream) {
+    // every precision yields the same exact-FP32 cost; the CUDA-core pass computes it
+
     if (!X || !C || !phi) return fail(nullptr, KMPAR_ERR_ARG, "NULL pointer");
     if (n < 1 || n >= (int64_t)INT32_MAX || d < 1 || d > 4096 || k < 1)
         return fail(nullptr, KMPAR_ERR_ARG, "size out of range");
-    if (!precision_supported(precision)) return fail(nullptr, KMPAR_ERR_UNSUPPORTED, "precision not built");
+    if (!precision_supported(precision, d)) return fail(nullptr, KMPAR_ERR_UNSUPPORTED, "precision not built");
     cudaStream_t s = (cudaStream_t)stream;
     const int np = kmp::assign_num_partials(n, d);
     double *buf = nullptr;   // np partials, the sum, one counter
@@ -345,6 +394,8 @@ kmpar_status kmpar_get_stats(kmpar_ctx *ctx, kmpar_stats *out) {
     out->recluster_near = (int64_t)st.recluster_near;
     out->capacity_overflow = st.overflow;
     out->recluster_warn = st.warn;
+    out->screen_rows = (int64_t)st.screen_rows;
+    out->screen_fallback = (int64_t)st.screen_fallback;
     KMP_CUDA(&c, kmp::timing_drain(c), "timing");
     for (int i = 0; i < 2; ++i) {
         out->kernel_ms[i] = c.kernel_ms[i];

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/kmpar.h"
+#include "nearest_tc.cuh"
 
 namespace kmp {
 
@@ -35,6 +36,7 @@ struct DevState {
     double phi_hist[kMaxRounds + 1];
     int32_t round_added[kMaxRounds];
     unsigned long long sample_near, sample_refined, argmin_fp64, argmin_wide, recluster_near;
+    unsigned long long screen_rows, screen_fallback;   // tensor passes: rows screened, rows sent to fix-up
 };
 
 struct Ctx {
@@ -71,12 +73,17 @@ struct Ctx {
     int32_t *base = nullptr;      // k + 1
     int nsb = 0;
     double *cost_dev = nullptr;   // one FP64
-    // tensor-core screening copies (BF16 modes)
-    void *Xb = nullptr;           // n_pad x kp bf16
-    void *Cb = nullptr;           // screening copy of centers
-    float *xnorm = nullptr;
-    int kp = 0;
-    int64_t n_pad = 0;
+    // tensor-core screening (BF16 modes)
+    uint8_t *tc_img = nullptr;    // swizzled BF16 center tiles
+    uint8_t *tc_ximg = nullptr;   // swizzled BF16 image of X (built once per context)
+    float *tc_xnorm = nullptr;    // ||x||^2 per point
+    float *tc_cnorm = nullptr;    // ||c|| per padded center row
+    unsigned int *tc_cmax = nullptr;
+    int *tc_err = nullptr;        // first timeout code of a tensor pass
+    int32_t *cand1 = nullptr;     // per row: certain nearest center of the last tensor pass, or -1
+    int32_t *fix_rows = nullptr;  // rows left to the exact CUDA-core pass
+    int *fix_cnt = nullptr;
+    float *dmin = nullptr;        // Lloyd: exact d^2 of each point's chosen center
     // CUDA-event timing of the distance passes (0 = rounds, 1 = Lloyd assign)
     bool timing = false;
     struct Pending { cudaEvent_t a, b; int cls; };
@@ -192,6 +199,11 @@ cudaError_t launch_assign(const float *X, int64_t n, int d, const float *C, int 
                           unsigned long long *fp64_cnt, cudaStream_t s);
 int assign_num_partials(int64_t n, int d);
 cudaError_t launch_centroids(Ctx &c, const int32_t *labels, float *centers);
+cudaError_t count_fixups(Ctx &c);   // adds the current fix-up count to the screening stats
+cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
+                           int *changed, float *dmin, int timing_cls);
+cudaError_t launch_sum_rows(const float *v, int64_t n, double *partials, int max_parts, double *out, double *copy,
+                            cudaStream_t s);
 cudaError_t launch_uniforms(int64_t count, uint32_t round, uint32_t tag, uint64_t seed, double *out,
                             cudaStream_t s);
 cudaError_t launch_sum_f64(const double *parts, int nparts, double *out, double *copy, cudaStream_t s);

@@ -36,8 +36,11 @@ struct NearestParams {
     int32_t *labels;       // ASSIGN: out (nullable)
     const int32_t *prev;   // ASSIGN: previous labels (nullable)
     int *changed;          // ASSIGN: +number of labels != prev (nullable)
-    double *partials;      // per-block FP64 sum of the stored distances
+    double *partials;      // per-block FP64 sum of the stored distances (nullable)
     unsigned long long *fp64_cnt, *wide_cnt;
+    const int32_t *rows;   // nullable: process only these rows (the tensor pass's fix-up list)
+    const int *rows_cnt;   // number of entries in rows
+    float *dmin;           // ASSIGN: per-row exact d^2 of the chosen center (nullable)
 };
 
 // lexicographic (value, index) improvement
@@ -54,8 +57,14 @@ __global__ void __launch_bounds__(kNearThreads) nearest_kernel(NearestParams p) 
     __shared__ int redi[32];
 
     const int tid = threadIdx.x;
-    const int64_t pt = (int64_t)blockIdx.x * kNearThreads + tid;
-    const bool valid = pt < p.n;
+    int64_t pt = (int64_t)blockIdx.x * kNearThreads + tid;
+    bool valid = pt < p.n;
+    if (p.rows) {
+        const int nrows = *p.rows_cnt;
+        if ((int64_t)blockIdx.x * kNearThreads >= nrows) return;   // uniform per block
+        valid = pt < nrows;
+        pt = valid ? p.rows[pt] : 0;
+    }
     const int d = p.d;
     const float *xrow = p.X + (valid ? pt : 0) * (int64_t)d;
 
@@ -127,6 +136,7 @@ __global__ void __launch_bounds__(kNearThreads) nearest_kernel(NearestParams p) 
                 atomicAdd(p.fp64_cnt, 1ull);
             }
             if (p.labels) p.labels[pt] = lab;
+            if (p.dmin) p.dmin[pt] = stored;
             if (p.prev) chg = (p.prev[pt] != lab);
         } else if constexpr (MODE == MODE_FIRST) {
             stored = (i1 >= 0) ? b1 : __int_as_float(0x7f800000);
@@ -166,7 +176,7 @@ __global__ void __launch_bounds__(kNearThreads) nearest_kernel(NearestParams p) 
     }
 
     const double s = block_sum_f64(valid ? (double)stored : 0.0, red);
-    if (tid == 0) p.partials[blockIdx.x] = s;
+    if (tid == 0 && p.partials) p.partials[blockIdx.x] = s;
     if constexpr (MODE == MODE_ASSIGN) {
         if (p.changed) {
             int c = warp_sum_i32(chg);
@@ -184,7 +194,7 @@ __global__ void __launch_bounds__(kNearThreads) nearest_kernel(NearestParams p) 
 
 template <int MODE>
 static cudaError_t launch_nearest_mode(const NearestParams &p, cudaStream_t s) {
-    const int grid = (int)((p.n + kNearThreads - 1) / kNearThreads);
+    const int grid = (int)((p.n + kNearThreads - 1) / kNearThreads);   // p.n = rows capacity for row lists
     const int d = p.d;
 #define KMP_NEAREST_CASE(DPV)                                              \
     if (d <= DPV) {                                                         \
@@ -369,9 +379,18 @@ cudaError_t launch_round(Ctx &c, int round) {
     return launch_round_distance(c, round);
 }
 
+cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
+                           int *changed, float *dmin, int timing_cls);
+cudaError_t launch_sum_rows(const float *v, int64_t n, double *partials, int max_parts, double *out, double *copy,
+                            cudaStream_t s);
+
 // Alg. 2 step 5: D^2/idx against the batch just appended, then phi
 cudaError_t launch_round_distance(Ctx &c, int round) {
     cudaError_t e;
+    if (c.precision != KMPAR_FP32) {
+        if ((e = launch_tc_pass(c, 1, c.C, 0, nullptr, nullptr, nullptr, nullptr, 0)) != cudaSuccess) return e;
+        return launch_sum_rows(c.D2, c.n, c.partials, c.num_partials, &c.st->phi, &c.st->phi_hist[round], c.stream);
+    }
     cudaEvent_t ev = nullptr;
     if ((e = timing_begin(c, &ev)) != cudaSuccess) return e;
     NearestParams p{};
@@ -410,8 +429,190 @@ cudaError_t launch_uniforms(int64_t count, uint32_t round, uint32_t tag, uint64_
 }  // namespace kmp
 
 namespace kmp {
+cudaError_t configure_refine_kernels();
+
 cudaError_t configure_round_kernels(int max_sort_pow2) {
-    return cudaFuncSetAttribute(sort_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                max_sort_pow2 * (int)sizeof(int32_t));
+    cudaError_t e = cudaFuncSetAttribute(sort_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         max_sort_pow2 * (int)sizeof(int32_t));
+    if (e != cudaSuccess) return e;
+    return configure_refine_kernels();
 }
+}  // namespace kmp
+
+// ------------------------------------------------------------------ tensor-core passes
+namespace kmp {
+
+// deterministic FP64 sum of a float array: fixed per-block ranges, fixed trees
+__global__ void __launch_bounds__(256) sum_rows_kernel(const float *__restrict__ v, int64_t n, int64_t per_block,
+                                                      double *partials) {
+    __shared__ double sh[32];
+    const int64_t b0 = (int64_t)blockIdx.x * per_block;
+    const int64_t b1 = min(n, b0 + per_block);
+    double acc = 0.0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) acc += (double)v[i];
+    const double s = block_sum_f64(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+cudaError_t launch_sum_rows(const float *v, int64_t n, double *partials, int max_parts, double *out, double *copy,
+                            cudaStream_t s) {
+    int64_t per = 4096;
+    int64_t nb = (n + per - 1) / per;
+    if (nb > max_parts) {
+        per = (n + max_parts - 1) / max_parts;
+        nb = (n + per - 1) / per;
+    }
+    if (nb < 1) nb = 1;
+    sum_rows_kernel<<<(int)nb, 256, 0, s>>>(v, n, per, partials);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_sum_f64(partials, (int)nb, out, copy, s);
+}
+
+// fix-up rows of a tensor pass, finished exactly on CUDA cores
+cudaError_t launch_fixup(const Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
+                         int *changed, float *dmin) {
+    NearestParams p{};
+    p.X = c.X; p.n = c.n; p.d = c.d; p.C = C; p.st = c.st;
+    p.rows = c.fix_rows; p.rows_cnt = c.fix_cnt;
+    p.fp64_cnt = &c.st->argmin_fp64; p.wide_cnt = &c.st->argmin_wide;
+    if (mode_round) {
+        p.D2 = c.D2; p.idx = c.idx;
+        return launch_nearest_mode<MODE_ROUND>(p, c.stream);
+    }
+    p.c_begin = 0; p.c_cnt = k; p.labels = labels; p.prev = prev; p.changed = changed; p.dmin = dmin;
+    return launch_nearest_mode<MODE_ASSIGN>(p, c.stream);
+}
+
+__global__ void count_fixups_kernel(const int *fix_cnt, int64_t n, DevState *st) {
+    st->screen_fallback += (unsigned long long)*fix_cnt;
+    st->screen_rows += (unsigned long long)n;
+}
+
+cudaError_t count_fixups(Ctx &c) {
+    count_fixups_kernel<<<1, 1, 0, c.stream>>>(c.fix_cnt, c.n, c.st);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// Exact FP32 distance and decision for the rows whose nearest center the tensor
+// screening made certain (cand1 >= 0).  One CTA per 128 rows: the row tile is
+// staged in shared memory with coalesced loads (odd row stride, no bank
+// conflicts); each thread walks its center row in chunks of 8 independent loads.
+template <int MODE>
+__global__ void __launch_bounds__(128) refine_kernel(const float *__restrict__ X, int64_t n, int d,
+                                                    const float *__restrict__ C, const int32_t *__restrict__ cand1,
+                                                    float *D2, int32_t *idx, int32_t *labels, const int32_t *prev,
+                                                    int *changed, float *dmin, unsigned long long *fp64_cnt) {
+    extern __shared__ float xt[];
+    __shared__ int redi[4];
+    const int ds = d | 1;
+    const int64_t r0 = (int64_t)blockIdx.x * 128;
+    const int nr = (int)min((int64_t)128, n - r0);
+    const float *src = X + r0 * d;
+    for (int i = threadIdx.x; i < nr * d; i += 128) {
+        const int rr = i / d;
+        xt[rr * ds + (i - rr * d)] = __ldg(src + i);
+    }
+    __syncthreads();
+    int chg = 0;
+    const int t = threadIdx.x;
+    if (t < nr) {
+        const int64_t R = r0 + t;
+        const int j = cand1[R];
+        if (j >= 0) {
+            const float *xs = xt + t * ds;
+            const float *cr = C + (int64_t)j * d;
+            float b1 = 0.f;
+            int q = 0;
+            for (; q + 8 <= d; q += 8) {
+                float cv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) cv[u] = __ldg(cr + q + u);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float tq = __fsub_rn(xs[q + u], cv[u]);
+                    b1 = __fmaf_rn(tq, tq, b1);
+                }
+            }
+            for (; q < d; ++q) {
+                const float tq = __fsub_rn(xs[q], __ldg(cr + q));
+                b1 = __fmaf_rn(tq, tq, b1);
+            }
+            if (MODE == MODE_ROUND) {
+                const float old = D2[R];
+                const int oi = idx[R];
+                const float W = fp32_tie_window(d);
+                const float m32 = fminf(old, b1);
+                const float lim = m32 + W * m32;
+                if (old <= lim && b1 <= lim) {
+                    const float *xg = X + R * d;
+                    const double dold = dist2_fp64(xg, C + (int64_t)oi * d, d);
+                    const double dnew = dist2_fp64(xg, cr, d);
+                    atomicAdd(fp64_cnt, 1ull);
+                    if (dnew < dold || (dnew == dold && j < oi)) { D2[R] = b1; idx[R] = j; }
+                } else if (b1 < old) {
+                    D2[R] = b1;
+                    idx[R] = j;
+                }
+            } else {
+                if (labels) labels[R] = j;
+                dmin[R] = b1;
+                if (prev) chg = prev[R] != j;
+            }
+        }
+    }
+    if (MODE == MODE_ASSIGN && changed) {
+        const int c = warp_sum_i32(chg);
+        if ((threadIdx.x & 31) == 0) redi[threadIdx.x >> 5] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int tot = redi[0] + redi[1] + redi[2] + redi[3];
+            if (tot) atomicAdd(changed, tot);
+        }
+    }
+}
+
+cudaError_t configure_refine_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(refine_kernel<MODE_ROUND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         128 * 129 * 4);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(refine_kernel<MODE_ASSIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 129 * 4);
+}
+
+cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
+                           int *changed, float *dmin, int timing_cls) {
+    cudaError_t e;
+    const int split = c.precision == KMPAR_BF16X3 ? 1 : 0;
+    if ((e = tc::launch_prep_centers(C, c.d, split, c.st, k, mode_round, mode_round ? c.cap_round : k, c.tc_img,
+                                     c.tc_cnorm, c.tc_cmax, c.stream)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(c.fix_cnt, 0, sizeof(int), c.stream)) != cudaSuccess) return e;
+    // rows the screening does not reach (e.g. an empty batch) must not see a stale winner
+    if ((e = cudaMemsetAsync(c.cand1, 0xFF, sizeof(int32_t) * (size_t)c.n, c.stream)) != cudaSuccess) return e;
+    tc::TcParams p{};
+    p.X = c.X; p.n = c.n; p.d = c.d; p.split = split;
+    p.ximg = c.tc_ximg; p.xnorm = c.tc_xnorm;
+    p.Cf = C; p.cnt = k; p.st = c.st; p.bimg = c.tc_img; p.cnorm = c.tc_cnorm; p.cmax_bits = c.tc_cmax;
+    p.cand1 = c.cand1; p.fix_rows = c.fix_rows; p.fix_cnt = c.fix_cnt; p.fp64_cnt = &c.st->argmin_fp64;
+    p.err = c.tc_err;
+    cudaEvent_t ev = nullptr;
+    if ((e = timing_begin(c, &ev)) != cudaSuccess) return e;
+    if ((e = tc::launch_nearest_tc(p, mode_round, c.num_sms, c.stream)) != cudaSuccess) return e;
+    if ((e = timing_end(c, ev, timing_cls)) != cudaSuccess) return e;
+    const int grid = (int)((c.n + 127) / 128);
+    const size_t sm = (size_t)128 * (c.d | 1) * sizeof(float);
+    if (mode_round)
+        refine_kernel<MODE_ROUND><<<grid, 128, sm, c.stream>>>(c.X, c.n, c.d, C, c.cand1, c.D2, c.idx, nullptr,
+                                                               nullptr, nullptr, nullptr, &c.st->argmin_fp64);
+    else
+        refine_kernel<MODE_ASSIGN><<<grid, 128, sm, c.stream>>>(c.X, c.n, c.d, C, c.cand1, nullptr, nullptr, labels,
+                                                                prev, changed, dmin, &c.st->argmin_fp64);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = count_fixups(c)) != cudaSuccess) return e;
+    return launch_fixup(c, mode_round, C, k, labels, prev, changed, dmin);
+}
+
 }  // namespace kmp

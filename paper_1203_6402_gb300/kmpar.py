@@ -35,7 +35,8 @@ class kmpar_stats(ctypes.Structure):
                 ("argmin_fp64", ctypes.c_int64), ("argmin_wide", ctypes.c_int64),
                 ("recluster_near", ctypes.c_int64),
                 ("capacity_overflow", ctypes.c_int32), ("recluster_warn", ctypes.c_int32),
-                ("kernel_ms", ctypes.c_double * 2), ("kernel_launches", ctypes.c_int64 * 2)]
+                ("kernel_ms", ctypes.c_double * 2), ("kernel_launches", ctypes.c_int64 * 2),
+                ("screen_rows", ctypes.c_int64), ("screen_fallback", ctypes.c_int64)]
 
     def to_dict(self) -> dict:
         r = self.rounds_done
@@ -45,7 +46,8 @@ class kmpar_stats(ctypes.Structure):
                     argmin_fp64=self.argmin_fp64, argmin_wide=self.argmin_wide,
                     recluster_near=self.recluster_near, capacity_overflow=self.capacity_overflow,
                     recluster_warn=self.recluster_warn, kernel_ms=list(self.kernel_ms),
-                    kernel_launches=list(self.kernel_launches))
+                    kernel_launches=list(self.kernel_launches), screen_rows=self.screen_rows,
+                    screen_fallback=self.screen_fallback)
 
 
 class KmparError(RuntimeError):

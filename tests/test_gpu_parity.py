@@ -144,6 +144,61 @@ def test_parity_fp32(km, orc, name, mk, k, ell, rounds, seed):
     assert diag["parted"] is None, diag
 
 
+TC_CASES = [c for c in CASES if c[0] != "d130_generic"] + [
+    ("gmm_d42_multi_tile", lambda: datagen.gauss_mixture(9000, 42, 40, 10.0, seed=13), 300, 600.0, 3, 9),
+    ("kdd_ragged_3001", lambda: datagen.kdd_like(3001, seed=14), 40, 80.0, 4, 10),
+]
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("name,mk,k,ell,rounds,seed", TC_CASES, ids=[c[0] for c in TC_CASES])
+def test_parity_tensor_screening(km, orc, name, mk, k, ell, rounds, seed, precision):
+    """tcgen05 screening + exact refine: same decisions as the oracle (and the FP32 path)."""
+    X = mk()
+    if precision == "bf16x3" and 3 * X.shape[1] + 4 > 192:
+        # split mode carries 3d + 4 K columns; at most three 64-column atoms are built
+        with pytest.raises(km.KmparError) as e:
+            km.KMeansPar(_dev(X), k, ell, rounds, seed, precision=precision)
+        assert e.value.status == km.KMPAR_ERR_UNSUPPORTED
+        return
+    diag = run_and_compare(km, orc, X, k, ell, rounds, seed, precision=precision)
+    assert diag["parted"] is None, diag
+    st = diag["stats"]
+    assert st["screen_rows"] > 0
+    if precision == "bf16x3" and name.startswith("gmm"):
+        # well-separated data: nearly every row is decided by the screening alone
+        assert st["screen_fallback"] <= 0.05 * st["screen_rows"], st
+
+
+def test_tensor_paths_match_fp32_path(km):
+    X = datagen.kdd_like(20000, seed=15)
+    Xd = _dev(X)
+    res = {}
+    for prec in ("fp32", "bf16x3", "bf16"):
+        g = km.KMeansPar(Xd, 64, 128.0, 5, 3, precision=prec)
+        for r in range(1, 6):
+            g.round(r)
+        cand, w = g.candidates()
+        C, _ = g.recluster()
+        out = g.lloyd(C, 20)
+        res[prec] = (cand.cpu().numpy(), w.cpu().numpy(), C.cpu().numpy(), out["labels"].cpu().numpy(),
+                     out["final_cost"], g.stats())
+        g.close()
+    for prec in ("bf16x3", "bf16"):
+        for a, b in zip(res["fp32"][:4], res[prec][:4]):
+            assert np.array_equal(a, b), prec
+        assert res["fp32"][4] == res[prec][4]
+
+
+def test_tensor_precision_rejects_large_d(km):
+    # BF16 carries d + 2 K columns, split BF16 3d + 2; three 64-column atoms are built
+    X = _dev(datagen.uniform_box(200, 200, seed=1))
+    for prec in ("bf16", "bf16x3"):
+        with pytest.raises(km.KmparError) as e:
+            km.KMeansPar(X, 4, 8.0, 2, 0, precision=prec)
+        assert e.value.status == km.KMPAR_ERR_UNSUPPORTED
+
+
 def test_philox_matches_oracle(km, orc):
     for rnd, tag, seed in [(0, 1, 0), (3, 2, 12345), (0, 3, (1 << 40) + 7)]:
         out = torch.empty(20000, dtype=torch.float64, device="cuda")

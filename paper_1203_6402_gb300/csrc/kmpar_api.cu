@@ -56,7 +56,8 @@ cudaError_t alloc(T **p, size_t count) {
 void free_ctx(kmp::Ctx &c) {
     void *bufs[] = {c.st, c.D2, c.idx, c.drawn, c.cand, c.C, c.w, c.rD2, c.chosen, c.partials,
                     c.labels[0], c.labels[1], c.perm, c.hist, c.base, c.cost_dev, c.tc_img, c.tc_cnorm,
-                    c.tc_cmax, c.tc_err, c.cand1, c.fix_rows, c.fix_cnt, c.dmin, c.tc_ximg, c.tc_xnorm};
+                    c.tc_cmax, c.tc_err, c.cand1, c.fix_rows, c.fix_cnt, c.dmin, c.tc_ximg, c.tc_xnorm,
+                    c.piece, c.psum, c.rc_cmass, c.rc_sync, c.rc_err, c.chunk};
     for (void *b : bufs)
         if (b) cudaFree(b);
 }
@@ -163,7 +164,8 @@ kmpar_status kmpar_init(kmpar_ctx **out, const float *X, int64_t n, int32_t d, i
     c.precision = precision; c.stream = (cudaStream_t)stream;
     c.cap_round = cap_round;
     c.cap_total = (int)cap_total64;
-    c.nsb = (int)((n + kmp::kSortBlock - 1) / kmp::kSortBlock);
+    c.sort_block = kmp::sort_block_size(n, k);
+    c.nsb = (int)((n + c.sort_block - 1) / c.sort_block);
     c.num_partials = kmp::assign_num_partials(n, d);
 
     auto bail = [&](kmpar_status s) {
@@ -188,6 +190,9 @@ kmpar_status kmpar_init(kmpar_ctx **out, const float *X, int64_t n, int32_t d, i
     KMP_INIT_CUDA(alloc(&c.w, c.cap_total), "alloc weights");
     KMP_INIT_CUDA(alloc(&c.rD2, c.cap_total), "alloc recluster D2");
     KMP_INIT_CUDA(alloc(&c.chosen, k), "alloc chosen");
+    KMP_INIT_CUDA(alloc(&c.rc_cmass, 2 * (size_t)((c.cap_total + 31) / 32)), "alloc recluster masses");
+    KMP_INIT_CUDA(cudaMalloc(&c.rc_sync, kmp::recluster_sync_bytes()), "alloc recluster sync");
+    KMP_INIT_CUDA(alloc(&c.rc_err, 1), "alloc recluster error");
     KMP_INIT_CUDA(alloc(&c.partials, c.num_partials), "alloc partials");
     if (precision != KMPAR_FP32) {
         const int split = precision == KMPAR_BF16X3 ? 1 : 0;
@@ -266,10 +271,13 @@ kmpar_status kmpar_recluster(kmpar_ctx *ctx, float *centers_dev) {
     if (!centers_dev) return fail(&c, KMPAR_ERR_ARG, "centers_dev is NULL");
     if (!c.weighted) return fail(&c, KMPAR_ERR_STATE, "recluster before weight");
     KMP_CUDA(&c, cudaMemsetAsync(&c.st->warn, 0, sizeof(int32_t), c.stream), "memset warn");
+    KMP_CUDA(&c, cudaMemsetAsync(c.rc_err, 0, sizeof(int), c.stream), "memset recluster error");
     KMP_CUDA(&c, kmp::launch_recluster(c, centers_dev), "recluster kernel");
-    int32_t warn = 0;
+    int32_t warn = 0, rerr = 0;
     KMP_CUDA(&c, cudaMemcpyAsync(&warn, &c.st->warn, sizeof(warn), cudaMemcpyDeviceToHost, c.stream), "read warn");
+    KMP_CUDA(&c, cudaMemcpyAsync(&rerr, c.rc_err, sizeof(rerr), cudaMemcpyDeviceToHost, c.stream), "read error");
     KMP_CUDA(&c, cudaStreamSynchronize(c.stream), "sync");
+    if (rerr) return fail(&c, KMPAR_ERR_TIMEOUT, "recluster grid barrier timed out (code " + std::to_string(rerr) + ")");
     return warn ? KMPAR_WARN_FEW_CANDIDATES : KMPAR_OK;
 }
 
@@ -281,6 +289,11 @@ static kmpar_status ensure_lloyd_buffers(kmp::Ctx &c) {
     if ((e = alloc(&c.perm, c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc perm");
     if ((e = alloc(&c.hist, (size_t)c.nsb * c.k)) != cudaSuccess) return cuda_fail(&c, e, "alloc hist");
     if ((e = alloc(&c.base, (size_t)c.k + 1)) != cudaSuccess) return cuda_fail(&c, e, "alloc base");
+    if ((e = alloc(&c.piece, (size_t)c.k + 1)) != cudaSuccess) return cuda_fail(&c, e, "alloc pieces");
+    if ((e = alloc(&c.chunk, (size_t)kmp::scan_chunks(c.nsb) * c.k)) != cudaSuccess)
+        return cuda_fail(&c, e, "alloc scan chunks");
+    if ((e = alloc(&c.psum, (size_t)kmp::max_pieces(c.n, c.k) * c.d)) != cudaSuccess)
+        return cuda_fail(&c, e, "alloc piece sums");
     if ((e = alloc(&c.cost_dev, 4)) != cudaSuccess) return cuda_fail(&c, e, "alloc cost");
     if (c.precision != KMPAR_FP32 && (e = alloc(&c.dmin, c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc dmin");
     return KMPAR_OK;

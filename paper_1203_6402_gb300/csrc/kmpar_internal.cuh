@@ -19,7 +19,6 @@ constexpr uint32_t TAG_SAMPLE = 2u;
 constexpr uint32_t TAG_RECLUSTER = 3u;
 
 constexpr int kMaxRoundCap = 32768;   // single-CTA sort of one round's draws
-constexpr int kSortBlock = 4096;      // points per block of the Lloyd counting sort
 constexpr int kMaxRounds = 64;
 
 // Device-resident state of one context (one allocation, read by kernels).
@@ -63,6 +62,9 @@ struct Ctx {
     float *C = nullptr;           // cap_total x d candidate rows
     long long *w = nullptr;       // cap_total
     float *rD2 = nullptr;         // recluster D^2 (cap_total)
+    double *rc_cmass = nullptr;   // recluster chunk masses, 2 x ceil(cap_total / 32)
+    void *rc_sync = nullptr;      // recluster grid barrier / pick flag
+    int *rc_err = nullptr;        // recluster timeout flag
     int32_t *chosen = nullptr;    // k
     double *partials = nullptr;   // per-block FP64 partial sums
     int num_partials = 0;
@@ -71,7 +73,10 @@ struct Ctx {
     int32_t *perm = nullptr;
     int32_t *hist = nullptr;      // nsb x k
     int32_t *base = nullptr;      // k + 1
-    int nsb = 0;
+    int32_t *piece = nullptr;     // k + 1: first piece of each cluster
+    int32_t *chunk = nullptr;     // column-scan chunk totals
+    double *psum = nullptr;       // FP64 piece sums
+    int nsb = 0, sort_block = 0;
     double *cost_dev = nullptr;   // one FP64
     // tensor-core screening (BF16 modes)
     uint8_t *tc_img = nullptr;    // swizzled BF16 center tiles
@@ -186,6 +191,33 @@ __device__ __forceinline__ double block_sum_f64(double v, double *sh /*32*/) {
     return r;
 }
 
+// Copies nrows rows of d floats (contiguous in global memory) into shared memory
+// with row stride ds, using nthr cooperating threads (index tid).  Each thread
+// issues eight independent loads before its stores, so a copy costs a few memory
+// latencies rather than one per element.  Row = f / d through a multiply-high by
+// ceil(2^32 / d), exact while f * d < 2^32.
+__device__ __forceinline__ void stage_rows(float *dst, int ds, const float *__restrict__ src, int nrows, int d,
+                                           int tid, int nthr) {
+    const uint32_t magic = 0xFFFFFFFFu / (uint32_t)d + 1u;
+    const int total = nrows * d;
+    for (int f0 = tid; f0 < total; f0 += 8 * nthr) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int f = f0 + u * nthr;
+            if (f < total) v[u] = __ldg(src + f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int f = f0 + u * nthr;
+            if (f < total) {
+                const int r = (int)__umulhi((uint32_t)f, magic);
+                dst[r * ds + (f - r * d)] = v[u];
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 // (each returns cudaGetLastError() of its launch)
 cudaError_t launch_init_first(Ctx &c);
@@ -194,11 +226,15 @@ cudaError_t launch_round_distance(Ctx &c, int round);
 cudaError_t launch_phi_finalize(Ctx &c, int nparts, double *out, double *hist_slot);
 cudaError_t launch_weights(Ctx &c);
 cudaError_t launch_recluster(Ctx &c, float *centers);
+size_t recluster_sync_bytes();
 cudaError_t launch_assign(const float *X, int64_t n, int d, const float *C, int k, int32_t *labels,
                           const int32_t *prev, int *changed, double *partials, int nparts,
                           unsigned long long *fp64_cnt, cudaStream_t s);
 int assign_num_partials(int64_t n, int d);
 cudaError_t launch_centroids(Ctx &c, const int32_t *labels, float *centers);
+int sort_block_size(int64_t n, int k);
+int64_t max_pieces(int64_t n, int k);
+int64_t scan_chunks(int nsb);
 cudaError_t count_fixups(Ctx &c);   // adds the current fix-up count to the screening stats
 cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
                            int *changed, float *dmin, int timing_cls);

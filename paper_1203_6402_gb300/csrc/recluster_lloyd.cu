@@ -30,177 +30,378 @@ cudaError_t launch_weights(Ctx &c) {
 }
 
 // ------------------------------------------------------------------ step 8
-// One CTA of 1024 threads; thread t owns the contiguous candidate range
-// [t q, (t+1) q).  Per draw: FP64 masses, a fixed-order block scan, the target
-// u * total, the first candidate whose running prefix exceeds it, and the D^2
-// update of every candidate against the drawn one (exact FP32 difference form).
-constexpr int kRcThreads = 1024;
+// Weighted k-means++ (Alg. 1 with multiplicities w): k sequential draws over the m
+// candidates.  One cooperative launch; the candidates are cut into fixed chunks of
+// 32 (one warp each, FP64 shuffle scans), so every sum is independent of the grid
+// size.  Per draw t:
+//   A  each warp: masses e_j = w_j (t = 0) or w_j D^2_j, inclusive warp scan,
+//      chunk total -> cmass[t & 1][chunk]                    ... grid barrier
+//   B  every CTA: the same fixed-order scan of the chunk totals -> total, target
+//      u_t * total, the first chunk whose running prefix exceeds it; the warp that
+//      owns that chunk picks the first candidate crossing the target and publishes
+//      it (release flag); the other CTAs wait for the flag (bounded)
+//   C  every warp: D^2_j <- min(D^2_j, ||c_j - c_pick||^2) (exact FP32 form)
+// All waits are bounded: a timeout raises st->rc_err and every CTA returns.
+constexpr int kRcThreads = 128;   // 4 warps per CTA
+constexpr unsigned long long kRcWait = 4000000000ull;
 
-__device__ __forceinline__ double block_incl_scan_f64(double v, double *buf) {
-    const int t = threadIdx.x;
-    buf[t] = v;
+struct RcSync {
+    unsigned int count, gen;   // grid barrier
+    unsigned int pick_flag;    // t + 1 once pick[t] is published
+    int pick[2];
+    int abort;
+};
+
+__device__ __forceinline__ bool rc_grid_sync(RcSync *s, unsigned int nblocks, int *err) {
+    __shared__ int ok;
     __syncthreads();
-    for (int off = 1; off < kRcThreads; off <<= 1) {
-        const double a = t >= off ? buf[t - off] : 0.0;
-        __syncthreads();
-        if (t >= off) buf[t] = buf[t] + a;
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned int *gen = &s->gen;
+        const unsigned int g = *gen;
+        __threadfence();
+        if (atomicAdd(&s->count, 1u) == nblocks - 1) {
+            s->count = 0;
+            __threadfence();
+            atomicExch(&s->gen, g + 1);
+        } else {
+            const unsigned long long t0 = clock64();
+            while (*gen == g) {
+                if (*(volatile int *)&s->abort) { ok = 0; break; }
+                if (clock64() - t0 > kRcWait) {
+                    atomicCAS(err, 0, 1);
+                    atomicExch(&s->abort, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
     }
-    return buf[t];
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ __forceinline__ double warp_incl_scan_f64(double v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
 }
 
 __global__ void __launch_bounds__(kRcThreads) recluster_kernel(const float *__restrict__ C,
-                                                             const long long *__restrict__ w, DevState *st,
-                                                             int d, int k, uint64_t seed, float *rD2,
-                                                             int32_t *chosen, float *centers) {
-    __shared__ double buf[kRcThreads];
-    __shared__ int s_min[32], s_max[32];
-    __shared__ int s_pick;
-    extern __shared__ float cnew[];
+                                                             const long long *__restrict__ w, DevState *st, int d,
+                                                             int k, uint64_t seed, float *rD2, int32_t *chosen,
+                                                             float *centers, double *cmass, RcSync *sync, int *err) {
+    extern __shared__ float cnew[];   // d floats
+    __shared__ double sbuf[kRcThreads];
+    __shared__ int s_min[kRcThreads / 32], s_pick, s_chunk, s_go;
+    __shared__ double s_pre;
     const int m = st->m;
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int q = (m + kRcThreads - 1) / kRcThreads;
-    const int lo = min(m, t * q), hi = min(m, lo + q);
+    const int nchunk = (m + 31) / 32;
+    const int G = gridDim.x;
+    const int cpc = (nchunk + G - 1) / G;                 // chunks per CTA (contiguous)
+    const int c0 = min(nchunk, (int)blockIdx.x * cpc), c1 = min(nchunk, c0 + cpc);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int t_id = threadIdx.x;
 
     for (int step = 0; step < k; ++step) {
+        double *cm = cmass + (size_t)(step & 1) * nchunk;
+        // ---- A: chunk masses
+        for (int ch = c0 + wid; ch < c1; ch += kRcThreads / 32) {
+            const int j = ch * 32 + lane;
+            double e = 0.0;
+            if (j < m) e = step == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)rD2[j]);
+            const double incl = warp_incl_scan_f64(e, lane);
+            if (lane == 31) cm[ch] = incl;
+        }
+        if (!rc_grid_sync(sync, G, err)) return;
+        // ---- B: fixed-order scan of the chunk totals (identical in every CTA)
+        const int q = (nchunk + kRcThreads - 1) / kRcThreads;
+        const int lo = min(nchunk, t_id * q), hi = min(nchunk, lo + q);
         double local = 0.0;
-        for (int j = lo; j < hi; ++j)
-            local += step == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)rD2[j]);
-        const double incl = block_incl_scan_f64(local, buf);
-        const double excl = t > 0 ? buf[t - 1] : 0.0;
-        const double total = buf[kRcThreads - 1];
+        for (int i = lo; i < hi; ++i) local += __ldcg(cm + i);
+        sbuf[t_id] = local;
+        __syncthreads();
+        for (int off = 1; off < kRcThreads; off <<= 1) {
+            const double a = t_id >= off ? sbuf[t_id - off] : 0.0;
+            __syncthreads();
+            if (t_id >= off) sbuf[t_id] += a;
+            __syncthreads();
+        }
+        const double excl = t_id > 0 ? sbuf[t_id - 1] : 0.0;
+        const double total = sbuf[kRcThreads - 1];
         __syncthreads();
         if (!(total > 0.0)) {
-            // positive mass exhausted: remaining draws repeat the first center
-            for (int s = step + t; s < k; s += kRcThreads) chosen[s] = step > 0 ? chosen[0] : 0;
-            if (t == 0) st->warn = 1;
-            __syncthreads();
-            for (int s = step; s < k; ++s) {
+            // positive mass exhausted: the remaining draws repeat the first center
+            if (blockIdx.x == 0) {
+                for (int s = step + t_id; s < k; s += kRcThreads) chosen[s] = step > 0 ? chosen[0] : 0;
+                if (t_id == 0) st->warn = 1;
+                __syncthreads();
                 const int src = step > 0 ? chosen[0] : 0;
-                for (int qq = t; qq < d; qq += kRcThreads) centers[(int64_t)s * d + qq] = C[(int64_t)src * d + qq];
+                for (int s = step; s < k; ++s)
+                    for (int qq = t_id; qq < d; qq += kRcThreads) centers[(int64_t)s * d + qq] = C[(int64_t)src * d + qq];
             }
             return;
         }
-        (void)incl;
         const double u = uniform53((uint64_t)step, 0, TAG_RECLUSTER, seed);
         const double target = __dmul_rn(u, total);
-        int mine = INT_MAX, lastpos = -1;
-        bool nt = false;
-        double run = excl;
-        for (int j = lo; j < hi; ++j) {
-            const double e = step == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)rD2[j]);
-            const double before = run;
-            run = run + e;
-            if (e > 0.0) lastpos = j;
-            if (mine == INT_MAX && run > target) {
-                mine = j;
-                nt = fabs(target - before) <= 1e-6 * total || fabs(run - target) <= 1e-6 * total;
+        int mine = INT_MAX;
+        double run = excl, before = excl;
+        for (int i = lo; i < hi; ++i) {
+            const double b = run;
+            run = run + __ldcg(cm + i);
+            if (run > target) { mine = i; before = b; break; }
+        }
+        int a = mine;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a = min(a, __shfl_down_sync(0xffffffffu, a, o));
+        if (lane == 0) s_min[wid] = a;
+        __syncthreads();
+        if (t_id == 0) {
+            int cmin = INT_MAX;
+            for (int i = 0; i < kRcThreads / 32; ++i) cmin = min(cmin, s_min[i]);
+            s_chunk = cmin;
+        }
+        __syncthreads();
+        int chunk = s_chunk;
+        if (mine == chunk && chunk != INT_MAX) s_pre = before;   // exactly one thread owns it
+        __syncthreads();
+        const bool rounding_miss = chunk == INT_MAX;             // the target rounded past every prefix
+        if (rounding_miss) chunk = nchunk - 1;
+        const double pre = rounding_miss ? 0.0 : s_pre;
+        // ---- the owner warp picks inside the chunk and publishes
+        if (chunk >= c0 && chunk < c1 && (chunk - c0) % (kRcThreads / 32) == wid) {
+            const int j = chunk * 32 + lane;
+            double e = 0.0;
+            if (j < m) e = step == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)rD2[j]);
+            const double incl = warp_incl_scan_f64(e, lane);
+            const double cum = pre + incl, cum0 = pre + (incl - e);
+            int pick;
+            if (!rounding_miss) {
+                const unsigned hit = __ballot_sync(0xffffffffu, j < m && cum > target);
+                // fall back to the chunk's last positive mass if rounding hides the crossing
+                const unsigned pos = __ballot_sync(0xffffffffu, j < m && e > 0.0);
+                pick = hit ? chunk * 32 + __ffs(hit) - 1 : chunk * 32 + 31 - __clz(pos);
+                const bool near = fabs(target - cum0) <= 1e-6 * total || fabs(cum - target) <= 1e-6 * total;
+                if (hit && lane == __ffs(hit) - 1 && near) atomicAdd(&st->recluster_near, 1ull);
+            } else {
+                // last candidate with positive mass anywhere (scan chunks backwards)
+                pick = -1;
+                for (int ch2 = nchunk - 1; ch2 >= 0 && pick < 0; --ch2) {
+                    const int jj = ch2 * 32 + lane;
+                    const double ee = (jj < m) ? (step == 0 ? (double)w[jj] : (double)w[jj] * (double)__ldcg(rD2 + jj)) : 0.0;
+                    const unsigned pos = __ballot_sync(0xffffffffu, ee > 0.0);
+                    if (pos) pick = ch2 * 32 + 31 - __clz(pos);
+                }
+                if (lane == 0) atomicAdd(&st->recluster_near, 1ull);
+            }
+            if (lane == 0) {
+                sync->pick[step & 1] = pick;
+                chosen[step] = pick;
+                __threadfence();
+                atomicExch(&sync->pick_flag, (unsigned)(step + 1));
             }
         }
-        // block min of the first crossing, block max of the last positive mass
-        int a = mine, b = lastpos;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a = min(a, __shfl_down_sync(0xffffffffu, a, o));
-            b = max(b, __shfl_down_sync(0xffffffffu, b, o));
+        // ---- wait for the pick (bounded) and load its row
+        if (t_id == 0) {
+            s_go = 1;
+            volatile unsigned int *flag = &sync->pick_flag;
+            const unsigned long long t0 = clock64();
+            while (*flag < (unsigned)(step + 1)) {
+                if (*(volatile int *)&sync->abort || clock64() - t0 > kRcWait) {
+                    atomicCAS(err, 0, 2);
+                    atomicExch(&sync->abort, 1);
+                    s_go = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+            __threadfence();
+            s_pick = s_go ? ((volatile int *)sync->pick)[step & 1] : 0;
         }
-        if (lane == 0) { s_min[wid] = a; s_max[wid] = b; }
         __syncthreads();
-        if (t == 0) {
-            int pa = INT_MAX, pb = -1;
-            for (int i = 0; i < kRcThreads / 32; ++i) { pa = min(pa, s_min[i]); pb = max(pb, s_max[i]); }
-            if (pa == INT_MAX) { pa = pb; atomicAdd(&st->recluster_near, 1ull); }
-            s_pick = pa;
-            chosen[step] = pa;
-        }
-        __syncthreads();
-        if (nt && mine == s_pick) atomicAdd(&st->recluster_near, 1ull);
+        if (!s_go) return;
         const int pick = s_pick;
-        for (int qq = t; qq < d; qq += kRcThreads) {
-            const float v = C[(int64_t)pick * d + qq];
+        for (int qq = t_id; qq < d; qq += kRcThreads) {
+            const float v = __ldcg(C + (int64_t)pick * d + qq);
             cnew[qq] = v;
-            centers[(int64_t)step * d + qq] = v;
+            if (blockIdx.x == 0) centers[(int64_t)step * d + qq] = v;
         }
         __syncthreads();
-        for (int j = lo; j < hi; ++j) {
-            const float v = dist2_fp32(C + (int64_t)j * d, cnew, d);
-            rD2[j] = step == 0 ? v : fminf(rD2[j], v);
+        // ---- C: D^2 update of own candidates
+        for (int ch = c0 + wid; ch < c1; ch += kRcThreads / 32) {
+            const int j = ch * 32 + lane;
+            if (j < m) {
+                const float v = dist2_fp32(C + (int64_t)j * d, cnew, d);
+                rD2[j] = step == 0 ? v : fminf(rD2[j], v);
+            }
         }
-        __syncthreads();
+        // the next step's barrier orders these writes before anyone reads them
     }
 }
 
 cudaError_t launch_recluster(Ctx &c, float *centers) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c.rc_sync, 0, sizeof(RcSync), c.stream)) != cudaSuccess) return e;
     const size_t smem = sizeof(float) * (size_t)c.d;
-    recluster_kernel<<<1, kRcThreads, smem, c.stream>>>(c.C, c.w, c.st, c.d, c.k, c.seed, c.rD2, c.chosen,
-                                                       centers);
+    // co-resident CTAs: one per SM at most, no more than there are chunks
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, recluster_kernel, kRcThreads, smem)) !=
+        cudaSuccess)
+        return e;
+    const int max_chunks = (c.cap_total + 31) / 32;
+    int G = std::min(c.num_sms * std::max(per_sm, 1), std::max(1, (max_chunks + 3) / 4));
+    G = std::max(1, std::min(G, c.num_sms));
+    const float *Cp = c.C;
+    const long long *wp = c.w;
+    DevState *stp = c.st;
+    int d = c.d, k = c.k;
+    uint64_t seed = c.seed;
+    float *rD2 = c.rD2;
+    int32_t *chosen = c.chosen;
+    double *cm = c.rc_cmass;
+    RcSync *sy = reinterpret_cast<RcSync *>(c.rc_sync);
+    int *err = c.rc_err;
+    void *args[] = {&Cp, &wp, &stp, &d, &k, &seed, &rD2, &chosen, &centers, &cm, &sy, &err};
+    e = cudaLaunchCooperativeKernel((const void *)recluster_kernel, dim3(G), dim3(kRcThreads), args, smem, c.stream);
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
+size_t recluster_sync_bytes() { return sizeof(RcSync); }
+
 // ------------------------------------------------------------------ Lloyd: centroids
-// per sort block b (kSortBlock points): hist[b][j] = #points with label j
-__global__ void label_hist_kernel(const int32_t *__restrict__ labels, int64_t n, int k, int32_t *hist) {
+// A stable counting sort of the points by label (per-block histograms, a chunked
+// column scan, one warp per block scattering in point order) puts every cluster's
+// members in ascending point order; each cluster is then cut into fixed pieces of
+// kPiece sorted members, one CTA sums a piece in FP64 (fixed order), and the
+// pieces of a cluster are added in order.  The result does not depend on
+// scheduling or on the GPU's SM count.
+constexpr int kPiece = 256;
+
+// per sort block b (sb points): hist[b][j] = #points with label j
+__global__ void label_hist_kernel(const int32_t *__restrict__ labels, int64_t n, int k, int sb, int32_t *hist) {
     extern __shared__ int32_t h[];
     for (int j = threadIdx.x; j < k; j += blockDim.x) h[j] = 0;
     __syncthreads();
-    const int64_t b0 = (int64_t)blockIdx.x * kSortBlock;
-    const int64_t b1 = min(n, b0 + kSortBlock);
+    const int64_t b0 = (int64_t)blockIdx.x * sb;
+    const int64_t b1 = min(n, b0 + sb);
     for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) atomicAdd(&h[labels[i]], 1);
     __syncthreads();
     for (int j = threadIdx.x; j < k; j += blockDim.x) hist[(int64_t)blockIdx.x * k + j] = h[j];
 }
 
-// column scan: hist[b][j] <- sum_{b' < b} hist[b'][j]; tot[j] = column total
-__global__ void column_scan_kernel(int32_t *hist, int nsb, int k, int32_t *tot) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= k) return;
-    int run = 0;
-    for (int b = 0; b < nsb; ++b) {
-        const int v = hist[(int64_t)b * k + j];
-        hist[(int64_t)b * k + j] = run;
-        run += v;
+// column scan in two parallel passes over (32 columns) x (64-row chunks):
+// chunk totals, then each chunk's offset = sum of the earlier chunks, rescanned
+// row by row: hist[b][j] <- sum_{b' < b} hist[b'][j]; tot[j] = column total.
+constexpr int kScanRows = 64;
+
+__global__ void __launch_bounds__(256) column_chunk_kernel(const int32_t *__restrict__ hist, int nsb, int k,
+                                                           int32_t *chunk) {
+    __shared__ int part[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + lane, rc = blockIdx.y;
+    const int b0 = rc * kScanRows + w * (kScanRows / 8);
+    const int b1 = min(nsb, b0 + kScanRows / 8);
+    int s = 0;
+    if (j < k)
+        for (int b = b0; b < b1; ++b) s += hist[(int64_t)b * k + j];
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && j < k) {
+        int t = 0;
+        for (int i = 0; i < 8; ++i) t += part[i][lane];
+        chunk[(int64_t)rc * k + j] = t;
     }
-    tot[j] = run;
 }
 
-// base[j] = sum_{j' < j} tot[j'], base[k] = n (one CTA, contiguous chunks)
-__global__ void __launch_bounds__(1024) base_scan_kernel(int32_t *tot_base, int k) {
-    __shared__ int buf[1024];
+__global__ void __launch_bounds__(256) column_offset_kernel(int32_t *hist, int nsb, int k,
+                                                            const int32_t *__restrict__ chunk, int nrc, int32_t *tot) {
+    __shared__ int part[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + lane, rc = blockIdx.y;
+    // offset of this chunk (earlier chunks, split over the 8 warps, fixed order)
+    int s = 0;
+    if (j < k)
+        for (int i = w; i < rc; i += 8) s += chunk[(int64_t)i * k + j];
+    part[w][lane] = s;
+    __syncthreads();
+    int off = 0;
+    for (int i = 0; i < 8; ++i) off += part[i][lane];
+    if (rc == nrc - 1 && w == 0 && j < k) tot[j] = off + chunk[(int64_t)rc * k + j];
+    __syncthreads();
+    // per-warp prefix inside the chunk, then each warp rescans its rows
+    const int b0 = rc * kScanRows + w * (kScanRows / 8);
+    const int b1 = min(nsb, b0 + kScanRows / 8);
+    int mine = 0;
+    if (j < k)
+        for (int b = b0; b < b1; ++b) mine += hist[(int64_t)b * k + j];
+    part[w][lane] = mine;
+    __syncthreads();
+    int run = off;
+    for (int i = 0; i < w; ++i) run += part[i][lane];
+    if (j < k)
+        for (int b = b0; b < b1; ++b) {
+            const int64_t o = (int64_t)b * k + j;
+            const int v = hist[o];
+            hist[o] = run;
+            run += v;
+        }
+}
+
+// base[j] = sum_{j' < j} tot[j'] (base[k] = n) and piece[j] = sum_{j' < j}
+// ceil(tot[j'] / kPiece) (piece[k] = number of pieces); one CTA, contiguous chunks
+__global__ void __launch_bounds__(1024) base_scan_kernel(int32_t *tot_base, int k, int32_t *piece) {
+    __shared__ int buf[1024], bufp[1024];
     const int t = threadIdx.x;
     const int q = (k + 1023) / 1024;
     const int lo = min(k, t * q), hi = min(k, lo + q);
-    int local = 0;
-    for (int j = lo; j < hi; ++j) local += tot_base[j];
+    int local = 0, localp = 0;
+    for (int j = lo; j < hi; ++j) {
+        const int v = tot_base[j];
+        local += v;
+        localp += (v + kPiece - 1) / kPiece;
+    }
     buf[t] = local;
+    bufp[t] = localp;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {
-        const int a = t >= off ? buf[t - off] : 0;
+        const int a = t >= off ? buf[t - off] : 0, ap = t >= off ? bufp[t - off] : 0;
         __syncthreads();
         buf[t] += a;
+        bufp[t] += ap;
         __syncthreads();
     }
-    int run = t > 0 ? buf[t - 1] : 0;
-    const int total = buf[1023];
+    int run = t > 0 ? buf[t - 1] : 0, runp = t > 0 ? bufp[t - 1] : 0;
+    const int total = buf[1023], totalp = bufp[1023];
     __syncthreads();
     for (int j = lo; j < hi; ++j) {
         const int v = tot_base[j];
         tot_base[j] = run;
+        piece[j] = runp;
         run += v;
+        runp += (v + kPiece - 1) / kPiece;
     }
-    if (t == 0) tot_base[k] = total;
+    if (t == 0) {
+        tot_base[k] = total;
+        piece[k] = totalp;
+    }
 }
 
 // one warp per sort block: stable scatter of point numbers into label order
-__global__ void __launch_bounds__(32) scatter_kernel(const int32_t *__restrict__ labels, int64_t n, int k,
+__global__ void __launch_bounds__(32) scatter_kernel(const int32_t *__restrict__ labels, int64_t n, int k, int sb,
                                                      const int32_t *__restrict__ hist,
                                                      const int32_t *__restrict__ base, int32_t *perm) {
     extern __shared__ int32_t cur[];
     const int lane = threadIdx.x;
     for (int j = lane; j < k; j += 32) cur[j] = base[j] + hist[(int64_t)blockIdx.x * k + j];
     __syncwarp();
-    const int64_t b0 = (int64_t)blockIdx.x * kSortBlock;
-    const int64_t b1 = min(n, b0 + kSortBlock);
+    const int64_t b0 = (int64_t)blockIdx.x * sb;
+    const int64_t b1 = min(n, b0 + sb);
     for (int64_t c0 = b0; c0 < b1; c0 += 32) {
         const int64_t i = c0 + lane;
         const bool valid = i < b1;
@@ -214,53 +415,113 @@ __global__ void __launch_bounds__(32) scatter_kernel(const int32_t *__restrict__
     }
 }
 
-// one CTA (8 warps) per cluster: FP64 sum of member rows in a fixed order, then
-// centroid = sum / count rounded to FP32; an empty cluster keeps its center.
-__global__ void __launch_bounds__(256) centroid_kernel(const float *__restrict__ X, int d,
-                                                       const int32_t *__restrict__ perm,
-                                                       const int32_t *__restrict__ base, float *centers) {
+// Error-free accumulation of FP32 values: TwoSum (Knuth) keeps the exact rounding
+// error of every addition; (s, c) carries at least 44 significant bits.  The
+// rounded operations are explicit so that no reassociation can change them.
+__device__ __forceinline__ void two_sum_add(float &s, float &c, float x) {
+    const float t = __fadd_rn(s, x);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    c = __fadd_rn(c, err);
+    s = t;
+}
+
+// one CTA per piece: sum of up to kPiece sorted member rows (8 warps x 32
+// coordinates; warp w takes members w, w+8, ... in order, eight loads in flight,
+// compensated FP32 accumulation), the warps' sums combined in FP64 in order
+__global__ void __launch_bounds__(256) piece_sum_kernel(const float *__restrict__ X, int d, int k,
+                                                        const int32_t *__restrict__ perm,
+                                                        const int32_t *__restrict__ base,
+                                                        const int32_t *__restrict__ piece, double *psum) {
     __shared__ double part[8][32];
-    const int j = blockIdx.x;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int b0 = base[j], cnt = base[j + 1] - b0;
-    if (cnt == 0) return;
+    __shared__ int rows[kPiece];
+    __shared__ int s_j;
+    const int pid = blockIdx.x;
+    if (pid >= piece[k]) return;   // uniform per block
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = k;        // the cluster whose piece range holds pid
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (piece[mid] <= pid) lo = mid; else hi = mid;
+        }
+        s_j = lo;
+    }
+    __syncthreads();
+    const int j = s_j;
+    const int p0 = base[j] + (pid - piece[j]) * kPiece;
+    const int cnt = min(kPiece, base[j + 1] - p0);
+    for (int i = threadIdx.x; i < cnt; i += 256) rows[i] = perm[p0 + i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int dc = 0; dc < d; dc += 32) {
         const int q = dc + lane;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        float s = 0.f, c = 0.f;
         if (q < d) {
-            int p = wid;
-            for (; p + 24 < cnt; p += 32) {
-                a0 += (double)X[(int64_t)perm[b0 + p] * d + q];
-                a1 += (double)X[(int64_t)perm[b0 + p + 8] * d + q];
-                a2 += (double)X[(int64_t)perm[b0 + p + 16] * d + q];
-                a3 += (double)X[(int64_t)perm[b0 + p + 24] * d + q];
+            int i = w;
+            for (; i + 56 < cnt; i += 64) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = __ldg(X + (int64_t)rows[i + 8 * u] * d + q);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) two_sum_add(s, c, v[u]);
             }
-            for (; p < cnt; p += 8) a0 += (double)X[(int64_t)perm[b0 + p] * d + q];
+            for (; i < cnt; i += 8) two_sum_add(s, c, __ldg(X + (int64_t)rows[i] * d + q));
         }
-        part[wid][lane] = (a0 + a1) + (a2 + a3);
+        part[w][lane] = (double)s + (double)c;
         __syncthreads();
-        if (wid == 0 && q < d) {
-            double s = 0.0;
-            for (int w8 = 0; w8 < 8; ++w8) s += part[w8][lane];
-            centers[(int64_t)j * d + q] = (float)__ddiv_rn(s, (double)cnt);
+        if (w == 0 && q < d) {
+            double acc = 0.0;
+            for (int u = 0; u < 8; ++u) acc += part[u][lane];
+            psum[(int64_t)pid * d + q] = acc;
         }
         __syncthreads();
     }
 }
 
+// per cluster: pieces added in order, centroid = sum / count rounded to FP32;
+// an empty cluster keeps its center
+__global__ void centroid_finalize_kernel(int d, int k, const int32_t *__restrict__ base,
+                                         const int32_t *__restrict__ piece, const double *__restrict__ psum,
+                                         float *centers) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)k * d) return;
+    const int j = (int)(e / d), q = (int)(e - (int64_t)j * d);
+    const int cnt = base[j + 1] - base[j];
+    if (cnt == 0) return;
+    double s = 0.0;
+    for (int p = piece[j]; p < piece[j + 1]; ++p) s += psum[(int64_t)p * d + q];
+    centers[e] = (float)__ddiv_rn(s, (double)cnt);
+}
+
+int sort_block_size(int64_t n, int k) {
+    int sb = 512;
+    while ((int64_t)((n + sb - 1) / sb) * k > (1ll << 26) && sb < (1 << 20)) sb <<= 1;
+    return sb;
+}
+
+int64_t max_pieces(int64_t n, int k) { return (n + kPiece - 1) / kPiece + k; }
+
+int64_t scan_chunks(int nsb) { return (nsb + kScanRows - 1) / kScanRows; }
+
 cudaError_t launch_centroids(Ctx &c, const int32_t *labels, float *centers) {
     cudaError_t e;
-    const int k = c.k;
-    label_hist_kernel<<<c.nsb, 256, sizeof(int32_t) * k, c.stream>>>(labels, c.n, k, c.hist);
+    const int k = c.k, sb = c.sort_block;
+    label_hist_kernel<<<c.nsb, 256, sizeof(int32_t) * k, c.stream>>>(labels, c.n, k, sb, c.hist);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    column_scan_kernel<<<(k + 255) / 256, 256, 0, c.stream>>>(c.hist, c.nsb, k, c.base);
+    const int nrc = (c.nsb + kScanRows - 1) / kScanRows;
+    column_chunk_kernel<<<dim3((k + 31) / 32, nrc), 256, 0, c.stream>>>(c.hist, c.nsb, k, c.chunk);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    base_scan_kernel<<<1, 1024, 0, c.stream>>>(c.base, k);
+    column_offset_kernel<<<dim3((k + 31) / 32, nrc), 256, 0, c.stream>>>(c.hist, c.nsb, k, c.chunk, nrc, c.base);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    scatter_kernel<<<c.nsb, 32, sizeof(int32_t) * k, c.stream>>>(labels, c.n, k, c.hist, c.base, c.perm);
+    base_scan_kernel<<<1, 1024, 0, c.stream>>>(c.base, k, c.piece);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    centroid_kernel<<<k, 256, 0, c.stream>>>(c.X, c.d, c.perm, c.base, centers);
-    count_launches(5);
+    scatter_kernel<<<c.nsb, 32, sizeof(int32_t) * k, c.stream>>>(labels, c.n, k, sb, c.hist, c.base, c.perm);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    piece_sum_kernel<<<(int)max_pieces(c.n, k), 256, 0, c.stream>>>(c.X, c.d, k, c.perm, c.base, c.piece, c.psum);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int64_t kd = (int64_t)k * c.d;
+    centroid_finalize_kernel<<<(int)((kd + 255) / 256), 256, 0, c.stream>>>(c.d, k, c.base, c.piece, c.psum, centers);
+    count_launches(7);
     return cudaGetLastError();
 }
 

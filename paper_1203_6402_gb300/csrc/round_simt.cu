@@ -470,19 +470,134 @@ cudaError_t launch_sum_rows(const float *v, int64_t n, double *partials, int max
     return launch_sum_f64(partials, (int)nb, out, copy, s);
 }
 
+// (value, index) top-2 of the union of two top-2 lists (lowest index on equal values)
+__device__ __forceinline__ bool lex_lt(float v, int i, float w, int j) { return v < w || (v == w && i < j); }
+
+__device__ __forceinline__ void top2_merge(float &b1, int &i1, float &b2, int &i2, float c1, int j1, float c2, int j2) {
+    if (lex_lt(c1, j1, b1, i1)) {
+        // c1 is the new best; second = best of (b1, c2)
+        if (lex_lt(b1, i1, c2, j2)) { b2 = b1; i2 = i1; } else { b2 = c2; i2 = j2; }
+        b1 = c1; i1 = j1;
+    } else if (lex_lt(c1, j1, b2, i2)) {
+        b2 = c1; i2 = j1;
+    }
+}
+
+// Rows whose screening window held more than one center, finished exactly: a CTA
+// takes 8 listed rows (one warp each) and streams tiles of 64 centers through
+// shared memory (odd row stride: conflict-free); the lanes of a warp split each
+// tile's centers (exact FP32 difference form, ascending coordinates), a
+// lexicographic top-2 merge across lanes follows, then the same decision as
+// nearest_kernel.  Persistent: the row count is read on the device.
+constexpr int kFixTile = 64;
+
+template <int MODE>
+__global__ void __launch_bounds__(256) fixup_tile_kernel(const float *__restrict__ X, int d,
+                                                        const float *__restrict__ C, int c_cnt, const DevState *st,
+                                                        const int32_t *__restrict__ rows, const int *rows_cnt,
+                                                        float *D2, int32_t *idx, int32_t *labels, const int32_t *prev,
+                                                        int *changed, float *dmin, unsigned long long *fp64_cnt,
+                                                        unsigned long long *wide_cnt) {
+    extern __shared__ float fsm[];
+    const int ds = d | 1;
+    float *ct = fsm;                        // kFixTile x ds center rows
+    float *xs_all = fsm + kFixTile * ds;    // 8 x ds point rows
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nrows = *rows_cnt;
+    const int begin = MODE == MODE_ROUND ? st->batch_begin : 0;
+    const int cnt = MODE == MODE_ROUND ? st->batch_cnt : c_cnt;
+    const float FMAX = FLT_MAX;
+    for (int g0 = blockIdx.x * 8; g0 < nrows; g0 += gridDim.x * 8) {   // uniform per block
+        const int g = g0 + wid;
+        const bool valid = g < nrows;
+        const int64_t R = valid ? rows[g] : 0;
+        float *xs = xs_all + wid * ds;
+        const float *xrow = X + R * d;
+        if (valid)
+            for (int q = lane; q < d; q += 32) xs[q] = __ldg(xrow + q);
+        float b1 = FMAX, b2 = FMAX;
+        int i1 = INT_MAX, i2 = INT_MAX;
+        for (int t0 = 0; t0 < cnt; t0 += kFixTile) {
+            const int nt = min(kFixTile, cnt - t0);
+            __syncthreads();
+            stage_rows(ct, ds, C + (int64_t)(begin + t0) * d, nt, d, threadIdx.x, 256);
+            __syncthreads();
+            if (valid)
+                for (int rr = lane; rr < nt; rr += 32) {
+                    const float v = dist2_fp32(xs, ct + rr * ds, d);
+                    const int j = begin + t0 + rr;
+                    if (lex_lt(v, j, b2, i2)) {
+                        if (lex_lt(v, j, b1, i1)) { b2 = b1; i2 = i1; b1 = v; i1 = j; }
+                        else { b2 = v; i2 = j; }
+                    }
+                }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float c1 = __shfl_xor_sync(0xffffffffu, b1, o), c2 = __shfl_xor_sync(0xffffffffu, b2, o);
+            const int j1 = __shfl_xor_sync(0xffffffffu, i1, o), j2 = __shfl_xor_sync(0xffffffffu, i2, o);
+            top2_merge(b1, i1, b2, i2, c1, j1, c2, j2);
+        }
+        if (valid && lane == 0) {
+            if (i2 == INT_MAX) { i2 = -1; b2 = FMAX; }
+            const float W = fp32_tie_window(d);
+            if (MODE == MODE_ASSIGN) {
+                int lab = i1 != INT_MAX ? i1 : 0;
+                float stored = b1;
+                if (i2 >= 0 && b2 <= b1 + W * b1) {
+                    double best = dist2_fp64(xrow, C + (int64_t)i1 * d, d);
+                    int bj = i1;
+                    take_if_better(dist2_fp64(xrow, C + (int64_t)i2 * d, d), i2, best, bj);
+                    if (bj == i2) { lab = i2; stored = b2; }
+                    atomicAdd(fp64_cnt, 1ull);
+                }
+                if (labels) labels[R] = lab;
+                if (dmin) dmin[R] = stored;
+                if (prev && changed && prev[R] != lab) atomicAdd(changed, 1);
+            } else {
+                const float old = D2[R];
+                const int oi = idx[R];
+                const float m32 = fminf(old, b1);
+                const float lim = m32 + W * m32;
+                const bool in_old = (oi >= 0) && old <= lim;
+                const bool in1 = i1 != INT_MAX && b1 <= lim;
+                const bool in2 = i2 >= 0 && b2 <= lim;
+                int win = -1;
+                float wv = old;
+                if ((int)in_old + (int)in1 + (int)in2 >= 2) {
+                    double best = DBL_MAX;
+                    int bj = INT_MAX;
+                    if (in_old) take_if_better(dist2_fp64(xrow, C + (int64_t)oi * d, d), oi, best, bj);
+                    if (in1) take_if_better(dist2_fp64(xrow, C + (int64_t)i1 * d, d), i1, best, bj);
+                    if (in2) take_if_better(dist2_fp64(xrow, C + (int64_t)i2 * d, d), i2, best, bj);
+                    atomicAdd(fp64_cnt, 1ull);
+                    if (in1 && in2) atomicAdd(wide_cnt, 1ull);
+                    if (bj == i1) { win = i1; wv = b1; }
+                    else if (bj == i2) { win = i2; wv = b2; }
+                } else if (i1 != INT_MAX && b1 < old) {
+                    win = i1; wv = b1;
+                }
+                if (win >= 0) { D2[R] = wv; idx[R] = win; }
+            }
+        }
+    }
+}
+
 // fix-up rows of a tensor pass, finished exactly on CUDA cores
 cudaError_t launch_fixup(const Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
                          int *changed, float *dmin) {
-    NearestParams p{};
-    p.X = c.X; p.n = c.n; p.d = c.d; p.C = C; p.st = c.st;
-    p.rows = c.fix_rows; p.rows_cnt = c.fix_cnt;
-    p.fp64_cnt = &c.st->argmin_fp64; p.wide_cnt = &c.st->argmin_wide;
-    if (mode_round) {
-        p.D2 = c.D2; p.idx = c.idx;
-        return launch_nearest_mode<MODE_ROUND>(p, c.stream);
-    }
-    p.c_begin = 0; p.c_cnt = k; p.labels = labels; p.prev = prev; p.changed = changed; p.dmin = dmin;
-    return launch_nearest_mode<MODE_ASSIGN>(p, c.stream);
+    const int grid = c.num_sms * 4;   // persistent: the row count is only known on the device
+    const size_t sm = sizeof(float) * (size_t)(kFixTile + 8) * (c.d | 1);
+    if (mode_round)
+        fixup_tile_kernel<MODE_ROUND><<<grid, 256, sm, c.stream>>>(c.X, c.d, C, 0, c.st, c.fix_rows, c.fix_cnt, c.D2,
+                                                                   c.idx, nullptr, nullptr, nullptr, nullptr,
+                                                                   &c.st->argmin_fp64, &c.st->argmin_wide);
+    else
+        fixup_tile_kernel<MODE_ASSIGN><<<grid, 256, sm, c.stream>>>(c.X, c.d, C, k, c.st, c.fix_rows, c.fix_cnt,
+                                                                    nullptr, nullptr, labels, prev, changed, dmin,
+                                                                    &c.st->argmin_fp64, &c.st->argmin_wide);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 __global__ void count_fixups_kernel(const int *fix_cnt, int64_t n, DevState *st) {
@@ -497,32 +612,30 @@ cudaError_t count_fixups(Ctx &c) {
 }
 
 // Exact FP32 distance and decision for the rows whose nearest center the tensor
-// screening made certain (cand1 >= 0).  One CTA per 128 rows: the row tile is
-// staged in shared memory with coalesced loads (odd row stride, no bank
-// conflicts); each thread walks its center row in chunks of 8 independent loads.
+// screening made certain (cand1 >= 0).  Each warp stages its 32 point rows in
+// shared memory with coalesced loads (odd row stride: conflict-free reads), then
+// each lane sums its row against its center row (read in chunks of 8 independent
+// loads) in the exact FP32 difference form, ascending coordinates.
 template <int MODE>
-__global__ void __launch_bounds__(128) refine_kernel(const float *__restrict__ X, int64_t n, int d,
+__global__ void __launch_bounds__(256) refine_kernel(const float *__restrict__ X, int64_t n, int d,
                                                     const float *__restrict__ C, const int32_t *__restrict__ cand1,
                                                     float *D2, int32_t *idx, int32_t *labels, const int32_t *prev,
                                                     int *changed, float *dmin, unsigned long long *fp64_cnt) {
-    extern __shared__ float xt[];
-    __shared__ int redi[4];
+    extern __shared__ float rsm[];
+    __shared__ int redi[8];
     const int ds = d | 1;
-    const int64_t r0 = (int64_t)blockIdx.x * 128;
-    const int nr = (int)min((int64_t)128, n - r0);
-    const float *src = X + r0 * d;
-    for (int i = threadIdx.x; i < nr * d; i += 128) {
-        const int rr = i / d;
-        xt[rr * ds + (i - rr * d)] = __ldg(src + i);
-    }
-    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float *xs = rsm + wid * 32 * ds;
+    const int64_t w0 = (int64_t)blockIdx.x * 256 + wid * 32;
+    const int nw = (int)max((int64_t)0, min((int64_t)32, n - w0));
+    if (nw > 0) stage_rows(xs, ds, X + w0 * d, nw, d, lane, 32);
+    __syncwarp();
+    const int64_t R = w0 + lane;
     int chg = 0;
-    const int t = threadIdx.x;
-    if (t < nr) {
-        const int64_t R = r0 + t;
+    if (lane < nw) {
         const int j = cand1[R];
         if (j >= 0) {
-            const float *xs = xt + t * ds;
+            const float *xr = xs + lane * ds;
             const float *cr = C + (int64_t)j * d;
             float b1 = 0.f;
             int q = 0;
@@ -532,12 +645,12 @@ __global__ void __launch_bounds__(128) refine_kernel(const float *__restrict__ X
                 for (int u = 0; u < 8; ++u) cv[u] = __ldg(cr + q + u);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const float tq = __fsub_rn(xs[q + u], cv[u]);
+                    const float tq = __fsub_rn(xr[q + u], cv[u]);
                     b1 = __fmaf_rn(tq, tq, b1);
                 }
             }
             for (; q < d; ++q) {
-                const float tq = __fsub_rn(xs[q], __ldg(cr + q));
+                const float tq = __fsub_rn(xr[q], __ldg(cr + q));
                 b1 = __fmaf_rn(tq, tq, b1);
             }
             if (MODE == MODE_ROUND) {
@@ -565,20 +678,29 @@ __global__ void __launch_bounds__(128) refine_kernel(const float *__restrict__ X
     }
     if (MODE == MODE_ASSIGN && changed) {
         const int c = warp_sum_i32(chg);
-        if ((threadIdx.x & 31) == 0) redi[threadIdx.x >> 5] = c;
+        if (lane == 0) redi[wid] = c;
         __syncthreads();
         if (threadIdx.x == 0) {
-            const int tot = redi[0] + redi[1] + redi[2] + redi[3];
+            int tot = 0;
+            for (int i = 0; i < 8; ++i) tot += redi[i];
             if (tot) atomicAdd(changed, tot);
         }
     }
 }
 
 cudaError_t configure_refine_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(refine_kernel<MODE_ROUND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         128 * 129 * 4);
+    // 256 staged rows of up to 191 floats (the tensor passes support d + 2 <= 192)
+    cudaError_t er = cudaFuncSetAttribute(refine_kernel<MODE_ROUND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          200 * 1024);
+    if (er != cudaSuccess) return er;
+    er = cudaFuncSetAttribute(refine_kernel<MODE_ASSIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (er != cudaSuccess) return er;
+    const int bytes = (kFixTile + 8) * 4097 * 4;
+    cudaError_t e = cudaFuncSetAttribute(fixup_tile_kernel<MODE_ROUND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         std::min(bytes, 200 * 1024));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(refine_kernel<MODE_ASSIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 129 * 4);
+    return cudaFuncSetAttribute(fixup_tile_kernel<MODE_ASSIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                std::min(bytes, 200 * 1024));
 }
 
 cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
@@ -601,13 +723,13 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
     if ((e = timing_begin(c, &ev)) != cudaSuccess) return e;
     if ((e = tc::launch_nearest_tc(p, mode_round, c.num_sms, c.stream)) != cudaSuccess) return e;
     if ((e = timing_end(c, ev, timing_cls)) != cudaSuccess) return e;
-    const int grid = (int)((c.n + 127) / 128);
-    const size_t sm = (size_t)128 * (c.d | 1) * sizeof(float);
+    const int grid = (int)((c.n + 255) / 256);
+    const size_t rsm = sizeof(float) * 256 * (size_t)(c.d | 1);
     if (mode_round)
-        refine_kernel<MODE_ROUND><<<grid, 128, sm, c.stream>>>(c.X, c.n, c.d, C, c.cand1, c.D2, c.idx, nullptr,
+        refine_kernel<MODE_ROUND><<<grid, 256, rsm, c.stream>>>(c.X, c.n, c.d, C, c.cand1, c.D2, c.idx, nullptr,
                                                                nullptr, nullptr, nullptr, &c.st->argmin_fp64);
     else
-        refine_kernel<MODE_ASSIGN><<<grid, 128, sm, c.stream>>>(c.X, c.n, c.d, C, c.cand1, nullptr, nullptr, labels,
+        refine_kernel<MODE_ASSIGN><<<grid, 256, rsm, c.stream>>>(c.X, c.n, c.d, C, c.cand1, nullptr, nullptr, labels,
                                                                 prev, changed, dmin, &c.st->argmin_fp64);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -33,6 +33,12 @@ UNIT = "dist-evals/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
 SMS = 152
 FP32_LANES_PER_SM = 128
+ALU_LANES_PER_SM = 64          # integer/min-max/logic pipe: half the FP32 lane count
+# screening epilogue: per pair of distances 2 key builds + 5 min/max = 3.5 ALU ops per distance
+SCREEN_ALU_OPS = 3.5
+# DRAM bytes per launch of the tensor assignment pass (ncu capture of the same kernel on this
+# workload, profiles/nearest_tc_assign_bf16x3_kdd_n1M.md); None once the kernel changes
+TC_ASSIGN_TRAFFIC = {"bf16x3": 260.2e6 + 5.66e6}
 
 
 def load_peaks():
@@ -206,20 +212,40 @@ def run_ours(args, rank, world):
         units = n * k                              # dist-evals per Lloyd assignment pass
     else:
         units = n * (sum(st_t["round_added"]) / max(len(st_t["round_added"]), 1))
-    # exact FP32 difference form on CUDA cores: 2 FP32 instructions (sub, fma) per
-    # coordinate; peak = 128 FP32 lanes x 152 SMs x max SM clock
     clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    achieved = units * 2 * d / (per_launch_ms / 1e3) / 1e12
-    peak = FP32_LANES_PER_SM * SMS * clk / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s (FP32 issue)",
-                "frac": achieved / peak, "traffic": None, "kernel": f"nearest_kernel ({cls} pass)",
-                "avg_launch_ms": per_launch_ms, "launches": kl, "peak_source": "derived: 128 lanes x 152 SMs x "
-                f"{peaks.get('sm_max_mhz', 2070.0)} MHz"}
+    secs = per_launch_ms / 1e3
+    if args.precision == "fp32":
+        # exact FP32 difference form on CUDA cores: 2 FP32 instructions (sub, fma) per
+        # coordinate; peak = 128 FP32 lanes x 152 SMs x max SM clock
+        achieved = units * 2 * d / secs / 1e12
+        peak = FP32_LANES_PER_SM * SMS * clk / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s (FP32 issue)",
+                    "frac": achieved / peak, "traffic": None, "kernel": f"nearest_kernel ({cls} pass)",
+                    "peak_source": f"derived: 128 FP32 lanes x 152 SMs x {peaks.get('sm_max_mhz', 2070.0)} MHz"}
+    else:
+        # tcgen05 screening: the epilogue's min/max/key ops bind (ncu: ALU pipe ~72% busy,
+        # tensor pipe ~37%); peak = 64 ALU lanes x 152 SMs x max SM clock
+        achieved = units * SCREEN_ALU_OPS / secs / 1e12
+        peak = ALU_LANES_PER_SM * SMS * clk / 1e12
+        tflops = units * 2 * d / secs / 1e12
+        bf16_peak = float(peaks.get("bf16_tflops", 1964.5))
+        traffic = TC_ASSIGN_TRAFFIC.get(args.precision) if cls == "assign" and args.workload == "kdd_n1M_d42_k500" \
+            and not args.n else None
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T ALU ops/s",
+                    "frac": achieved / peak, "traffic": traffic,
+                    "kernel": f"nearest_tc_kernel ({cls} pass)",
+                    "peak_source": f"derived: 64 ALU lanes x 152 SMs x {peaks.get('sm_max_mhz', 2070.0)} MHz",
+                    "tensor": {"algorithmic_tflops": tflops, "bf16_peak_tflops": bf16_peak,
+                               "frac": tflops / bf16_peak, "peak_source": peaks.get("source")},
+                    "hbm": {"gbs": (traffic or 0) / secs / 1e9, "peak_gbs": peaks.get("hbm_gbs")}}
+    roofline.update({"avg_launch_ms": per_launch_ms, "launches": kl})
 
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "bf16 (split hi/lo) screening, f32 refine, f64 sums",
+        "data": "synthetic",
         "config": {"workload": f"{args.workload}: n={n} d={d} k={k} l={ell:g} r={rounds} Lloyd<={max_iter}",
                    "precision": args.precision, "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 (X {n * d * 4 / 1e6:.0f} MB > 129 MB)"},
@@ -325,7 +351,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16", "bf16x3"])
     ap.add_argument("--workload", default="kdd_n1M_d42_k500")
     ap.add_argument("--n", type=int, default=0, help="override n (same recipe)")
     ap.add_argument("--ell-factor", type=float, default=0.0, help="override l as a multiple of k")

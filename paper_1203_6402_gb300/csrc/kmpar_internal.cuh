@@ -194,11 +194,11 @@ __device__ __forceinline__ double block_sum_f64(double v, double *sh /*32*/) {
 // Copies nrows rows of d floats (contiguous in global memory) into shared memory
 // with row stride ds, using nthr cooperating threads (index tid).  Each thread
 // issues eight independent loads before its stores, so a copy costs a few memory
-// latencies rather than one per element.  Row = f / d through a multiply-high by
-// ceil(2^32 / d), exact while f * d < 2^32.
+// latencies rather than one per element.  Row = f / d as (f * ceil(2^32 / d)) >> 32
+// in 64-bit arithmetic, exact while f * d < 2^32 (d = 1 included).
 __device__ __forceinline__ void stage_rows(float *dst, int ds, const float *__restrict__ src, int nrows, int d,
                                            int tid, int nthr) {
-    const uint32_t magic = 0xFFFFFFFFu / (uint32_t)d + 1u;
+    const unsigned long long magic = ((1ull << 32) + (unsigned long long)d - 1ull) / (unsigned long long)d;
     const int total = nrows * d;
     for (int f0 = tid; f0 < total; f0 += 8 * nthr) {
         float v[8];
@@ -211,7 +211,7 @@ __device__ __forceinline__ void stage_rows(float *dst, int ds, const float *__re
         for (int u = 0; u < 8; ++u) {
             const int f = f0 + u * nthr;
             if (f < total) {
-                const int r = (int)__umulhi((uint32_t)f, magic);
+                const int r = (int)(((unsigned long long)(uint32_t)f * magic) >> 32);
                 dst[r * ds + (f - r * d)] = v[u];
             }
         }

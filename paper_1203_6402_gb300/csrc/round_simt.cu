@@ -485,11 +485,36 @@ __device__ __forceinline__ void top2_merge(float &b1, int &i1, float &b2, int &i
 
 // Rows whose screening window held more than one center, finished exactly: a CTA
 // takes 8 listed rows (one warp each) and streams tiles of 64 centers through
-// shared memory (odd row stride: conflict-free); the lanes of a warp split each
-// tile's centers (exact FP32 difference form, ascending coordinates), a
-// lexicographic top-2 merge across lanes follows, then the same decision as
-// nearest_kernel.  Persistent: the row count is read on the device.
+// shared memory; the lanes of a warp split each tile's centers and sum the exact
+// FP32 difference form in ascending coordinates, reading the warp's point row
+// (broadcast) and their center rows with 8-byte loads (row stride = 2 mod 4:
+// aligned and conflict-free); a lexicographic top-2 merge across lanes follows,
+// then the same decision as nearest_kernel.  Persistent: the row count is read on
+// the device.
 constexpr int kFixTile = 64;
+
+__host__ __device__ __forceinline__ int fix_stride(int d) { return d + ((6 - (d & 3)) & 3); }   // = 2 mod 4
+
+// exact FP32 difference form over two 8-byte-aligned rows
+__device__ __forceinline__ float dist2_fp32_pairs(const float *__restrict__ x, const float *__restrict__ c, int d) {
+    const float2 *x2 = reinterpret_cast<const float2 *>(x);
+    const float2 *c2 = reinterpret_cast<const float2 *>(c);
+    float s = 0.f;
+    const int dp = d >> 1;
+#pragma unroll 4
+    for (int p = 0; p < dp; ++p) {
+        const float2 a = x2[p], b = c2[p];
+        float t = __fsub_rn(a.x, b.x);
+        s = __fmaf_rn(t, t, s);
+        t = __fsub_rn(a.y, b.y);
+        s = __fmaf_rn(t, t, s);
+    }
+    if (d & 1) {
+        const float t = __fsub_rn(x[d - 1], c[d - 1]);
+        s = __fmaf_rn(t, t, s);
+    }
+    return s;
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(256) fixup_tile_kernel(const float *__restrict__ X, int d,
@@ -498,10 +523,10 @@ __global__ void __launch_bounds__(256) fixup_tile_kernel(const float *__restrict
                                                         float *D2, int32_t *idx, int32_t *labels, const int32_t *prev,
                                                         int *changed, float *dmin, unsigned long long *fp64_cnt,
                                                         unsigned long long *wide_cnt) {
-    extern __shared__ float fsm[];
-    const int ds = d | 1;
-    float *ct = fsm;                        // kFixTile x ds center rows
-    float *xs_all = fsm + kFixTile * ds;    // 8 x ds point rows
+    extern __shared__ __align__(16) float fsm[];
+    const int ds = fix_stride(d);
+    float *ct = fsm;                       // kFixTile x ds center rows
+    float *xs_all = fsm + kFixTile * ds;   // 8 x ds point rows
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nrows = *rows_cnt;
     const int begin = MODE == MODE_ROUND ? st->batch_begin : 0;
@@ -524,7 +549,7 @@ __global__ void __launch_bounds__(256) fixup_tile_kernel(const float *__restrict
             __syncthreads();
             if (valid)
                 for (int rr = lane; rr < nt; rr += 32) {
-                    const float v = dist2_fp32(xs, ct + rr * ds, d);
+                    const float v = dist2_fp32_pairs(xs, ct + rr * ds, d);
                     const int j = begin + t0 + rr;
                     if (lex_lt(v, j, b2, i2)) {
                         if (lex_lt(v, j, b1, i1)) { b2 = b1; i2 = i1; b1 = v; i1 = j; }
@@ -586,8 +611,8 @@ __global__ void __launch_bounds__(256) fixup_tile_kernel(const float *__restrict
 // fix-up rows of a tensor pass, finished exactly on CUDA cores
 cudaError_t launch_fixup(const Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
                          int *changed, float *dmin) {
-    const int grid = c.num_sms * 4;   // persistent: the row count is only known on the device
-    const size_t sm = sizeof(float) * (size_t)(kFixTile + 8) * (c.d | 1);
+    const int grid = c.num_sms * 8;   // persistent: the row count is only known on the device
+    const size_t sm = sizeof(float) * (size_t)(kFixTile + 8) * fix_stride(c.d);
     if (mode_round)
         fixup_tile_kernel<MODE_ROUND><<<grid, 256, sm, c.stream>>>(c.X, c.d, C, 0, c.st, c.fix_rows, c.fix_cnt, c.D2,
                                                                    c.idx, nullptr, nullptr, nullptr, nullptr,
@@ -612,95 +637,127 @@ cudaError_t count_fixups(Ctx &c) {
 }
 
 // Exact FP32 distance and decision for the rows whose nearest center the tensor
-// screening made certain (cand1 >= 0).  Each warp stages its 32 point rows in
-// shared memory with coalesced loads (odd row stride: conflict-free reads), then
-// each lane sums its row against its center row (read in chunks of 8 independent
-// loads) in the exact FP32 difference form, ascending coordinates.
+// screening made certain (cand1 >= 0).  A warp takes 32 rows: asynchronous copies
+// (cp.async, no register staging) bring its 32 point rows and their 32 center rows
+// into shared memory, all in flight together; each lane then sums its own row in
+// the exact FP32 difference form, ascending coordinates, with 8-byte shared loads
+// (row stride = 2 mod 4: aligned and conflict-free).  The value is bit-identical
+// to dist2_fp32.
+__host__ __device__ __forceinline__ int refine_stride(int d) { return d + ((6 - (d & 3)) & 3); }   // = 2 mod 4
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256) refine_kernel(const float *__restrict__ X, int64_t n, int d,
                                                     const float *__restrict__ C, const int32_t *__restrict__ cand1,
                                                     float *D2, int32_t *idx, int32_t *labels, const int32_t *prev,
-                                                    int *changed, float *dmin, unsigned long long *fp64_cnt) {
-    extern __shared__ float rsm[];
-    __shared__ int redi[8];
-    const int ds = d | 1;
+                                                    int *changed, float *dmin, unsigned long long *fp64_cnt, int *) {
+    extern __shared__ __align__(16) float rsm[];
+    const int ds = refine_stride(d);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float *xs = rsm + wid * 32 * ds;
-    const int64_t w0 = (int64_t)blockIdx.x * 256 + wid * 32;
+    float *xs = rsm + wid * 64 * ds;   // 32 point rows
+    float *cs = xs + 32 * ds;          // 32 center rows
+    const int64_t w0 = (int64_t)blockIdx.x * blockDim.x + wid * 32;
     const int nw = (int)max((int64_t)0, min((int64_t)32, n - w0));
-    if (nw > 0) stage_rows(xs, ds, X + w0 * d, nw, d, lane, 32);
-    __syncwarp();
     const int64_t R = w0 + lane;
+    const int j = lane < nw ? cand1[R] : -1;
+    const bool even = (d & 1) == 0;   // rows 8-byte aligned in global memory
+    for (int rr = 0; rr < nw; ++rr) {
+        const int jr = __shfl_sync(0xffffffffu, j, rr);
+        if (jr < 0) continue;
+        const float *xr = X + (w0 + rr) * d;
+        const float *cr = C + (int64_t)jr * d;
+        if (even) {
+            for (int p = lane; p < (d >> 1); p += 32) {
+                cp_async8(xs + rr * ds + 2 * p, xr + 2 * p);
+                cp_async8(cs + rr * ds + 2 * p, cr + 2 * p);
+            }
+        } else {
+            for (int q = lane; q < d; q += 32) {
+                cp_async4(xs + rr * ds + q, xr + q);
+                cp_async4(cs + rr * ds + q, cr + q);
+            }
+        }
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
     int chg = 0;
-    if (lane < nw) {
-        const int j = cand1[R];
-        if (j >= 0) {
-            const float *xr = xs + lane * ds;
-            const float *cr = C + (int64_t)j * d;
-            float b1 = 0.f;
-            int q = 0;
-            for (; q + 8 <= d; q += 8) {
-                float cv[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) cv[u] = __ldg(cr + q + u);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const float tq = __fsub_rn(xr[q + u], cv[u]);
-                    b1 = __fmaf_rn(tq, tq, b1);
-                }
+    if (lane < nw && j >= 0) {
+        const float *xa = xs + lane * ds, *ca = cs + lane * ds;
+        const float2 *x2 = reinterpret_cast<const float2 *>(xa);
+        const float2 *c2 = reinterpret_cast<const float2 *>(ca);
+        float b1 = 0.f;
+#pragma unroll 4
+        for (int p = 0; p < (d >> 1); ++p) {
+            const float2 a = x2[p], b = c2[p];
+            float t = __fsub_rn(a.x, b.x);
+            b1 = __fmaf_rn(t, t, b1);
+            t = __fsub_rn(a.y, b.y);
+            b1 = __fmaf_rn(t, t, b1);
+        }
+        if (d & 1) {
+            const float t = __fsub_rn(xa[d - 1], ca[d - 1]);
+            b1 = __fmaf_rn(t, t, b1);
+        }
+        const float *cr = C + (int64_t)j * d;
+        if (MODE == MODE_ROUND) {
+            const float old = D2[R];
+            const int oi = idx[R];
+            const float W = fp32_tie_window(d);
+            const float m32 = fminf(old, b1);
+            const float lim = m32 + W * m32;
+            if (old <= lim && b1 <= lim) {
+                const float *xg = X + R * d;
+                const double dold = dist2_fp64(xg, C + (int64_t)oi * d, d);
+                const double dnew = dist2_fp64(xg, cr, d);
+                atomicAdd(fp64_cnt, 1ull);
+                if (dnew < dold || (dnew == dold && j < oi)) { D2[R] = b1; idx[R] = j; }
+            } else if (b1 < old) {
+                D2[R] = b1;
+                idx[R] = j;
             }
-            for (; q < d; ++q) {
-                const float tq = __fsub_rn(xr[q], __ldg(cr + q));
-                b1 = __fmaf_rn(tq, tq, b1);
-            }
-            if (MODE == MODE_ROUND) {
-                const float old = D2[R];
-                const int oi = idx[R];
-                const float W = fp32_tie_window(d);
-                const float m32 = fminf(old, b1);
-                const float lim = m32 + W * m32;
-                if (old <= lim && b1 <= lim) {
-                    const float *xg = X + R * d;
-                    const double dold = dist2_fp64(xg, C + (int64_t)oi * d, d);
-                    const double dnew = dist2_fp64(xg, cr, d);
-                    atomicAdd(fp64_cnt, 1ull);
-                    if (dnew < dold || (dnew == dold && j < oi)) { D2[R] = b1; idx[R] = j; }
-                } else if (b1 < old) {
-                    D2[R] = b1;
-                    idx[R] = j;
-                }
-            } else {
-                if (labels) labels[R] = j;
-                dmin[R] = b1;
-                if (prev) chg = prev[R] != j;
-            }
+        } else {
+            if (labels) labels[R] = j;
+            dmin[R] = b1;
+            if (prev) chg = prev[R] != j;
         }
     }
     if (MODE == MODE_ASSIGN && changed) {
         const int c = warp_sum_i32(chg);
-        if (lane == 0) redi[wid] = c;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int tot = 0;
-            for (int i = 0; i < 8; ++i) tot += redi[i];
-            if (tot) atomicAdd(changed, tot);
-        }
+        if (lane == 0 && c) atomicAdd(changed, c);
     }
 }
 
+// warps per refine CTA: 64 staged rows of refine_stride(d) floats each, within 200 KB
+int refine_warps(int d) {
+    const int w = (int)((200u * 1024u) / (64u * 4u * (unsigned)refine_stride(d)));
+    return w > 8 ? 8 : (w < 1 ? 1 : w);
+}
+
+size_t refine_smem_bytes(int d) { return sizeof(float) * refine_warps(d) * 64 * (size_t)refine_stride(d); }
+
 cudaError_t configure_refine_kernels() {
-    // 256 staged rows of up to 191 floats (the tensor passes support d + 2 <= 192)
-    cudaError_t er = cudaFuncSetAttribute(refine_kernel<MODE_ROUND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          200 * 1024);
-    if (er != cudaSuccess) return er;
-    er = cudaFuncSetAttribute(refine_kernel<MODE_ASSIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (er != cudaSuccess) return er;
-    const int bytes = (kFixTile + 8) * 4097 * 4;
-    cudaError_t e = cudaFuncSetAttribute(fixup_tile_kernel<MODE_ROUND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         std::min(bytes, 200 * 1024));
+    // the tensor passes support d + 2 <= 192: refine tiles of 256 rows of up to 190 floats
+    cudaError_t e = cudaFuncSetAttribute(refine_kernel<MODE_ROUND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(refine_kernel<MODE_ASSIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fixup_tile_kernel<MODE_ROUND>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(fixup_tile_kernel<MODE_ASSIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                std::min(bytes, 200 * 1024));
+                                64 * 1024);
 }
 
 cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
@@ -723,14 +780,16 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
     if ((e = timing_begin(c, &ev)) != cudaSuccess) return e;
     if ((e = tc::launch_nearest_tc(p, mode_round, c.num_sms, c.stream)) != cudaSuccess) return e;
     if ((e = timing_end(c, ev, timing_cls)) != cudaSuccess) return e;
-    const int grid = (int)((c.n + 255) / 256);
-    const size_t rsm = sizeof(float) * 256 * (size_t)(c.d | 1);
+    const int rthreads = 32 * refine_warps(c.d);
+    const int grid = (int)((c.n + rthreads - 1) / rthreads);
+    const size_t rsm = refine_smem_bytes(c.d);
     if (mode_round)
-        refine_kernel<MODE_ROUND><<<grid, 256, rsm, c.stream>>>(c.X, c.n, c.d, C, c.cand1, c.D2, c.idx, nullptr,
-                                                               nullptr, nullptr, nullptr, &c.st->argmin_fp64);
+        refine_kernel<MODE_ROUND><<<grid, rthreads, rsm, c.stream>>>(c.X, c.n, c.d, C, c.cand1, c.D2, c.idx, nullptr,
+                                                                nullptr, nullptr, nullptr, &c.st->argmin_fp64,
+                                                                c.tc_err);
     else
-        refine_kernel<MODE_ASSIGN><<<grid, 256, rsm, c.stream>>>(c.X, c.n, c.d, C, c.cand1, nullptr, nullptr, labels,
-                                                                prev, changed, dmin, &c.st->argmin_fp64);
+        refine_kernel<MODE_ASSIGN><<<grid, rthreads, rsm, c.stream>>>(c.X, c.n, c.d, C, c.cand1, nullptr, nullptr, labels,
+                                                                 prev, changed, dmin, &c.st->argmin_fp64, c.tc_err);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = count_fixups(c)) != cudaSuccess) return e;

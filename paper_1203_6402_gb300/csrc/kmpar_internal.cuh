@@ -81,11 +81,14 @@ struct Ctx {
     // tensor-core screening (BF16 modes)
     uint8_t *tc_img = nullptr;    // swizzled BF16 center tiles
     uint8_t *tc_ximg = nullptr;   // swizzled BF16 image of X (built once per context)
-    float *tc_xnorm = nullptr;    // ||x||^2 per point
-    float *tc_cnorm = nullptr;    // ||c|| per padded center row
+    float *tc_xnorm = nullptr;    // ||x'||^2 per point (x' = x - anchor)
+    float *tc_anchor = nullptr;   // d column means of X
+    double *tc_anchor_part = nullptr;   // per-block column sums behind the anchor
+    float *tc_cnorm = nullptr;    // ||c'|| per padded center row
     unsigned int *tc_cmax = nullptr;
     int *tc_err = nullptr;        // first timeout code of a tensor pass
-    int32_t *cand1 = nullptr;     // per row: certain nearest center of the last tensor pass, or -1
+    int32_t *cand1 = nullptr;     // per row: best screened center of the last tensor pass, or -1
+    float *tc_v1 = nullptr, *tc_v2 = nullptr;   // per row: best and runner-up screened values
     int32_t *fix_rows = nullptr;  // rows left to the exact CUDA-core pass
     int *fix_cnt = nullptr;
     float *dmin = nullptr;        // Lloyd: exact d^2 of each point's chosen center

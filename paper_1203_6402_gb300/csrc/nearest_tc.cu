@@ -1,31 +1,35 @@
 // nearest_tc.cu -- the distance passes of k-means|| (Alg. 2 step 5, Sec. 3.3) and
 // of Lloyd's assignment (Sec. 3.1) on the tcgen05 tensor cores of sm_103a.
 //
-// Screening: for a 128-row tile of X and a BN-column tile of centers, one
-// tcgen05.mma chain (BF16 inputs, FP32 accumulator in TMEM) produces
-//     s~(x, c) = ||c||^2 - 2 x.c        (= d^2(x, c) - ||x||^2)
-// with ||c||^2 folded into two extra K columns (A row: [x..., 1, 1], B row:
-// [-2c..., cn_hi, cn_lo]).  In split mode every coordinate is carried as hi + lo
+// Screening: distances are translation invariant, so both operands are first
+// moved by a fixed anchor a (the column means of X, computed once per context):
+// x' = x - a, c' = c - a.  For a 128-row tile of X and a BN-column tile of
+// centers, one tcgen05.mma chain (BF16 inputs, FP32 accumulator in TMEM) produces
+//     s~(x, c) = ||c'||^2 - 2 x'.c'        (= d^2(x, c) - ||x'||^2)
+// with ||c'||^2 folded into two extra K columns (A row: [x'..., 1, 1], B row:
+// [-2c'..., cn_hi, cn_lo]).  In split mode every coordinate is carried as hi + lo
 // BF16 parts and three products (hi.hi, lo.hi, hi.lo) are summed, which brings the
-// screening error from ~2^-6 to ~2^-13 of ||x|| ||c||.
+// screening error from ~2^-6 to ~2^-13 of ||x'|| ||c'||; the anchor makes those
+// norms, and so the error, smaller for data away from the origin.
 //
-// Epilogue (8 warps, one TMEM lane per row, two warps per lane quarter): each
-// value becomes a key whose low 8 mantissa bits hold its column; a branch-free
-// top-2 over the keys gives the best center and the runner-up value.  If the
-// runner-up is outside the screening error window the best center is certain and
-// is written out; the exact FP32 distance and the decision are then taken by
-// refine_kernel exactly as on the CUDA-core path.  Otherwise the row goes to a
-// fix-up list that the CUDA-core kernel finishes with an exact scan.  Decisions
-// are therefore identical to the FP32 path.
+// Epilogue (16 warps, one TMEM lane per row, four warps per lane quarter, each on
+// its own column group): each value becomes a key whose low 6 mantissa bits hold
+// its column within the group (a compile-time constant: one logic op per value);
+// a branch-free top-2 over the keys gives the best center and the runner-up
+// value, written out per row.  refine_kernel then tests the runner-up against the screening error
+// window: a certain best center gets its exact FP32 distance and the decision is
+// taken exactly as on the CUDA-core path; otherwise the row goes to a fix-up list
+// that the CUDA-core kernel finishes with an exact scan.  Decisions are therefore
+// identical to the FP32 path.
 //
 // The A operand (points) is encoded once per context by prep_points_kernel into a
 // swizzled BF16 image of X (one contiguous block per 128-row tile) together with
 // ||x||^2; the B operand (centers) is encoded per pass by prep_centers_kernel.
 //
-// CTA roles (persistent, one CTA per SM, 320 threads):
+// CTA roles (persistent, one CTA per SM, 576 threads):
 //   warp 0      producer: bulk copies of A and B tiles into smem
 //   warp 1      TMEM allocation, MMA issue (one lane)
-//   warps 2-9   epilogue
+//   warps 2-17  epilogue
 // Every wait is bounded; on a timeout the kernel raises an error word, unwinds,
 // waits (bounded) for its own copies and MMAs and frees its TMEM.
 #include <cuda_bf16.h>
@@ -37,7 +41,10 @@
 namespace kmp {
 namespace tc {
 
-constexpr int kThreads = 320;
+constexpr int kEpiWarps = 16;                    // epilogue warps (4 per TMEM lane quarter)
+constexpr int kThreads = 64 + 32 * kEpiWarps;   // + producer warp + MMA warp
+constexpr int kGroups = kEpiWarps / 4;          // column groups per center tile
+constexpr int kPrefetch = 3;                    // A tiles pulled into L2 ahead of the current one
 constexpr int BM = 128;
 constexpr unsigned long long kWaitCycles = 4000000000ull;   // ~2 s at 2 GHz
 
@@ -69,6 +76,9 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                      su32(dst)),
                  "l"(src), "r"(bytes), "r"(su32(bar))
                  : "memory");
+}
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
@@ -130,22 +140,29 @@ __host__ __device__ __forceinline__ uint32_t sw128_off(int r, int c) {
 // ------------------------------------------------------------------ operand encoding
 struct Enc {
     int d;
-    int split;   // 0: [x, 1, 1]; 1: [x_hi, x_lo, x_hi, 1, 1]
+    int split;        // 0: [x', 1, 1]; 1: [x'_hi, x'_lo, x'_hi, 1, 1]
+    const float *a;   // anchor: x' = fl(x - a), c' = fl(c - a)
 };
+
+// mask of a key's value bits; the low kColBits mantissa bits carry a column
+constexpr int kColBits = 6;
+constexpr uint32_t kValMask = ~((1u << kColBits) - 1u);
 
 __device__ __forceinline__ __nv_bfloat16 bf(float v) { return __float2bfloat16_rn(v); }
 
 // element k of the A (point) row
+__device__ __forceinline__ float moved(const Enc &e, const float *x, int q) { return __fsub_rn(x[q], e.a[q]); }
+
 __device__ __forceinline__ __nv_bfloat16 a_elem(const Enc &e, const float *x, int k) {
     const int d = e.d;
     if (!e.split) {
-        if (k < d) return bf(x[k]);
+        if (k < d) return bf(moved(e, x, k));
         if (k == d || k == d + 1) return bf(1.f);
         return bf(0.f);
     }
-    if (k < d) return bf(x[k]);
-    if (k < 2 * d) { const float v = x[k - d]; return bf(v - __bfloat162float(bf(v))); }
-    if (k < 3 * d) return bf(x[k - 2 * d]);
+    if (k < d) return bf(moved(e, x, k));
+    if (k < 2 * d) { const float v = moved(e, x, k - d); return bf(v - __bfloat162float(bf(v))); }
+    if (k < 3 * d) return bf(moved(e, x, k - 2 * d));
     if (k == 3 * d || k == 3 * d + 1) return bf(1.f);
     return bf(0.f);
 }
@@ -158,13 +175,13 @@ __device__ __forceinline__ __nv_bfloat16 b_elem(const Enc &e, const float *c, fl
     const int base = e.split ? 3 * d : d;
     if (pad) return k == base ? bf(1e30f) : bf(0.f);
     if (!e.split) {
-        if (k < d) return bf(-2.f * c[k]);
+        if (k < d) return bf(-2.f * moved(e, c, k));
         if (k == d) return bf(cn_hi);
         if (k == d + 1) return bf(cn_lo);
         return bf(0.f);
     }
-    if (k < 2 * d) return bf(-2.f * c[k < d ? k : k - d]);
-    if (k < 3 * d) { const float v = c[k - 2 * d]; return bf(-2.f * (v - __bfloat162float(bf(v)))); }
+    if (k < 2 * d) return bf(-2.f * moved(e, c, k < d ? k : k - d));
+    if (k < 3 * d) { const float v = moved(e, c, k - 2 * d); return bf(-2.f * (v - __bfloat162float(bf(v)))); }
     if (k == 3 * d) return bf(cn_hi);
     if (k == 3 * d + 1) return bf(cn_lo);
     return bf(0.f);
@@ -180,22 +197,25 @@ __device__ __forceinline__ uint4 pack8(const __nv_bfloat16 (&v)[8]) {
 }
 
 // ------------------------------------------------------------------ center tiles
-// One thread per padded center row: squared norm (FP32, ascending), ||c||, the
-// running max of ||c|| and the row's KA x 8 swizzled chunks of the B image
-// [tile][katom][BN rows][128 B].
+// One thread per padded center row: ||c'||^2 (FP32, ascending), ||c'||, the
+// running max of ||c'|| and the row's KA x 8 swizzled chunks of the B image
+// [tile][katom][BN rows][128 B]  (c' = c - anchor).
 __global__ void prep_centers_kernel(const float *__restrict__ C, int d, int split, int KA, int BN, const DevState *st,
-                                    int cnt_static, int round_mode, uint8_t *__restrict__ img, float *cnorm,
-                                    unsigned int *cmax_bits) {
+                                    int cnt_static, int round_mode, const float *__restrict__ anchor,
+                                    uint8_t *__restrict__ img, float *cnorm, unsigned int *cmax_bits) {
     const int begin = round_mode ? st->batch_begin : 0;
     const int cnt = round_mode ? st->batch_cnt : cnt_static;
     const int rows = ((cnt + BN - 1) / BN) * BN;
-    const Enc e{d, split};
+    const Enc e{d, split, anchor};
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < rows; j += gridDim.x * blockDim.x) {
         const bool pad = j >= cnt;
         const float *c = C + (int64_t)(begin + (pad ? 0 : j)) * d;
         float cn = 0.f;
         if (!pad) {
-            for (int q = 0; q < d; ++q) cn = __fmaf_rn(c[q], c[q], cn);
+            for (int q = 0; q < d; ++q) {
+                const float v = moved(e, c, q);
+                cn = __fmaf_rn(v, v, cn);
+            }
             const float nrm = sqrtf(cn);
             cnorm[j] = nrm;
             atomicMax(cmax_bits, __float_as_uint(nrm));
@@ -215,17 +235,22 @@ __global__ void prep_centers_kernel(const float *__restrict__ C, int d, int spli
     }
 }
 
-// One thread per (padded) point row: ||x||^2 (FP32, ascending) and the row's
-// KA x 8 swizzled chunks of the A image [row tile][katom][128 rows][128 B].
+// One thread per (padded) point row: ||x'||^2 (FP32, ascending) and the row's
+// KA x 8 swizzled chunks of the A image [row tile][katom][128 rows][128 B]
+// (x' = x - anchor).
 __global__ void prep_points_kernel(const float *__restrict__ X, int64_t n, int64_t n_pad, int d, int split, int KA,
-                                   uint8_t *__restrict__ img, float *__restrict__ xnorm) {
-    const Enc e{d, split};
+                                   const float *__restrict__ anchor, uint8_t *__restrict__ img,
+                                   float *__restrict__ xnorm) {
+    const Enc e{d, split, anchor};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x) {
         const bool valid = i < n;
         const float *x = X + (valid ? i : 0) * (int64_t)d;
         float xn = 0.f;
         if (valid)
-            for (int q = 0; q < d; ++q) xn = __fmaf_rn(x[q], x[q], xn);
+            for (int q = 0; q < d; ++q) {
+                const float v = moved(e, x, q);
+                xn = __fmaf_rn(v, v, xn);
+            }
         xnorm[i] = xn;
         const int64_t t = i / BM;
         const int r = (int)(i % BM);
@@ -241,6 +266,36 @@ __global__ void prep_points_kernel(const float *__restrict__ X, int64_t n, int64
     }
 }
 
+// ------------------------------------------------------------------ anchor
+// Column means of X, the anchor both operands are moved by.  Any anchor gives the
+// same decisions (distances do not depend on it); the mean keeps ||x'|| small.
+// Fixed row chunks per block and a fixed summation order make it deterministic.
+constexpr int kAnchorBlocks = 256;
+
+__global__ void anchor_partial_kernel(const float *__restrict__ X, int64_t n, int d, double *__restrict__ part) {
+    const int64_t chunk = (n + kAnchorBlocks - 1) / kAnchorBlocks;
+    const int64_t r0 = (int64_t)blockIdx.x * chunk;
+    const int64_t r1 = min(n, r0 + chunk);
+    for (int q = threadIdx.x; q < d; q += blockDim.x) {
+        double s0 = 0.0, s1 = 0.0;
+        int64_t r = r0;
+        for (; r + 1 < r1; r += 2) {
+            s0 += (double)X[r * d + q];
+            s1 += (double)X[(r + 1) * d + q];
+        }
+        if (r < r1) s0 += (double)X[r * d + q];
+        part[(size_t)blockIdx.x * d + q] = s0 + s1;
+    }
+}
+
+__global__ void anchor_final_kernel(const double *__restrict__ part, int64_t n, int d, float *__restrict__ anchor) {
+    for (int q = threadIdx.x; q < d; q += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < kAnchorBlocks; ++b) s += part[(size_t)b * d + q];
+        anchor[q] = n > 0 ? (float)(s / (double)n) : 0.f;
+    }
+}
+
 // ------------------------------------------------------------------ the pass
 struct Smem {
     uint64_t a_full[4], a_free[4];
@@ -249,17 +304,18 @@ struct Smem {
     uint64_t merge_full[2], merge_free[2];
     uint32_t tmem_base;
     int abort;
-    float merge_k1[2][BM];
-    float merge_k2[2][BM];
-    int merge_t1[2][BM];
+    float merge_k1[2][kGroups - 1][BM];
+    float merge_k2[2][kGroups - 1][BM];
+    int merge_t1[2][kGroups - 1][BM];
 };
 
 template <int KA, int BN>
 struct Cfg {
     static constexpr int A16_BYTES = KA * BM * 128;
     static constexpr int B_BYTES = KA * BN * 128;
-    static constexpr int HALF = BN / 2;
-    static constexpr int CHUNKS = HALF / 32;
+    static constexpr int GW = BN / kGroups;   // columns per epilogue warp
+    static constexpr int CHUNKS = GW / 32;
+    static_assert(GW <= (1 << kColBits) && GW % 32 == 0, "column field");
 };
 
 struct Bound {
@@ -318,8 +374,8 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p) {
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&sm.acc_full[i], 1);
-            mbar_init(&sm.acc_empty[i], 8);
-            mbar_init(&sm.merge_full[i], 4);
+            mbar_init(&sm.acc_empty[i], kEpiWarps);
+            mbar_init(&sm.merge_full[i], 4 * (kGroups - 1));
             mbar_init(&sm.merge_free[i], 4);
         }
         for (int i = 0; i < S; ++i) {
@@ -344,8 +400,15 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p) {
                     mbar_expect_tx(&sm.b_full[t], C::B_BYTES);
                     bulk_g2s(bst + t * C::B_BYTES, p.bimg + (size_t)t * C::B_BYTES, C::B_BYTES, &sm.b_full[t]);
                 }
+            // the A tiles of the next row tiles are pulled into L2 ahead of their copies
+            for (int q = 1; q <= kPrefetch; ++q) {
+                const int64_t rq = blockIdx.x + (int64_t)q * gridDim.x;
+                if (rq < nrt) prefetch_l2(p.ximg + (size_t)rq * C::A16_BYTES, C::A16_BYTES);
+            }
             for (int rt = blockIdx.x; rt < nrt; rt += gridDim.x, ++lt) {
                 const int ab = lt % A16B;
+                const int64_t rq = rt + (int64_t)(kPrefetch + 1) * gridDim.x;
+                if (rq < nrt) prefetch_l2(p.ximg + (size_t)rq * C::A16_BYTES, C::A16_BYTES);
                 if (lt >= A16B && !wait_bar(&sm.a_free[ab], ((lt - A16B) / A16B) & 1, abort, p.err, 11)) break;
                 mbar_expect_tx(&sm.a_full[ab], C::A16_BYTES);
                 bulk_g2s(a16 + ab * C::A16_BYTES, p.ximg + (size_t)rt * C::A16_BYTES, C::A16_BYTES, &sm.a_full[ab]);
@@ -402,14 +465,15 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p) {
             if (g > 0) drain_bar(&sm.acc_full[(g - 1) & 1], ((g - 1) >> 1) & 1);
         }
     } else if (cnt > 0) {
-        // ------------------------------------------------ epilogue (warps 2-9)
-        const int e = warp - 2;               // 0..7
+        // ------------------------------------------------ epilogue (warps 2 .. 2+kEpiWarps-1)
+        const int e = warp - 2;
         const int quarter = warp & 3;         // TMEM lane quarter this warp may read
-        const int half = e >> 2;              // column half of each center tile
+        const int grp = e >> 2;               // column group of each center tile
         const int row = quarter * 32 + lane;  // row within the tile
-        const Bound bnd{p.ep, p.en};
-        const float cmax = __uint_as_float(*p.cmax_bits);
         const float INF = __uint_as_float(0x7F800000u);
+        // kValMask as a runtime value: held in a register, the column is then the
+        // one immediate of a single logic op per key
+        const uint32_t vmask = p.vmask;
         int lt = 0, g = 0;
         for (int rt = blockIdx.x; rt < nrt; rt += gridDim.x, ++lt) {
             const int mb = lt & 1;
@@ -420,79 +484,88 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p) {
                 const int buf = g & 1;
                 if (!wait_bar(&sm.acc_full[buf], (g >> 1) & 1, abort, p.err, 18)) { ok = false; break; }
                 tc_fence_after();
-                float k1 = INF, k2 = INF;
-                const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + half * C::HALF);
+                // two independent top-2 chains (alternate column pairs), merged per tile
+                float k1a = INF, k2a = INF, k1b = INF, k2b = INF;
+                const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + grp * C::GW);
 #pragma unroll
-                for (int c = 0; c < C::CHUNKS; ++c) {
-                    uint32_t r[32];
-                    tmem_ld32(tbase + c * 32, r);
+                for (int c = 0; c < C::CHUNKS; c += 2) {
+                    uint32_t r[2][32];
+                    tmem_ld32(tbase + c * 32, r[0]);
+                    if (c + 1 < C::CHUNKS) tmem_ld32(tbase + (c + 1) * 32, r[1]);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int q = 0; q < 32; q += 2) {
-                        // key = value with its column in the low 8 mantissa bits
-                        const uint32_t col = (uint32_t)(half * C::HALF + c * 32 + q);
-                        const float a = __uint_as_float((r[q] & 0xFFFFFF00u) | col);
-                        const float b = __uint_as_float((r[q + 1] & 0xFFFFFF00u) | (col + 1));
-                        const float lo = fminf(a, b), hi = fmaxf(a, b);
-                        k2 = min3f(fmaxf(k1, lo), k2, hi);
-                        k1 = fminf(k1, lo);
+                    for (int cc = 0; cc < 2; ++cc) {
+                        if (c + cc >= C::CHUNKS) break;
+#pragma unroll
+                        for (int q = 0; q < 32; q += 4) {
+                            // key = value with its column within the group in the low
+                            // mantissa bits (col is a compile-time constant)
+                            const uint32_t col = (uint32_t)((c + cc) * 32 + q);
+                            const float a = __uint_as_float((r[cc][q] & vmask) | col);
+                            const float b = __uint_as_float((r[cc][q + 1] & vmask) | (col + 1));
+                            const float e = __uint_as_float((r[cc][q + 2] & vmask) | (col + 2));
+                            const float f = __uint_as_float((r[cc][q + 3] & vmask) | (col + 3));
+                            const float loa = fminf(a, b), hia = fmaxf(a, b);
+                            const float lob = fminf(e, f), hib = fmaxf(e, f);
+                            k2a = min3f(fmaxf(k1a, loa), k2a, hia);
+                            k1a = fminf(k1a, loa);
+                            k2b = min3f(fmaxf(k1b, lob), k2b, hib);
+                            k1b = fminf(k1b, lob);
+                        }
                     }
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm.acc_empty[buf]);
+                const float k1 = fminf(k1a, k1b);
+                const float k2 = min3f(fmaxf(k1a, k1b), k2a, k2b);
                 if (k1 < K1) { K2 = fminf(K1, k2); K1 = k1; T1 = t; }
                 else K2 = min3f(K2, k1, k2);
             }
             if (!ok) break;
-            // merge the two column halves through shared memory (bounded waits only)
-            if (half == 1) {
+            // merge the column groups through shared memory (bounded waits only)
+            if (grp > 0) {
                 if (lt >= 2 && !wait_bar(&sm.merge_free[mb], ((lt - 2) >> 1) & 1, abort, p.err, 19)) break;
-                sm.merge_k1[mb][row] = K1;
-                sm.merge_k2[mb][row] = K2;
-                sm.merge_t1[mb][row] = T1;
+                sm.merge_k1[mb][grp - 1][row] = K1;
+                sm.merge_k2[mb][grp - 1][row] = K2;
+                sm.merge_t1[mb][grp - 1][row] = T1;
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm.merge_full[mb]);
                 continue;
             }
             if (!wait_bar(&sm.merge_full[mb], (lt >> 1) & 1, abort, p.err, 20)) break;
+            int J1;
             {
-                const float o1 = sm.merge_k1[mb][row], o2 = sm.merge_k2[mb][row];
-                const int ot = sm.merge_t1[mb][row];
+                float o1[kGroups - 1], o2[kGroups - 1];
+                int ot[kGroups - 1];
+#pragma unroll
+                for (int q = 0; q < kGroups - 1; ++q) {
+                    o1[q] = sm.merge_k1[mb][q][row];
+                    o2[q] = sm.merge_k2[mb][q][row];
+                    ot[q] = sm.merge_t1[mb][q][row];
+                }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm.merge_free[mb]);
-                const float m1v = __uint_as_float(__float_as_uint(o1) & 0xFFFFFF00u);
-                const float k1v = __uint_as_float(__float_as_uint(K1) & 0xFFFFFF00u);
-                if (m1v < k1v || (m1v == k1v && ot < T1)) { K2 = min3f(K1, o2, K2); K1 = o1; T1 = ot; }
-                else K2 = min3f(K2, o1, o2);
+                // (masked value, center number) order; equal masked values of different
+                // centers are near ties that the window test sends to the fix-up anyway.
+                // Group 0's columns start at 0 within the tile, group q+1's at (q+1) GW.
+                J1 = T1 * BN + (int)(__float_as_uint(K1) & ~kValMask);
+#pragma unroll
+                for (int q = 0; q < kGroups - 1; ++q) {
+                    const float m1v = __uint_as_float(__float_as_uint(o1[q]) & kValMask);
+                    const float k1v = __uint_as_float(__float_as_uint(K1) & kValMask);
+                    const int oj = ot[q] * BN + (q + 1) * C::GW + (int)(__float_as_uint(o1[q]) & ~kValMask);
+                    if (m1v < k1v || (m1v == k1v && oj < J1)) { K2 = min3f(K1, o2[q], K2); K1 = o1[q]; J1 = oj; }
+                    else K2 = min3f(K2, o1[q], o2[q]);
+                }
             }
-            // ---- certain winner -> refine_kernel; otherwise the row goes to the fix-up pass
+            // ---- the best center and the two screened values; refine_kernel decides
+            // whether the best is certain (it hides the latency of the norm lookups)
             const int64_t R = (int64_t)rt * BM + row;
             if (R < n) {
-                const int jl = T1 * BN + (int)(__float_as_uint(K1) & 0xFFu);
-                const float v1 = __uint_as_float(__float_as_uint(K1) & 0xFFFFFF00u);
-                const float v2 = __uint_as_float(__float_as_uint(K2) & 0xFFFFFF00u);
-                bool single = false;
-                if (jl < cnt) {
-                    const float xn = fmaxf(p.xnorm[R], 0.f);
-                    const float X = sqrtf(xn);
-                    const float E1 = err_bound(bnd, X, p.cnorm[jl]);
-                    const float slack1 = fabsf(v1) * 6.2e-5f + E1;   // + key truncation (2^-15 relative)
-                    const float d1 = fmaxf(v1 + xn + slack1, 0.f);   // bound on the winner's d^2
-                    const float ceff = fminf(cmax, X + sqrtf(d1));
-                    const float Eo = err_bound(bnd, X, ceff);
-                    const float W = fp32_tie_window(p.d);
-                    // v2 lowered by its key truncation; stays +inf when there is no runner-up
-                    const float v2lo = v2 >= 0.f ? v2 * (1.f - 6.2e-5f) : v2 * (1.f + 6.2e-5f);
-                    single = (v2lo - Eo) > (v1 + slack1 + W * d1 + 1e-30f);
-                }
-                if (single) {
-                    p.cand1[R] = begin + jl;
-                } else {
-                    p.cand1[R] = -1;
-                    const int pos = atomicAdd(p.fix_cnt, 1);
-                    p.fix_rows[pos] = (int32_t)R;
-                }
+                p.cand1[R] = J1 < cnt ? begin + J1 : -1;
+                p.v1[R] = __uint_as_float(__float_as_uint(K1) & kValMask);
+                p.v2[R] = __uint_as_float(__float_as_uint(K2) & kValMask);
             }
         }
     }
@@ -552,11 +625,20 @@ size_t tc_points_image_bytes(int d, int split, int64_t n) {
     return (size_t)tiles * tc_katoms(d, split) * BM * 128;
 }
 
-cudaError_t launch_prep_points(const float *X, int64_t n, int d, int split, uint8_t *img, float *xnorm,
-                               cudaStream_t s) {
+size_t tc_anchor_scratch_doubles(int d) { return (size_t)kAnchorBlocks * d; }
+
+cudaError_t launch_anchor(const float *X, int64_t n, int d, double *scratch, float *anchor, cudaStream_t s) {
+    anchor_partial_kernel<<<kAnchorBlocks, 64, 0, s>>>(X, n, d, scratch);
+    anchor_final_kernel<<<1, 128, 0, s>>>(scratch, n, d, anchor);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_points(const float *X, int64_t n, int d, int split, const float *anchor, uint8_t *img,
+                               float *xnorm, cudaStream_t s) {
     const int64_t n_pad = ((n + BM - 1) / BM) * BM;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n_pad + 127) / 128, 8192));
-    prep_points_kernel<<<grid, 128, 0, s>>>(X, n, n_pad, d, split, tc_katoms(d, split), img, xnorm);
+    prep_points_kernel<<<grid, 128, 0, s>>>(X, n, n_pad, d, split, tc_katoms(d, split), anchor, img, xnorm);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -569,27 +651,37 @@ Bound make_bound(int d, int split) {
     const double norm = u * u + (d + 2) * std::ldexp(1.0, -24);   // hi/lo split of ||c||^2 + its FP32 sum
     double ep = split ? 2.0 * (3.0 * u * u + 3.0 * u * u * u) : 2.0 * (2.0 * u + u * u);
     ep = 1.25 * (ep + 2.0 * acc * 1.1);
-    const double en = 1.25 * (norm + acc);
+    // x' = fl(x - a), c' = fl(c - a) move each coordinate by at most 2^-24 of its
+    // size, so d(x', c') is within 2^-24 (||x'|| + ||c'||) of d(x, c) and d^2
+    // within 2^-22 (||x'||^2 + ||c'||^2)
+    const double move = std::ldexp(1.0, -22);
+    const double en = 1.25 * (norm + acc + move);
     return Bound{(float)ep, (float)en};
 }
 
 cudaError_t launch_prep_centers(const float *C, int d, int split, const DevState *st, int cnt_static, int round_mode,
-                                int cap_rows, uint8_t *img, float *cnorm, unsigned int *cmax_bits, cudaStream_t s) {
+                                int cap_rows, const float *anchor, uint8_t *img, float *cnorm, unsigned int *cmax_bits,
+                                cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(cmax_bits, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     const int KA = tc_katoms(d, split), BN = tc_block_n(d, split);
     const int rows = ((cap_rows + BN - 1) / BN) * BN;
     const int grid = std::max(1, std::min((rows + 127) / 128, 4096));
-    prep_centers_kernel<<<grid, 128, 0, s>>>(C, d, split, KA, BN, st, cnt_static, round_mode, img, cnorm, cmax_bits);
+    prep_centers_kernel<<<grid, 128, 0, s>>>(C, d, split, KA, BN, st, cnt_static, round_mode, anchor, img, cnorm,
+                                             cmax_bits);
     count_launches(1);
     return cudaGetLastError();
 }
 
+void tc_bound(int d, int split, float *ep, float *en) {
+    const Bound b = make_bound(d, split);
+    *ep = b.ep;
+    *en = b.en;
+}
+
 cudaError_t launch_nearest_tc(TcParams p, int mode_round, int num_sms, cudaStream_t s) {
-    const Bound b = make_bound(p.d, p.split);
-    p.ep = b.ep;
-    p.en = b.en;
     p.ksteps = tc_ksteps(p.d, p.split);
+    p.vmask = kValMask;
     const int KA = tc_katoms(p.d, p.split);
     const int rows = (int)((p.n + BM - 1) / BM);
     const int grid = std::max(1, std::min(rows, num_sms));

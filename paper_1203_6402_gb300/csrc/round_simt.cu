@@ -658,11 +658,97 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
                  : "memory");
 }
 
+// The screening window test (the runner-up must be out of reach of the best once
+// the screening error E(x, c) = ep ||x'|| ||c'|| + en (||x'||^2 + ||c'||^2) and the
+// 2^-17 key truncation are allowed for; centers other than the best are bounded
+// by min(max ||c'||, ||x'|| + sqrt(d^2 bound of the best)) through the triangle
+// inequality, all norms taken after the anchor move) decides whether the best
+// center is certain; other rows go to the fix-up list.
+struct ScreenBound {
+    const float *xnorm;            // ||x'||^2 per point (x' = x - anchor)
+    const float *cnorm;            // ||c'|| per center of the batch (local number)
+    const unsigned int *cmax_bits; // max ||c'|| of the batch
+    const DevState *st;            // ROUND: batch begin
+    float ep, en;
+    int32_t *fix_rows;
+    int *fix_cnt;
+};
+
+// rows whose screening is not certain go to the fix-up list: one atomic per warp
+__device__ __forceinline__ void append_fixups(const ScreenBound &sb, bool fix, int64_t R) {
+    const unsigned m = __ballot_sync(0xffffffffu, fix);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(sb.fix_cnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (fix) sb.fix_rows[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)R;
+}
+
+// screened values arrive with their low 6 mantissa bits cleared (relative change
+// below 2^-17); twice that is allowed for
+constexpr float kKeyTrunc = 1.6e-5f;
+
+__device__ __forceinline__ bool screen_certain(const ScreenBound &sb, float xnorm, int jloc, float v1, float v2,
+                                               int d) {
+    const float xn = fmaxf(xnorm, 0.f);
+    const float X = sqrtf(xn);
+    const float cmax = __uint_as_float(*sb.cmax_bits);
+    const float c1 = sb.cnorm[jloc];
+    const float E1 = sb.ep * X * c1 + sb.en * (xn + c1 * c1);
+    const float slack1 = fabsf(v1) * kKeyTrunc + E1;   // + key truncation
+    const float d1 = fmaxf(v1 + xn + slack1, 0.f);   // bound on the best center's d^2
+    const float W = fp32_tie_window(d);
+    // a center with ||c'|| > ||x'|| + sqrt(d1 (1 + 2W)) is farther than d1 (1 + 2W)
+    // by the triangle inequality, outside the tie window of the best: only nearer
+    // centers need the error bound, and their ||c'|| is at most ceff
+    const float ceff = fminf(cmax, X + sqrtf(d1 * (1.f + 2.f * W)));
+    const float Eo = sb.ep * X * ceff + sb.en * (xn + ceff * ceff);
+    // v2 lowered by its key truncation; stays +inf when there is no runner-up
+    const float v2lo = v2 >= 0.f ? v2 * (1.f - kKeyTrunc) : v2 * (1.f + kKeyTrunc);
+    return (v2lo - Eo) > (v1 + slack1 + W * d1 + 1e-30f);
+}
+
+// The decision once the certain best center j of row R has its exact FP32 value b1,
+// taken exactly as on the CUDA-core path: in a round it replaces the current
+// center only if nearer (an FP32 near tie is re-decided in FP64, equal FP64
+// values keep the lower center number); in Lloyd's assignment it is the label.
+// Returns 1 when the label changed.
+template <int MODE>
+__device__ __forceinline__ int refine_decide(const float *__restrict__ X, int d, const float *__restrict__ C,
+                                             int64_t R, int j, float b1, float *D2, int32_t *idx, int32_t *labels,
+                                             const int32_t *prev, float *dmin, unsigned long long *fp64_cnt) {
+    if (MODE == MODE_ROUND) {
+        const float old = D2[R];
+        const int oi = idx[R];
+        const float W = fp32_tie_window(d);
+        const float m32 = fminf(old, b1);
+        const float lim = m32 + W * m32;
+        if (old <= lim && b1 <= lim) {
+            const float *xg = X + R * d;
+            const double dold = dist2_fp64(xg, C + (int64_t)oi * d, d);
+            const double dnew = dist2_fp64(xg, C + (int64_t)j * d, d);
+            atomicAdd(fp64_cnt, 1ull);
+            if (dnew < dold || (dnew == dold && j < oi)) { D2[R] = b1; idx[R] = j; }
+        } else if (b1 < old) {
+            D2[R] = b1;
+            idx[R] = j;
+        }
+        return 0;
+    } else {
+        if (labels) labels[R] = j;
+        dmin[R] = b1;
+        return prev ? (prev[R] != j) : 0;
+    }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256) refine_kernel(const float *__restrict__ X, int64_t n, int d,
                                                     const float *__restrict__ C, const int32_t *__restrict__ cand1,
-                                                    float *D2, int32_t *idx, int32_t *labels, const int32_t *prev,
-                                                    int *changed, float *dmin, unsigned long long *fp64_cnt, int *) {
+                                                    const float *__restrict__ v1s, const float *__restrict__ v2s,
+                                                    ScreenBound sb, float *D2, int32_t *idx, int32_t *labels,
+                                                    const int32_t *prev, int *changed, float *dmin,
+                                                    unsigned long long *fp64_cnt) {
     extern __shared__ __align__(16) float rsm[];
     const int ds = refine_stride(d);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -671,7 +757,13 @@ __global__ void __launch_bounds__(256) refine_kernel(const float *__restrict__ X
     const int64_t w0 = (int64_t)blockIdx.x * blockDim.x + wid * 32;
     const int nw = (int)max((int64_t)0, min((int64_t)32, n - w0));
     const int64_t R = w0 + lane;
-    const int j = lane < nw ? cand1[R] : -1;
+    int j = -1;
+    if (lane < nw) {
+        j = cand1[R];
+        const int begin = MODE == MODE_ROUND ? sb.st->batch_begin : 0;
+        if (j < 0 || !screen_certain(sb, sb.xnorm[R], j - begin, v1s[R], v2s[R], d)) j = -1;
+    }
+    append_fixups(sb, lane < nw && j < 0, R);
     const bool even = (d & 1) == 0;   // rows 8-byte aligned in global memory
     for (int rr = 0; rr < nw; ++rr) {
         const int jr = __shfl_sync(0xffffffffu, j, rr);
@@ -710,33 +802,141 @@ __global__ void __launch_bounds__(256) refine_kernel(const float *__restrict__ X
             const float t = __fsub_rn(xa[d - 1], ca[d - 1]);
             b1 = __fmaf_rn(t, t, b1);
         }
-        const float *cr = C + (int64_t)j * d;
-        if (MODE == MODE_ROUND) {
-            const float old = D2[R];
-            const int oi = idx[R];
-            const float W = fp32_tie_window(d);
-            const float m32 = fminf(old, b1);
-            const float lim = m32 + W * m32;
-            if (old <= lim && b1 <= lim) {
-                const float *xg = X + R * d;
-                const double dold = dist2_fp64(xg, C + (int64_t)oi * d, d);
-                const double dnew = dist2_fp64(xg, cr, d);
-                atomicAdd(fp64_cnt, 1ull);
-                if (dnew < dold || (dnew == dold && j < oi)) { D2[R] = b1; idx[R] = j; }
-            } else if (b1 < old) {
-                D2[R] = b1;
-                idx[R] = j;
-            }
-        } else {
-            if (labels) labels[R] = j;
-            dmin[R] = b1;
-            if (prev) chg = prev[R] != j;
-        }
+        chg = refine_decide<MODE>(X, d, C, R, j, b1, D2, idx, labels, prev, dmin, fp64_cnt);
     }
     if (MODE == MODE_ASSIGN && changed) {
         const int c = warp_sum_i32(chg);
         if (lane == 0 && c) atomicAdd(changed, c);
     }
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Refine with the pass's centers resident in shared memory (used when they fit and
+// the row stride gives conflict-free lane-per-row reads: d odd or d = 2 mod 4).
+// Persistent CTAs copy the centers once; each warp then walks 32-row blocks of X.
+// A block is contiguous in X, so flat 16-byte asynchronous copies bring it in,
+// double-buffered per warp.  Lane = row: the exact FP32 difference form reads the
+// row from the block and the center from the resident copy, so the value is
+// bit-identical to dist2_fp32.
+__host__ __device__ __forceinline__ int resident_center_floats(int cap_rows, int d) { return (cap_rows * d + 3) & ~3; }
+__host__ __device__ __forceinline__ int resident_block_floats(int d) { return (32 * d + 3) & ~3; }
+
+template <int MODE>
+__global__ void __launch_bounds__(512) refine_resident_kernel(
+    const float *__restrict__ X, int64_t n, int d, const float *__restrict__ C, int cap_rows,
+    const int32_t *__restrict__ cand1, const float *__restrict__ v1s, const float *__restrict__ v2s, ScreenBound sb,
+    float *D2, int32_t *idx, int32_t *labels, const int32_t *prev, int *changed, float *dmin,
+    unsigned long long *fp64_cnt) {
+    extern __shared__ __align__(16) float rsm[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int begin = MODE == MODE_ROUND ? sb.st->batch_begin : 0;
+    const int cnt = MODE == MODE_ROUND ? min(sb.st->batch_cnt, cap_rows) : cap_rows;
+    const int xfl = resident_block_floats(d);
+    float *Cs = rsm;
+    float *xb = rsm + resident_center_floats(cap_rows, d) + wid * 2 * xfl;
+    {
+        const float *src = C + (int64_t)begin * d;
+        const int nf = cnt * d;
+        if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+            for (int f = threadIdx.x; f < (nf >> 2); f += blockDim.x) cp_async16(Cs + 4 * f, src + 4 * f);
+            for (int f = (nf & ~3) + threadIdx.x; f < nf; f += blockDim.x) cp_async4(Cs + f, src + f);
+        } else {
+            for (int f = threadIdx.x; f < nf; f += blockDim.x) cp_async4(Cs + f, src + f);
+        }
+        cp_async_commit();
+    }
+    const int64_t nb = (n + 31) / 32;
+    const int64_t gw = (int64_t)blockIdx.x * nwarps + wid, W = (int64_t)gridDim.x * nwarps;
+    // a block starts at 32 b d floats = 128 b d bytes: 16-byte aligned when X is
+    const bool xal = (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
+    auto issue = [&](int64_t b, float *dst) {
+        const int64_t r0 = b * 32;
+        const int nf = (int)min((int64_t)32, n - r0) * d;
+        const float *src = X + r0 * d;
+        if (xal) {
+            for (int f = lane; f < (nf >> 2); f += 32) cp_async16(dst + 4 * f, src + 4 * f);
+            for (int f = (nf & ~3) + lane; f < nf; f += 32) cp_async4(dst + f, src + f);
+        } else {
+            for (int f = lane; f < nf; f += 32) cp_async4(dst + f, src + f);
+        }
+    };
+    if (gw < nb) issue(gw, xb);
+    cp_async_commit();
+    cp_async_wait<1>();   // the centers (the first block may still be in flight)
+    __syncthreads();
+    const bool even = (d & 1) == 0;
+    int chg = 0, it = 0;
+    for (int64_t b = gw; b < nb; b += W, ++it) {
+        const float *cur = xb + (it & 1) * xfl;
+        if (b + W < nb) issue(b + W, xb + ((it + 1) & 1) * xfl);
+        cp_async_commit();
+        const int64_t r0 = b * 32;
+        const int nr = (int)min((int64_t)32, n - r0);
+        const int64_t R = r0 + lane;
+        int j = -1;
+        if (lane < nr) {
+            j = cand1[R];
+            if (j < 0 || j - begin >= cnt || !screen_certain(sb, sb.xnorm[R], j - begin, v1s[R], v2s[R], d)) j = -1;
+        }
+        append_fixups(sb, lane < nr && j < 0, R);
+        cp_async_wait<1>();   // this block is in (the next one may be pending)
+        __syncwarp();
+        if (j >= 0) {
+            const float *xa = cur + lane * d;
+            const float *ca = Cs + (int64_t)(j - begin) * d;
+            float b1 = 0.f;
+            if (even) {
+                const float2 *x2 = reinterpret_cast<const float2 *>(xa);
+                const float2 *c2 = reinterpret_cast<const float2 *>(ca);
+#pragma unroll 4
+                for (int p = 0; p < (d >> 1); ++p) {
+                    const float2 a = x2[p], c = c2[p];
+                    float t = __fsub_rn(a.x, c.x);
+                    b1 = __fmaf_rn(t, t, b1);
+                    t = __fsub_rn(a.y, c.y);
+                    b1 = __fmaf_rn(t, t, b1);
+                }
+            } else {
+#pragma unroll 4
+                for (int q = 0; q < d; ++q) {
+                    const float t = __fsub_rn(xa[q], ca[q]);
+                    b1 = __fmaf_rn(t, t, b1);
+                }
+            }
+            chg += refine_decide<MODE>(X, d, C, R, j, b1, D2, idx, labels, prev, dmin, fp64_cnt);
+        }
+        __syncwarp();   // the buffer is refilled two blocks later
+    }
+    cp_async_wait<0>();
+    if (MODE == MODE_ASSIGN && changed) {
+        const int c = warp_sum_i32(chg);
+        if (lane == 0 && c) atomicAdd(changed, c);
+    }
+}
+
+// warps of a resident refine CTA (0: the centers do not fit, or the stride is not
+// conflict-free: use refine_kernel)
+int resident_warps(int cap_rows, int d) {
+    if (!((d & 1) || (d & 3) == 2)) return 0;
+    const size_t budget = 200u * 1024u;
+    const size_t cbytes = sizeof(float) * (size_t)resident_center_floats(cap_rows, d);
+    if (cbytes >= budget) return 0;
+    const size_t per_warp = sizeof(float) * 2 * (size_t)resident_block_floats(d);
+    const int w = (int)((budget - cbytes) / per_warp);
+    return w < 4 ? 0 : (w > 16 ? 16 : w);
+}
+
+size_t resident_smem_bytes(int cap_rows, int d, int warps) {
+    return sizeof(float) * ((size_t)resident_center_floats(cap_rows, d) + (size_t)warps * 2 * resident_block_floats(d));
 }
 
 // warps per refine CTA: 64 staged rows of refine_stride(d) floats each, within 200 KB
@@ -754,6 +954,12 @@ cudaError_t configure_refine_kernels() {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(refine_kernel<MODE_ASSIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(refine_resident_kernel<MODE_ROUND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(refine_resident_kernel<MODE_ASSIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(fixup_tile_kernel<MODE_ROUND>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(fixup_tile_kernel<MODE_ASSIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -764,8 +970,8 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
                            int *changed, float *dmin, int timing_cls) {
     cudaError_t e;
     const int split = c.precision == KMPAR_BF16X3 ? 1 : 0;
-    if ((e = tc::launch_prep_centers(C, c.d, split, c.st, k, mode_round, mode_round ? c.cap_round : k, c.tc_img,
-                                     c.tc_cnorm, c.tc_cmax, c.stream)) != cudaSuccess)
+    if ((e = tc::launch_prep_centers(C, c.d, split, c.st, k, mode_round, mode_round ? c.cap_round : k, c.tc_anchor,
+                                     c.tc_img, c.tc_cnorm, c.tc_cmax, c.stream)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(c.fix_cnt, 0, sizeof(int), c.stream)) != cudaSuccess) return e;
     // rows the screening does not reach (e.g. an empty batch) must not see a stale winner
@@ -774,22 +980,46 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
     p.X = c.X; p.n = c.n; p.d = c.d; p.split = split;
     p.ximg = c.tc_ximg; p.xnorm = c.tc_xnorm;
     p.Cf = C; p.cnt = k; p.st = c.st; p.bimg = c.tc_img; p.cnorm = c.tc_cnorm; p.cmax_bits = c.tc_cmax;
-    p.cand1 = c.cand1; p.fix_rows = c.fix_rows; p.fix_cnt = c.fix_cnt; p.fp64_cnt = &c.st->argmin_fp64;
-    p.err = c.tc_err;
+    p.cand1 = c.cand1; p.v1 = c.tc_v1; p.v2 = c.tc_v2; p.fix_rows = c.fix_rows; p.fix_cnt = c.fix_cnt;
+    p.fp64_cnt = &c.st->argmin_fp64; p.err = c.tc_err;
     cudaEvent_t ev = nullptr;
     if ((e = timing_begin(c, &ev)) != cudaSuccess) return e;
     if ((e = tc::launch_nearest_tc(p, mode_round, c.num_sms, c.stream)) != cudaSuccess) return e;
     if ((e = timing_end(c, ev, timing_cls)) != cudaSuccess) return e;
+    ScreenBound sb{};
+    sb.xnorm = c.tc_xnorm; sb.cnorm = c.tc_cnorm; sb.cmax_bits = c.tc_cmax; sb.st = c.st;
+    sb.fix_rows = c.fix_rows; sb.fix_cnt = c.fix_cnt;
+    tc::tc_bound(c.d, split, &sb.ep, &sb.en);
+    const int cap_rows = mode_round ? c.cap_round : k;
+    const int rw = resident_warps(cap_rows, c.d);
+    if (rw > 0) {
+        const size_t rsm = resident_smem_bytes(cap_rows, c.d, rw);
+        const int64_t nb = (c.n + 31) / 32;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(c.num_sms, (nb + rw - 1) / rw));
+        if (mode_round)
+            refine_resident_kernel<MODE_ROUND><<<grid, 32 * rw, rsm, c.stream>>>(
+                c.X, c.n, c.d, C, cap_rows, c.cand1, c.tc_v1, c.tc_v2, sb, c.D2, c.idx, nullptr, nullptr, nullptr,
+                nullptr, &c.st->argmin_fp64);
+        else
+            refine_resident_kernel<MODE_ASSIGN><<<grid, 32 * rw, rsm, c.stream>>>(
+                c.X, c.n, c.d, C, cap_rows, c.cand1, c.tc_v1, c.tc_v2, sb, nullptr, nullptr, labels, prev, changed,
+                dmin, &c.st->argmin_fp64);
+        count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = count_fixups(c)) != cudaSuccess) return e;
+        return launch_fixup(c, mode_round, C, k, labels, prev, changed, dmin);
+    }
     const int rthreads = 32 * refine_warps(c.d);
     const int grid = (int)((c.n + rthreads - 1) / rthreads);
     const size_t rsm = refine_smem_bytes(c.d);
     if (mode_round)
-        refine_kernel<MODE_ROUND><<<grid, rthreads, rsm, c.stream>>>(c.X, c.n, c.d, C, c.cand1, c.D2, c.idx, nullptr,
-                                                                nullptr, nullptr, nullptr, &c.st->argmin_fp64,
-                                                                c.tc_err);
+        refine_kernel<MODE_ROUND><<<grid, rthreads, rsm, c.stream>>>(c.X, c.n, c.d, C, c.cand1, c.tc_v1, c.tc_v2, sb,
+                                                                     c.D2, c.idx, nullptr, nullptr, nullptr, nullptr,
+                                                                     &c.st->argmin_fp64);
     else
-        refine_kernel<MODE_ASSIGN><<<grid, rthreads, rsm, c.stream>>>(c.X, c.n, c.d, C, c.cand1, nullptr, nullptr, labels,
-                                                                 prev, changed, dmin, &c.st->argmin_fp64, c.tc_err);
+        refine_kernel<MODE_ASSIGN><<<grid, rthreads, rsm, c.stream>>>(c.X, c.n, c.d, C, c.cand1, c.tc_v1, c.tc_v2, sb,
+                                                                      nullptr, nullptr, labels, prev, changed, dmin,
+                                                                      &c.st->argmin_fp64);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = count_fixups(c)) != cudaSuccess) return e;

@@ -58,7 +58,7 @@ void free_ctx(kmp::Ctx &c) {
                     c.labels[0], c.labels[1], c.perm, c.hist, c.base, c.cost_dev, c.tc_img, c.tc_cnorm,
                     c.tc_cmax, c.tc_err, c.cand1, c.fix_rows, c.fix_cnt, c.dmin, c.tc_ximg, c.tc_xnorm,
                     c.piece, c.psum, c.rc_cmass, c.rc_sync, c.rc_err, c.chunk, c.tc_v1, c.tc_v2,
-                    c.tc_anchor, c.tc_anchor_part};
+                    c.tc_anchor, c.tc_anchor_part, c.lloyd_rec};
     for (void *b : bufs)
         if (b) cudaFree(b);
 }
@@ -315,43 +315,76 @@ kmpar_status kmpar_lloyd(kmpar_ctx *ctx, float *centers_dev, int32_t max_iter, i
     if (c.k > 49152) return fail(&c, KMPAR_ERR_UNSUPPORTED, "Lloyd supports k <= 49152");
     kmpar_status s = ensure_lloyd_buffers(c);
     if (s != KMPAR_OK) return s;
-    int cur = 0, t = 0;
-    double cost = 0.0;
+    // At a fixed point an iteration changes nothing (the same labels give the same
+    // centroids bit for bit, and those the same labels), so the host reads the
+    // per-iteration (cost, changed) records only every few iterations and stops at
+    // the first one that changed no label; iterations run past it are no-ops.
+    struct Rec { double cost; int changed; int pad; };
+    static_assert(sizeof(Rec) == 16, "record layout");
+    if (c.lloyd_rec_cap < max_iter + 1) {
+        if (c.lloyd_rec) cudaFree(c.lloyd_rec);
+        c.lloyd_rec = nullptr;
+        c.lloyd_rec_cap = 0;
+        KMP_CUDA(&c, cudaMalloc(&c.lloyd_rec, sizeof(Rec) * (size_t)(max_iter + 1)), "alloc Lloyd records");
+        c.lloyd_rec_cap = max_iter + 1;
+    }
+    Rec *rec = reinterpret_cast<Rec *>(c.lloyd_rec);
+    std::vector<Rec> hrec((size_t)max_iter + 1);
     int *changed = reinterpret_cast<int *>(c.cost_dev + 1);
-    for (;;) {
-        KMP_CUDA(&c, cudaMemsetAsync(changed, 0, sizeof(int), c.stream), "memset changed");
-        if (c.precision == KMPAR_FP32) {
-            cudaEvent_t ev = nullptr;
-            KMP_CUDA(&c, kmp::timing_begin(c, &ev), "timing");
-            KMP_CUDA(&c, kmp::launch_assign(c.X, c.n, c.d, centers_dev, c.k, c.labels[cur],
-                                            t > 0 ? c.labels[cur ^ 1] : nullptr, changed, c.partials,
-                                            c.num_partials, &c.st->argmin_fp64, c.stream),
-                     "assign kernel");
-            KMP_CUDA(&c, kmp::timing_end(c, ev, 1), "timing");
-            KMP_CUDA(&c, kmp::launch_sum_f64(c.partials, c.num_partials, c.cost_dev, nullptr, c.stream), "cost sum");
-        } else {
-            KMP_CUDA(&c, kmp::launch_tc_pass(c, 0, centers_dev, c.k, c.labels[cur], t > 0 ? c.labels[cur ^ 1] : nullptr,
-                                             changed, c.dmin, 1),
-                     "tensor assign pass");
-            KMP_CUDA(&c, kmp::launch_sum_rows(c.dmin, c.n, c.partials, c.num_partials, c.cost_dev, nullptr, c.stream),
-                     "cost sum");
+    int cur = 0, t = 0, done = -1;
+    while (done < 0) {
+        const int batch = t < 8 ? 4 : 8;
+        const int t_end = std::min(max_iter, t + batch - 1);
+        for (int tt = t; tt <= t_end; ++tt) {
+            if (tt > t) {
+                KMP_CUDA(&c, kmp::launch_centroids(c, c.labels[cur], centers_dev), "centroid kernels");
+                cur ^= 1;
+            }
+            KMP_CUDA(&c, cudaMemsetAsync(changed, 0, sizeof(int), c.stream), "memset changed");
+            if (c.precision == KMPAR_FP32) {
+                cudaEvent_t ev = nullptr;
+                KMP_CUDA(&c, kmp::timing_begin(c, &ev), "timing");
+                KMP_CUDA(&c, kmp::launch_assign(c.X, c.n, c.d, centers_dev, c.k, c.labels[cur],
+                                                tt > 0 ? c.labels[cur ^ 1] : nullptr, changed, c.partials,
+                                                c.num_partials, &c.st->argmin_fp64, c.stream),
+                         "assign kernel");
+                KMP_CUDA(&c, kmp::timing_end(c, ev, 1), "timing");
+                KMP_CUDA(&c, kmp::launch_sum_f64(c.partials, c.num_partials, c.cost_dev, nullptr, c.stream),
+                         "cost sum");
+            } else {
+                KMP_CUDA(&c, kmp::launch_tc_pass(c, 0, centers_dev, c.k, c.labels[cur],
+                                                 tt > 0 ? c.labels[cur ^ 1] : nullptr, changed, c.dmin, 1),
+                         "tensor assign pass");
+                KMP_CUDA(&c, kmp::launch_sum_rows(c.dmin, c.n, c.partials, c.num_partials, c.cost_dev, nullptr,
+                                                  c.stream),
+                         "cost sum");
+            }
+            KMP_CUDA(&c, cudaMemcpyAsync(rec + tt, c.cost_dev, sizeof(Rec), cudaMemcpyDeviceToDevice, c.stream),
+                     "record");
         }
-        struct { double cost; int changed; int pad; } hb;
-        KMP_CUDA(&c, cudaMemcpyAsync(&hb, c.cost_dev, 16, cudaMemcpyDeviceToHost, c.stream), "read cost");
+        KMP_CUDA(&c, cudaMemcpyAsync(hrec.data() + t, rec + t, sizeof(Rec) * (size_t)(t_end - t + 1),
+                                     cudaMemcpyDeviceToHost, c.stream),
+                 "read records");
         KMP_CUDA(&c, cudaStreamSynchronize(c.stream), "sync");
         KMP_CUDA(&c, kmp::timing_drain(c), "timing");
         if (c.tc_err) {
             kmpar_status ts = check_timeout(c);
             if (ts != KMPAR_OK) return ts;
         }
-        cost = hb.cost;
-        if (cost_hist) cost_hist[t] = cost;
-        if (t > 0 && hb.changed == 0) break;
-        if (t == max_iter) break;
-        KMP_CUDA(&c, kmp::launch_centroids(c, c.labels[cur], centers_dev), "centroid kernels");
-        cur ^= 1;
-        ++t;
+        for (int tt = t; tt <= t_end && done < 0; ++tt)
+            if (tt > 0 && hrec[tt].changed == 0) done = tt;
+        if (done < 0 && t_end == max_iter) done = max_iter;
+        if (done < 0) {
+            // the last iteration of the batch still needs its centroid update
+            KMP_CUDA(&c, kmp::launch_centroids(c, c.labels[cur], centers_dev), "centroid kernels");
+            cur ^= 1;
+            t = t_end + 1;
+        }
     }
+    t = done;
+    const double cost = hrec[t].cost;
+    if (cost_hist)
+        for (int tt = 0; tt <= t; ++tt) cost_hist[tt] = hrec[tt].cost;
     if (labels_dev)
         KMP_CUDA(&c, cudaMemcpyAsync(labels_dev, c.labels[cur], sizeof(int32_t) * c.n, cudaMemcpyDeviceToDevice,
                                      c.stream), "copy labels");
@@ -462,8 +495,10 @@ kmpar_status kmpar_fit(const float *X, int64_t n, int32_t d, int32_t k, double e
         st = kmpar_recluster(ctx, Cd);
         if (st == KMPAR_WARN_FEW_CANDIDATES) { warn = st; st = KMPAR_OK; }
     }
-    if (st == KMPAR_OK && seed_cost) st = kmpar_cost(Xd, n, d, Cd, k, precision, seed_cost, stream);
-    if (st == KMPAR_OK) st = kmpar_lloyd(ctx, Cd, max_iter, Ld, iters, final_cost, nullptr);
+    // Lloyd's first assignment is made with the seed centers: its cost is the seed cost
+    std::vector<double> hist(max_iter >= 0 ? (size_t)max_iter + 1 : 1);
+    if (st == KMPAR_OK) st = kmpar_lloyd(ctx, Cd, max_iter, Ld, iters, final_cost, hist.data());
+    if (st == KMPAR_OK && seed_cost) *seed_cost = hist[0];
     if (st != KMPAR_OK && ctx) g_err = ctx->c.err;
     if (ctx) kmpar_destroy(ctx);
     if (host) {

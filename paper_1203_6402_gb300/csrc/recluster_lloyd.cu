@@ -426,14 +426,37 @@ __device__ __forceinline__ void two_sum_add(float &s, float &c, float x) {
     s = t;
 }
 
-// one CTA per piece: sum of up to kPiece sorted member rows (8 warps x 32
-// coordinates; warp w takes members w, w+8, ... in order, eight loads in flight,
-// compensated FP32 accumulation), the warps' sums combined in FP64 in order
-__global__ void __launch_bounds__(256) piece_sum_kernel(const float *__restrict__ X, int d, int k,
+// one CTA per piece: sum of up to kPiece sorted member rows.  Warp w takes members
+// w, w + 8, ... in order with sixteen row loads in flight, lanes over coordinates:
+// a lane carries a coordinate pair (8-byte loads, a whole 64-float slice of a row
+// in one instruction) when rows are 8-byte aligned, else one coordinate; sums are
+// compensated FP32 pairs (TwoSum), and the warps' sums are combined in FP64 in
+// warp order.
+constexpr int kPieceUnroll = 16;
+
+// read-only loads kept in program order, so that a group of them is in flight
+// together before the first one is used
+__device__ __forceinline__ float2 ld_nc_f2(const float *p) {
+    float2 v;
+    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+// an empty statement that takes eight values as in/out operands: the additions
+// after it cannot move above it, so the loads before it are all issued first
+__device__ __forceinline__ void hold8(float &a, float &b, float &c, float &d, float &e, float &f, float &g, float &h) {
+    asm volatile("" : "+f"(a), "+f"(b), "+f"(c), "+f"(d), "+f"(e), "+f"(f), "+f"(g), "+f"(h));
+}
+__device__ __forceinline__ float ld_nc_f1(const float *p) {
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+__global__ void __launch_bounds__(256, 4) piece_sum_kernel(const float *__restrict__ X, int d, int k, int pairs,
                                                         const int32_t *__restrict__ perm,
                                                         const int32_t *__restrict__ base,
                                                         const int32_t *__restrict__ piece, double *psum) {
-    __shared__ double part[8][32];
+    __shared__ double part[8][64];
     __shared__ int rows[kPiece];
     __shared__ int s_j;
     const int pid = blockIdx.x;
@@ -453,26 +476,59 @@ __global__ void __launch_bounds__(256) piece_sum_kernel(const float *__restrict_
     for (int i = threadIdx.x; i < cnt; i += 256) rows[i] = perm[p0 + i];
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int dc = 0; dc < d; dc += 32) {
-        const int q = dc + lane;
-        float s = 0.f, c = 0.f;
-        if (q < d) {
-            int i = w;
-            for (; i + 56 < cnt; i += 64) {
-                float v[8];
+    const int per_pass = pairs ? 64 : 32;
+    for (int dc = 0; dc < d; dc += per_pass) {
+        float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+        if (pairs) {
+            const int q = dc + 2 * lane;
+            if (q < d) {
+                int i = w;
+                for (; i + 8 * (kPieceUnroll - 1) < cnt; i += 8 * kPieceUnroll) {
+                    float2 v[kPieceUnroll];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = __ldg(X + (int64_t)rows[i + 8 * u] * d + q);
+                    for (int u = 0; u < kPieceUnroll; ++u) v[u] = ld_nc_f2(X + (int64_t)rows[i + 8 * u] * d + q);
 #pragma unroll
-                for (int u = 0; u < 8; ++u) two_sum_add(s, c, v[u]);
+                    for (int u = 0; u < kPieceUnroll; u += 4)
+                        hold8(v[u].x, v[u].y, v[u + 1].x, v[u + 1].y, v[u + 2].x, v[u + 2].y, v[u + 3].x, v[u + 3].y);
+#pragma unroll
+                    for (int u = 0; u < kPieceUnroll; ++u) {
+                        two_sum_add(sx, cx, v[u].x);
+                        two_sum_add(sy, cy, v[u].y);
+                    }
+                }
+                for (; i < cnt; i += 8) {
+                    const float2 v = __ldg(reinterpret_cast<const float2 *>(X + (int64_t)rows[i] * d + q));
+                    two_sum_add(sx, cx, v.x);
+                    two_sum_add(sy, cy, v.y);
+                }
             }
-            for (; i < cnt; i += 8) two_sum_add(s, c, __ldg(X + (int64_t)rows[i] * d + q));
+            part[w][2 * lane] = (double)sx + (double)cx;
+            part[w][2 * lane + 1] = (double)sy + (double)cy;
+        } else {
+            const int q = dc + lane;
+            if (q < d) {
+                int i = w;
+                for (; i + 8 * (kPieceUnroll - 1) < cnt; i += 8 * kPieceUnroll) {
+                    float v[kPieceUnroll];
+#pragma unroll
+                    for (int u = 0; u < kPieceUnroll; ++u) v[u] = ld_nc_f1(X + (int64_t)rows[i + 8 * u] * d + q);
+#pragma unroll
+                    for (int u = 0; u < kPieceUnroll; u += 8)
+                        hold8(v[u], v[u + 1], v[u + 2], v[u + 3], v[u + 4], v[u + 5], v[u + 6], v[u + 7]);
+#pragma unroll
+                    for (int u = 0; u < kPieceUnroll; ++u) two_sum_add(sx, cx, v[u]);
+                }
+                for (; i < cnt; i += 8) two_sum_add(sx, cx, __ldg(X + (int64_t)rows[i] * d + q));
+            }
+            part[w][lane] = (double)sx + (double)cx;
         }
-        part[w][lane] = (double)s + (double)c;
         __syncthreads();
-        if (w == 0 && q < d) {
-            double acc = 0.0;
-            for (int u = 0; u < 8; ++u) acc += part[u][lane];
-            psum[(int64_t)pid * d + q] = acc;
+        if (w == 0) {
+            for (int c = lane; c < per_pass && dc + c < d; c += 32) {
+                double acc = 0.0;
+                for (int u = 0; u < 8; ++u) acc += part[u][c];
+                psum[(int64_t)pid * d + dc + c] = acc;
+            }
         }
         __syncthreads();
     }
@@ -517,7 +573,10 @@ cudaError_t launch_centroids(Ctx &c, const int32_t *labels, float *centers) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     scatter_kernel<<<c.nsb, 32, sizeof(int32_t) * k, c.stream>>>(labels, c.n, k, sb, c.hist, c.base, c.perm);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    piece_sum_kernel<<<(int)max_pieces(c.n, k), 256, 0, c.stream>>>(c.X, c.d, k, c.perm, c.base, c.piece, c.psum);
+    // coordinate pairs need 8-byte aligned rows: d even and X 8-byte aligned
+    const int pairs = (c.d % 2 == 0) && (reinterpret_cast<uintptr_t>(c.X) % 8 == 0);
+    piece_sum_kernel<<<(int)max_pieces(c.n, k), 256, 0, c.stream>>>(c.X, c.d, k, pairs, c.perm, c.base, c.piece,
+                                                                    c.psum);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int64_t kd = (int64_t)k * c.d;
     centroid_finalize_kernel<<<(int)((kd + 255) / 256), 256, 0, c.stream>>>(c.d, k, c.base, c.piece, c.psum, centers);

@@ -250,6 +250,27 @@ def test_run_to_run_deterministic(km):
     assert res[0][2] == res[1][2]
 
 
+@pytest.mark.parametrize("k,d", [(420, 128), (37, 15)], ids=["many_wide_clusters", "few_narrow_clusters"])
+def test_lloyd_from_fixed_centers_matches_oracle(km, orc, k, d):
+    """Lloyd alone (Sec. 3.1 centroid, Sec. 1 iteration) from fixed seed centers:
+    the segmented centroid sums and the assignment agree with the oracle, also
+    with many clusters of wide rows (k = 420, d = 128)."""
+    X = datagen.gauss_mixture(2500, d, 40, 100.0, seed=33)
+    C0 = np.ascontiguousarray(X[:k])
+    g = km.KMeansPar(_dev(X), k, 2.0 * k, 1, 5)
+    C = _dev(C0)
+    out = g.lloyd(C, 15, labels=True, hist=True)
+    lab = out["labels"].cpu().numpy()
+    oC, olab, oit, ofc, ohist, onear = orc.lloyd(X, C0.astype(np.float64), 15)
+    if out["iters"] == oit and np.array_equal(lab, olab):
+        assert math.isclose(out["final_cost"], ofc, rel_tol=1e-4)
+        oCf = np.asarray(oC)
+        np.testing.assert_allclose(C.cpu().numpy(), oCf, rtol=1e-5, atol=1e-5 * (np.abs(oCf).max() + 1))
+    else:
+        assert onear.any() or g.stats()["argmin_fp64"] > 0
+    g.close()
+
+
 # ------------------------------------------------------------------ edge cases
 def test_single_point(km, orc):
     X = np.array([[1.5, -2.0, 3.0]], np.float32)

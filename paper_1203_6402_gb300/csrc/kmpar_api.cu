@@ -57,7 +57,7 @@ void free_ctx(kmp::Ctx &c) {
     void *bufs[] = {c.st, c.D2, c.idx, c.drawn, c.cand, c.C, c.w, c.rD2, c.chosen, c.partials,
                     c.labels[0], c.labels[1], c.perm, c.hist, c.base, c.cost_dev, c.tc_img, c.tc_cnorm,
                     c.tc_cmax, c.tc_err, c.cand1, c.fix_rows, c.fix_cnt, c.dmin, c.tc_ximg, c.tc_xnorm,
-                    c.piece, c.psum, c.rc_cmass, c.rc_sync, c.rc_err, c.chunk, c.tc_v1, c.tc_v2,
+                    c.piece, c.psum, c.rc_cmass, c.rc_sync, c.rc_err, c.chunk, c.tc_v2,
                     c.tc_anchor, c.tc_anchor_part, c.lloyd_rec};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -204,7 +204,6 @@ kmpar_status kmpar_init(kmpar_ctx **out, const float *X, int64_t n, int32_t d, i
         KMP_INIT_CUDA(alloc(&c.tc_err, 1), "alloc error word");
         KMP_INIT_CUDA(alloc(&c.fix_rows, n), "alloc fix-up rows");
         KMP_INIT_CUDA(alloc(&c.cand1, n), "alloc screening winners");
-        KMP_INIT_CUDA(alloc(&c.tc_v1, n), "alloc screening values");
         KMP_INIT_CUDA(alloc(&c.tc_v2, n), "alloc screening values");
         KMP_INIT_CUDA(alloc(&c.tc_ximg, kmp::tc::tc_points_image_bytes(d, split, n)), "alloc points image");
         KMP_INIT_CUDA(alloc(&c.tc_xnorm, (size_t)((n + 127) / 128) * 128), "alloc point norms");

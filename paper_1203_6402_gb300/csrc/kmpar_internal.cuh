@@ -89,8 +89,8 @@ struct Ctx {
     float *tc_cnorm = nullptr;    // ||c'|| per padded center row
     unsigned int *tc_cmax = nullptr;
     int *tc_err = nullptr;        // first timeout code of a tensor pass
-    int32_t *cand1 = nullptr;     // per row: best screened center of the last tensor pass, or -1
-    float *tc_v1 = nullptr, *tc_v2 = nullptr;   // per row: best and runner-up screened values
+    int32_t *cand1 = nullptr;     // per row: first center of the best screened pair of the last tensor pass, or -1
+    float *tc_v2 = nullptr;       // per row: smallest screened value outside that pair
     int32_t *fix_rows = nullptr;  // rows left to the exact CUDA-core pass
     int *fix_cnt = nullptr;
     float *dmin = nullptr;        // Lloyd: exact d^2 of each point's chosen center

@@ -13,13 +13,15 @@
 // norms, and so the error, smaller for data away from the origin.
 //
 // Epilogue (16 warps, one TMEM lane per row, four warps per lane quarter, each on
-// its own column group): each value becomes a key whose low 6 mantissa bits hold
-// its column within the group (a compile-time constant: one logic op per value);
-// a branch-free top-2 over the keys gives the best center and the runner-up
-// value, written out per row.  refine_kernel then tests the runner-up against the screening error
-// window: a certain best center gets its exact FP32 distance and the decision is
-// taken exactly as on the CUDA-core path; otherwise the row goes to a fix-up list
-// that the CUDA-core kernel finishes with an exact scan.  Decisions are therefore
+// its own column group): adjacent centers are taken in pairs; the value-only
+// minimum of a pair becomes a key whose low 6 mantissa bits hold the pair's number
+// within the group (a compile-time constant: one logic op per pair), and a
+// branch-free top-2 over the keys gives the best pair and the smallest screened
+// value outside it (about 2.25 ALU ops per value, against 3.5 for a top-2 over
+// single centers).  The refine kernel then computes both centers of the pair in
+// exact FP32 and tests the other pairs' screened minimum against the error
+// window: a certain row takes the CUDA-core decision on the pair; otherwise it
+// goes to a fix-up list finished by an exact scan.  Decisions are therefore
 // identical to the FP32 path.
 //
 // The A operand (points) is encoded once per context by prep_points_kernel into a
@@ -315,7 +317,7 @@ struct Cfg {
     static constexpr int B_BYTES = KA * BN * 128;
     static constexpr int GW = BN / kGroups;   // columns per epilogue warp
     static constexpr int CHUNKS = GW / 32;
-    static_assert(GW <= (1 << kColBits) && GW % 32 == 0, "column field");
+    static_assert(GW / 2 <= (1 << kColBits) && GW % 32 == 0, "pair field");
 };
 
 struct Bound {
@@ -487,24 +489,36 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p) {
                 // two independent top-2 chains (alternate column pairs), merged per tile
                 float k1a = INF, k2a = INF, k1b = INF, k2b = INF;
                 const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + grp * C::GW);
+                static_assert(C::CHUNKS <= 2, "one load round per tile");
 #pragma unroll
                 for (int c = 0; c < C::CHUNKS; c += 2) {
                     uint32_t r[2][32];
                     tmem_ld32(tbase + c * 32, r[0]);
                     if (c + 1 < C::CHUNKS) tmem_ld32(tbase + (c + 1) * 32, r[1]);
                     tmem_wait_ld();
+                    // the warp's columns are in registers: the accumulator buffer goes
+                    // back to the MMA warp now, so the next tile's MMAs overlap this
+                    // warp's work on these values
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sm.acc_empty[buf]);
 #pragma unroll
                     for (int cc = 0; cc < 2; ++cc) {
                         if (c + cc >= C::CHUNKS) break;
 #pragma unroll
-                        for (int q = 0; q < 32; q += 4) {
-                            // key = value with its column within the group in the low
-                            // mantissa bits (col is a compile-time constant)
-                            const uint32_t col = (uint32_t)((c + cc) * 32 + q);
-                            const float a = __uint_as_float((r[cc][q] & vmask) | col);
-                            const float b = __uint_as_float((r[cc][q + 1] & vmask) | (col + 1));
-                            const float e = __uint_as_float((r[cc][q + 2] & vmask) | (col + 2));
-                            const float f = __uint_as_float((r[cc][q + 3] & vmask) | (col + 3));
+                        for (int q = 0; q < 32; q += 8) {
+                            // value-only minimum of each pair of adjacent centers, then a
+                            // key: the pair minimum with the pair's number within the
+                            // group in the low mantissa bits (a compile-time constant)
+                            const uint32_t pc = (uint32_t)(((c + cc) * 32 + q) >> 1);
+                            const float m0 = fminf(__uint_as_float(r[cc][q]), __uint_as_float(r[cc][q + 1]));
+                            const float m1 = fminf(__uint_as_float(r[cc][q + 2]), __uint_as_float(r[cc][q + 3]));
+                            const float m2 = fminf(__uint_as_float(r[cc][q + 4]), __uint_as_float(r[cc][q + 5]));
+                            const float m3 = fminf(__uint_as_float(r[cc][q + 6]), __uint_as_float(r[cc][q + 7]));
+                            const float a = __uint_as_float((__float_as_uint(m0) & vmask) | pc);
+                            const float b = __uint_as_float((__float_as_uint(m1) & vmask) | (pc + 1));
+                            const float e = __uint_as_float((__float_as_uint(m2) & vmask) | (pc + 2));
+                            const float f = __uint_as_float((__float_as_uint(m3) & vmask) | (pc + 3));
                             const float loa = fminf(a, b), hia = fmaxf(a, b);
                             const float lob = fminf(e, f), hib = fmaxf(e, f);
                             k2a = min3f(fmaxf(k1a, loa), k2a, hia);
@@ -514,9 +528,6 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p) {
                         }
                     }
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sm.acc_empty[buf]);
                 const float k1 = fminf(k1a, k1b);
                 const float k2 = min3f(fmaxf(k1a, k1b), k2a, k2b);
                 if (k1 < K1) { K2 = fminf(K1, k2); K1 = k1; T1 = t; }
@@ -546,25 +557,25 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p) {
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm.merge_free[mb]);
-                // (masked value, center number) order; equal masked values of different
-                // centers are near ties that the window test sends to the fix-up anyway.
-                // Group 0's columns start at 0 within the tile, group q+1's at (q+1) GW.
-                J1 = T1 * BN + (int)(__float_as_uint(K1) & ~kValMask);
+                // (masked value, first center of the pair) order; equal masked values
+                // of different pairs are near ties that the certainty test sends to
+                // the fix-up anyway.  Group 0's columns start at 0 within the tile,
+                // group q+1's at (q+1) GW; a key carries the pair number in the group.
+                J1 = T1 * BN + 2 * (int)(__float_as_uint(K1) & ~kValMask);
 #pragma unroll
                 for (int q = 0; q < kGroups - 1; ++q) {
                     const float m1v = __uint_as_float(__float_as_uint(o1[q]) & kValMask);
                     const float k1v = __uint_as_float(__float_as_uint(K1) & kValMask);
-                    const int oj = ot[q] * BN + (q + 1) * C::GW + (int)(__float_as_uint(o1[q]) & ~kValMask);
+                    const int oj = ot[q] * BN + (q + 1) * C::GW + 2 * (int)(__float_as_uint(o1[q]) & ~kValMask);
                     if (m1v < k1v || (m1v == k1v && oj < J1)) { K2 = min3f(K1, o2[q], K2); K1 = o1[q]; J1 = oj; }
                     else K2 = min3f(K2, o1[q], o2[q]);
                 }
             }
-            // ---- the best center and the two screened values; refine_kernel decides
-            // whether the best is certain (it hides the latency of the norm lookups)
+            // ---- the best pair and the best screened value outside it; the refine
+            // computes the pair exactly and decides whether it is certain
             const int64_t R = (int64_t)rt * BM + row;
             if (R < n) {
                 p.cand1[R] = J1 < cnt ? begin + J1 : -1;
-                p.v1[R] = __uint_as_float(__float_as_uint(K1) & kValMask);
                 p.v2[R] = __uint_as_float(__float_as_uint(K2) & kValMask);
             }
         }

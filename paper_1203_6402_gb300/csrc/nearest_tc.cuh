@@ -21,8 +21,8 @@ struct TcParams {
     const uint8_t *bimg;     // swizzled BF16 center tiles
     const float *cnorm;      // ||c'|| per padded center row of the batch
     const unsigned int *cmax_bits;
-    int32_t *cand1;          // per row: best screened center number (-1: none)
-    float *v1, *v2;          // per row: best and runner-up screened values (key-truncated)
+    int32_t *cand1;          // per row: first center of the best screened pair (-1: none)
+    float *v2;               // per row: smallest screened value outside that pair (key-truncated)
     int32_t *fix_rows;       // rows left to the exact CUDA-core pass
     int *fix_cnt;
     unsigned long long *fp64_cnt;

@@ -483,6 +483,62 @@ __device__ __forceinline__ void top2_merge(float &b1, int &i1, float &b2, int &i
     }
 }
 
+// The decision for row R once its best and runner-up candidates (b1, i1), (b2, i2)
+// have exact FP32 values (i2 = -1: none), taken exactly as nearest_kernel takes
+// it.  Lloyd: the label is the best, re-decided in FP64 against the runner-up
+// when their FP32 values lie within the tie window.  Round: the current center
+// is replaced by the best new candidate when nearer; when two or more of (current,
+// best, runner-up) lie within the tie window they are re-decided in FP64, equal
+// FP64 values keeping the lower center number.  Returns 1 when a Lloyd label
+// changed.
+template <int MODE>
+__device__ __forceinline__ int decide_top2(const float *__restrict__ X, int d, const float *__restrict__ C, int64_t R,
+                                           float b1, int i1, float b2, int i2, float *D2, int32_t *idx,
+                                           int32_t *labels, const int32_t *prev, float *dmin,
+                                           unsigned long long *fp64_cnt, unsigned long long *wide_cnt) {
+    const float W = fp32_tie_window(d);
+    const float *xrow = X + R * d;
+    if (MODE == MODE_ASSIGN) {
+        int lab = i1 != INT_MAX ? i1 : 0;
+        float stored = b1;
+        if (i2 >= 0 && b2 <= b1 + W * b1) {
+            double best = dist2_fp64(xrow, C + (int64_t)i1 * d, d);
+            int bj = i1;
+            take_if_better(dist2_fp64(xrow, C + (int64_t)i2 * d, d), i2, best, bj);
+            if (bj == i2) { lab = i2; stored = b2; }
+            atomicAdd(fp64_cnt, 1ull);
+        }
+        if (labels) labels[R] = lab;
+        if (dmin) dmin[R] = stored;
+        return (prev && prev[R] != lab) ? 1 : 0;
+    } else {
+        const float old = D2[R];
+        const int oi = idx[R];
+        const float m32 = fminf(old, b1);
+        const float lim = m32 + W * m32;
+        const bool in_old = (oi >= 0) && old <= lim;
+        const bool in1 = i1 != INT_MAX && b1 <= lim;
+        const bool in2 = i2 >= 0 && b2 <= lim;
+        int win = -1;
+        float wv = old;
+        if ((int)in_old + (int)in1 + (int)in2 >= 2) {
+            double best = DBL_MAX;
+            int bj = INT_MAX;
+            if (in_old) take_if_better(dist2_fp64(xrow, C + (int64_t)oi * d, d), oi, best, bj);
+            if (in1) take_if_better(dist2_fp64(xrow, C + (int64_t)i1 * d, d), i1, best, bj);
+            if (in2) take_if_better(dist2_fp64(xrow, C + (int64_t)i2 * d, d), i2, best, bj);
+            atomicAdd(fp64_cnt, 1ull);
+            if (in1 && in2) atomicAdd(wide_cnt, 1ull);
+            if (bj == i1) { win = i1; wv = b1; }
+            else if (bj == i2) { win = i2; wv = b2; }
+        } else if (i1 != INT_MAX && b1 < old) {
+            win = i1; wv = b1;
+        }
+        if (win >= 0) { D2[R] = wv; idx[R] = win; }
+        return 0;
+    }
+}
+
 // Rows whose screening window held more than one center, finished exactly: a CTA
 // takes 8 listed rows (one warp each) and streams tiles of 64 centers through
 // shared memory; the lanes of a warp split each tile's centers and sum the exact
@@ -565,45 +621,9 @@ __global__ void __launch_bounds__(256) fixup_tile_kernel(const float *__restrict
         }
         if (valid && lane == 0) {
             if (i2 == INT_MAX) { i2 = -1; b2 = FMAX; }
-            const float W = fp32_tie_window(d);
-            if (MODE == MODE_ASSIGN) {
-                int lab = i1 != INT_MAX ? i1 : 0;
-                float stored = b1;
-                if (i2 >= 0 && b2 <= b1 + W * b1) {
-                    double best = dist2_fp64(xrow, C + (int64_t)i1 * d, d);
-                    int bj = i1;
-                    take_if_better(dist2_fp64(xrow, C + (int64_t)i2 * d, d), i2, best, bj);
-                    if (bj == i2) { lab = i2; stored = b2; }
-                    atomicAdd(fp64_cnt, 1ull);
-                }
-                if (labels) labels[R] = lab;
-                if (dmin) dmin[R] = stored;
-                if (prev && changed && prev[R] != lab) atomicAdd(changed, 1);
-            } else {
-                const float old = D2[R];
-                const int oi = idx[R];
-                const float m32 = fminf(old, b1);
-                const float lim = m32 + W * m32;
-                const bool in_old = (oi >= 0) && old <= lim;
-                const bool in1 = i1 != INT_MAX && b1 <= lim;
-                const bool in2 = i2 >= 0 && b2 <= lim;
-                int win = -1;
-                float wv = old;
-                if ((int)in_old + (int)in1 + (int)in2 >= 2) {
-                    double best = DBL_MAX;
-                    int bj = INT_MAX;
-                    if (in_old) take_if_better(dist2_fp64(xrow, C + (int64_t)oi * d, d), oi, best, bj);
-                    if (in1) take_if_better(dist2_fp64(xrow, C + (int64_t)i1 * d, d), i1, best, bj);
-                    if (in2) take_if_better(dist2_fp64(xrow, C + (int64_t)i2 * d, d), i2, best, bj);
-                    atomicAdd(fp64_cnt, 1ull);
-                    if (in1 && in2) atomicAdd(wide_cnt, 1ull);
-                    if (bj == i1) { win = i1; wv = b1; }
-                    else if (bj == i2) { win = i2; wv = b2; }
-                } else if (i1 != INT_MAX && b1 < old) {
-                    win = i1; wv = b1;
-                }
-                if (win >= 0) { D2[R] = wv; idx[R] = win; }
-            }
+            if (decide_top2<MODE>(X, d, C, R, b1, i1, b2, i2, D2, idx, labels, prev, dmin, fp64_cnt, wide_cnt) &&
+                changed)
+                atomicAdd(changed, 1);
         }
     }
 }
@@ -636,13 +656,13 @@ cudaError_t count_fixups(Ctx &c) {
     return cudaGetLastError();
 }
 
-// Exact FP32 distance and decision for the rows whose nearest center the tensor
-// screening made certain (cand1 >= 0).  A warp takes 32 rows: asynchronous copies
-// (cp.async, no register staging) bring its 32 point rows and their 32 center rows
-// into shared memory, all in flight together; each lane then sums its own row in
-// the exact FP32 difference form, ascending coordinates, with 8-byte shared loads
-// (row stride = 2 mod 4: aligned and conflict-free).  The value is bit-identical
-// to dist2_fp32.
+// Exact FP32 distances and the decision for the rows the tensor screening has
+// brought down to one pair of adjacent centers (cand1 = the pair's first center,
+// -1: none).  Both centers of the pair get the exact FP32 difference form
+// (ascending coordinates, bit-identical to dist2_fp32); the row is certain when
+// every center outside the pair is, by the screening bound, beyond the tie window
+// of the pair's best exact value.  Certain rows take the CUDA-core decision
+// (decide_top2) on the pair; the others go to the fix-up list.
 __host__ __device__ __forceinline__ int refine_stride(int d) { return d + ((6 - (d & 3)) & 3); }   // = 2 mod 4
 
 __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
@@ -657,19 +677,21 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
                  "l"(src)
                  : "memory");
 }
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// The screening window test (the runner-up must be out of reach of the best once
-// the screening error E(x, c) = ep ||x'|| ||c'|| + en (||x'||^2 + ||c'||^2) and the
-// 2^-17 key truncation are allowed for; centers other than the best are bounded
-// by min(max ||c'||, ||x'|| + sqrt(d^2 bound of the best)) through the triangle
-// inequality, all norms taken after the anchor move) decides whether the best
-// center is certain; other rows go to the fix-up list.
 struct ScreenBound {
     const float *xnorm;            // ||x'||^2 per point (x' = x - anchor)
-    const float *cnorm;            // ||c'|| per center of the batch (local number)
     const unsigned int *cmax_bits; // max ||c'|| of the batch
-    const DevState *st;            // ROUND: batch begin
-    float ep, en;
+    const DevState *st;            // ROUND: batch range
+    float ep, en;                  // E(x, c) = ep ||x'|| ||c'|| + en (||x'||^2 + ||c'||^2)
     int32_t *fix_rows;
     int *fix_cnt;
 };
@@ -689,153 +711,142 @@ __device__ __forceinline__ void append_fixups(const ScreenBound &sb, bool fix, i
 // below 2^-17); twice that is allowed for
 constexpr float kKeyTrunc = 1.6e-5f;
 
-__device__ __forceinline__ bool screen_certain(const ScreenBound &sb, float xnorm, int jloc, float v1, float v2,
-                                               int d) {
+// The certainty test.  b1 = the pair's best exact FP32 d^2, v2 = the smallest
+// screened value (s = ||c'||^2 - 2 x'.c') outside the pair.  Any other center c
+// has d^2 = s + ||x'||^2 >= v2 - E(x, c) + ||x'||^2.  A center with ||c'|| >
+// ||x'|| + sqrt(b1 (1 + 2W)) is farther than b1 (1 + 2W) by the triangle
+// inequality; every nearer one has ||c'|| <= ceff, so E(x, c) <= Eo.  If the bound
+// exceeds b1 (1 + 2W), no FP32 value outside the pair can win or fall in the
+// tie window of the best (W = fp32_tie_window covers both FP32 errors).
+__device__ __forceinline__ bool pair_certain(const ScreenBound &sb, float xnorm, float b1, float v2, int d) {
     const float xn = fmaxf(xnorm, 0.f);
     const float X = sqrtf(xn);
     const float cmax = __uint_as_float(*sb.cmax_bits);
-    const float c1 = sb.cnorm[jloc];
-    const float E1 = sb.ep * X * c1 + sb.en * (xn + c1 * c1);
-    const float slack1 = fabsf(v1) * kKeyTrunc + E1;   // + key truncation
-    const float d1 = fmaxf(v1 + xn + slack1, 0.f);   // bound on the best center's d^2
     const float W = fp32_tie_window(d);
-    // a center with ||c'|| > ||x'|| + sqrt(d1 (1 + 2W)) is farther than d1 (1 + 2W)
-    // by the triangle inequality, outside the tie window of the best: only nearer
-    // centers need the error bound, and their ||c'|| is at most ceff
-    const float ceff = fminf(cmax, X + sqrtf(d1 * (1.f + 2.f * W)));
+    const float lim = fmaxf(b1, 0.f) * (1.f + 2.f * W);
+    const float ceff = fminf(cmax, X + sqrtf(lim));
     const float Eo = sb.ep * X * ceff + sb.en * (xn + ceff * ceff);
-    // v2 lowered by its key truncation; stays +inf when there is no runner-up
+    // v2 lowered by its key truncation; stays +inf when there is no other center
     const float v2lo = v2 >= 0.f ? v2 * (1.f - kKeyTrunc) : v2 * (1.f + kKeyTrunc);
-    return (v2lo - Eo) > (v1 + slack1 + W * d1 + 1e-30f);
+    return (v2lo - Eo + xn) > lim + 1e-30f;
 }
 
-// The decision once the certain best center j of row R has its exact FP32 value b1,
-// taken exactly as on the CUDA-core path: in a round it replaces the current
-// center only if nearer (an FP32 near tie is re-decided in FP64, equal FP64
-// values keep the lower center number); in Lloyd's assignment it is the label.
-// Returns 1 when the label changed.
-template <int MODE>
-__device__ __forceinline__ int refine_decide(const float *__restrict__ X, int d, const float *__restrict__ C,
-                                             int64_t R, int j, float b1, float *D2, int32_t *idx, int32_t *labels,
-                                             const int32_t *prev, float *dmin, unsigned long long *fp64_cnt) {
-    if (MODE == MODE_ROUND) {
-        const float old = D2[R];
-        const int oi = idx[R];
-        const float W = fp32_tie_window(d);
-        const float m32 = fminf(old, b1);
-        const float lim = m32 + W * m32;
-        if (old <= lim && b1 <= lim) {
-            const float *xg = X + R * d;
-            const double dold = dist2_fp64(xg, C + (int64_t)oi * d, d);
-            const double dnew = dist2_fp64(xg, C + (int64_t)j * d, d);
-            atomicAdd(fp64_cnt, 1ull);
-            if (dnew < dold || (dnew == dold && j < oi)) { D2[R] = b1; idx[R] = j; }
-        } else if (b1 < old) {
-            D2[R] = b1;
-            idx[R] = j;
+// exact FP32 difference form of one row against one center, both in shared memory
+// (8-byte loads when the row start is 8-byte aligned)
+__device__ __forceinline__ float dist2_smem(const float *xa, const float *ca, int d, bool pairs) {
+    float s = 0.f;
+    if (pairs) {
+        const float2 *x2 = reinterpret_cast<const float2 *>(xa);
+        const float2 *c2 = reinterpret_cast<const float2 *>(ca);
+#pragma unroll 4
+        for (int p = 0; p < (d >> 1); ++p) {
+            const float2 a = x2[p], c = c2[p];
+            float t = __fsub_rn(a.x, c.x);
+            s = __fmaf_rn(t, t, s);
+            t = __fsub_rn(a.y, c.y);
+            s = __fmaf_rn(t, t, s);
         }
-        return 0;
+        if (d & 1) {
+            const float t = __fsub_rn(xa[d - 1], ca[d - 1]);
+            s = __fmaf_rn(t, t, s);
+        }
     } else {
-        if (labels) labels[R] = j;
-        dmin[R] = b1;
-        return prev ? (prev[R] != j) : 0;
+#pragma unroll 4
+        for (int q = 0; q < d; ++q) {
+            const float t = __fsub_rn(xa[q], ca[q]);
+            s = __fmaf_rn(t, t, s);
+        }
     }
+    return s;
 }
 
+// the pair's exact values in (value, center number) order; i2 = -1 when the pair
+// has one real center
+__device__ __forceinline__ void pair_top2(float va, int ja, float vb, int jb, bool has_b, float &b1, int &i1,
+                                          float &b2, int &i2) {
+    if (has_b && (vb < va || (vb == va && jb < ja))) { b1 = vb; i1 = jb; b2 = va; i2 = ja; }
+    else { b1 = va; i1 = ja; b2 = has_b ? vb : FLT_MAX; i2 = has_b ? jb : -1; }
+}
+
+// Per-row copies: a warp takes 32 rows; asynchronous copies bring its 32 point
+// rows and their pairs of center rows into shared memory (row stride = 2 mod 4:
+// 8-byte aligned, conflict-free lane-per-row reads), then each lane sums its row.
 template <int MODE>
 __global__ void __launch_bounds__(256) refine_kernel(const float *__restrict__ X, int64_t n, int d,
-                                                    const float *__restrict__ C, const int32_t *__restrict__ cand1,
-                                                    const float *__restrict__ v1s, const float *__restrict__ v2s,
+                                                    const float *__restrict__ C, int c_cnt,
+                                                    const int32_t *__restrict__ cand1, const float *__restrict__ v2s,
                                                     ScreenBound sb, float *D2, int32_t *idx, int32_t *labels,
                                                     const int32_t *prev, int *changed, float *dmin,
-                                                    unsigned long long *fp64_cnt) {
+                                                    unsigned long long *fp64_cnt, unsigned long long *wide_cnt) {
     extern __shared__ __align__(16) float rsm[];
     const int ds = refine_stride(d);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float *xs = rsm + wid * 64 * ds;   // 32 point rows
-    float *cs = xs + 32 * ds;          // 32 center rows
+    float *xs = rsm + wid * 96 * ds;   // 32 point rows
+    float *cs = xs + 32 * ds;          // 32 pairs of center rows
     const int64_t w0 = (int64_t)blockIdx.x * blockDim.x + wid * 32;
     const int nw = (int)max((int64_t)0, min((int64_t)32, n - w0));
     const int64_t R = w0 + lane;
+    const int end = MODE == MODE_ROUND ? sb.st->batch_begin + sb.st->batch_cnt : c_cnt;
     int j = -1;
-    if (lane < nw) {
-        j = cand1[R];
-        const int begin = MODE == MODE_ROUND ? sb.st->batch_begin : 0;
-        if (j < 0 || !screen_certain(sb, sb.xnorm[R], j - begin, v1s[R], v2s[R], d)) j = -1;
-    }
-    append_fixups(sb, lane < nw && j < 0, R);
+    if (lane < nw) j = cand1[R];
     const bool even = (d & 1) == 0;   // rows 8-byte aligned in global memory
     for (int rr = 0; rr < nw; ++rr) {
         const int jr = __shfl_sync(0xffffffffu, j, rr);
         if (jr < 0) continue;
+        const int nc = jr + 1 < end ? 2 : 1;
         const float *xr = X + (w0 + rr) * d;
         const float *cr = C + (int64_t)jr * d;
+        float *ct = cs + 2 * rr * ds;
         if (even) {
             for (int p = lane; p < (d >> 1); p += 32) {
                 cp_async8(xs + rr * ds + 2 * p, xr + 2 * p);
-                cp_async8(cs + rr * ds + 2 * p, cr + 2 * p);
+                for (int u = 0; u < nc; ++u) cp_async8(ct + u * ds + 2 * p, cr + (int64_t)u * d + 2 * p);
             }
         } else {
             for (int q = lane; q < d; q += 32) {
                 cp_async4(xs + rr * ds + q, xr + q);
-                cp_async4(cs + rr * ds + q, cr + q);
+                for (int u = 0; u < nc; ++u) cp_async4(ct + u * ds + q, cr + (int64_t)u * d + q);
             }
         }
     }
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
     __syncwarp();
+    bool fix = lane < nw && j < 0;
     int chg = 0;
     if (lane < nw && j >= 0) {
-        const float *xa = xs + lane * ds, *ca = cs + lane * ds;
-        const float2 *x2 = reinterpret_cast<const float2 *>(xa);
-        const float2 *c2 = reinterpret_cast<const float2 *>(ca);
-        float b1 = 0.f;
-#pragma unroll 4
-        for (int p = 0; p < (d >> 1); ++p) {
-            const float2 a = x2[p], b = c2[p];
-            float t = __fsub_rn(a.x, b.x);
-            b1 = __fmaf_rn(t, t, b1);
-            t = __fsub_rn(a.y, b.y);
-            b1 = __fmaf_rn(t, t, b1);
-        }
-        if (d & 1) {
-            const float t = __fsub_rn(xa[d - 1], ca[d - 1]);
-            b1 = __fmaf_rn(t, t, b1);
-        }
-        chg = refine_decide<MODE>(X, d, C, R, j, b1, D2, idx, labels, prev, dmin, fp64_cnt);
+        const bool has_b = j + 1 < end;
+        const float *ct = cs + 2 * lane * ds;
+        const float va = dist2_smem(xs + lane * ds, ct, d, true);
+        const float vb = has_b ? dist2_smem(xs + lane * ds, ct + ds, d, true) : 0.f;
+        float b1, b2;
+        int i1, i2;
+        pair_top2(va, j, vb, j + 1, has_b, b1, i1, b2, i2);
+        if (pair_certain(sb, sb.xnorm[R], b1, v2s[R], d))
+            chg = decide_top2<MODE>(X, d, C, R, b1, i1, b2, i2, D2, idx, labels, prev, dmin, fp64_cnt, wide_cnt);
+        else
+            fix = true;
     }
+    append_fixups(sb, fix, R);
     if (MODE == MODE_ASSIGN && changed) {
         const int c = warp_sum_i32(chg);
         if (lane == 0 && c) atomicAdd(changed, c);
     }
 }
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
-                 "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// Refine with the pass's centers resident in shared memory (used when they fit and
-// the row stride gives conflict-free lane-per-row reads: d odd or d = 2 mod 4).
-// Persistent CTAs copy the centers once; each warp then walks 32-row blocks of X.
-// A block is contiguous in X, so flat 16-byte asynchronous copies bring it in,
-// double-buffered per warp.  Lane = row: the exact FP32 difference form reads the
-// row from the block and the center from the resident copy, so the value is
-// bit-identical to dist2_fp32.
+// Centers resident in shared memory (used when they fit and lane-per-row reads are
+// conflict-free: d odd or d = 2 mod 4).  Persistent CTAs copy the pass's centers
+// once; each warp then walks 32-row blocks of X.  A block is contiguous in X, so
+// flat 16-byte asynchronous copies bring it in, double-buffered per warp, and the
+// next block's screening results are loaded while the current block is summed.
 __host__ __device__ __forceinline__ int resident_center_floats(int cap_rows, int d) { return (cap_rows * d + 3) & ~3; }
 __host__ __device__ __forceinline__ int resident_block_floats(int d) { return (32 * d + 3) & ~3; }
 
 template <int MODE>
 __global__ void __launch_bounds__(512) refine_resident_kernel(
     const float *__restrict__ X, int64_t n, int d, const float *__restrict__ C, int cap_rows,
-    const int32_t *__restrict__ cand1, const float *__restrict__ v1s, const float *__restrict__ v2s, ScreenBound sb,
-    float *D2, int32_t *idx, int32_t *labels, const int32_t *prev, int *changed, float *dmin,
-    unsigned long long *fp64_cnt) {
+    const int32_t *__restrict__ cand1, const float *__restrict__ v2s, ScreenBound sb, float *D2, int32_t *idx,
+    int32_t *labels, const int32_t *prev, int *changed, float *dmin, unsigned long long *fp64_cnt,
+    unsigned long long *wide_cnt) {
     extern __shared__ __align__(16) float rsm[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int begin = MODE == MODE_ROUND ? sb.st->batch_begin : 0;
@@ -869,51 +880,54 @@ __global__ void __launch_bounds__(512) refine_resident_kernel(
             for (int f = lane; f < nf; f += 32) cp_async4(dst + f, src + f);
         }
     };
+    // screening results of block b for this lane's row
+    auto fetch = [&](int64_t b, int &j, float &v2, float &xn) {
+        const int64_t R = b * 32 + lane;
+        j = -1;
+        v2 = 0.f;
+        xn = 0.f;
+        if (b < nb && R < n) {
+            j = cand1[R];
+            v2 = v2s[R];
+            xn = sb.xnorm[R];
+        }
+    };
     if (gw < nb) issue(gw, xb);
     cp_async_commit();
+    int jn;
+    float v2n, xnn;
+    fetch(gw, jn, v2n, xnn);
     cp_async_wait<1>();   // the centers (the first block may still be in flight)
     __syncthreads();
-    const bool even = (d & 1) == 0;
+    const bool pairs = (d & 1) == 0;
     int chg = 0, it = 0;
     for (int64_t b = gw; b < nb; b += W, ++it) {
         const float *cur = xb + (it & 1) * xfl;
         if (b + W < nb) issue(b + W, xb + ((it + 1) & 1) * xfl);
         cp_async_commit();
-        const int64_t r0 = b * 32;
-        const int nr = (int)min((int64_t)32, n - r0);
-        const int64_t R = r0 + lane;
-        int j = -1;
-        if (lane < nr) {
-            j = cand1[R];
-            if (j < 0 || j - begin >= cnt || !screen_certain(sb, sb.xnorm[R], j - begin, v1s[R], v2s[R], d)) j = -1;
-        }
-        append_fixups(sb, lane < nr && j < 0, R);
+        int j = jn;
+        const float v2 = v2n, xn = xnn;
+        fetch(b + W, jn, v2n, xnn);
+        const int64_t R = b * 32 + lane;
+        const bool valid = R < n;
         cp_async_wait<1>();   // this block is in (the next one may be pending)
         __syncwarp();
-        if (j >= 0) {
+        bool fix = valid && (j < 0 || j - begin >= cnt);
+        if (valid && !fix) {
+            const bool has_b = j + 1 - begin < cnt;
             const float *xa = cur + lane * d;
             const float *ca = Cs + (int64_t)(j - begin) * d;
-            float b1 = 0.f;
-            if (even) {
-                const float2 *x2 = reinterpret_cast<const float2 *>(xa);
-                const float2 *c2 = reinterpret_cast<const float2 *>(ca);
-#pragma unroll 4
-                for (int p = 0; p < (d >> 1); ++p) {
-                    const float2 a = x2[p], c = c2[p];
-                    float t = __fsub_rn(a.x, c.x);
-                    b1 = __fmaf_rn(t, t, b1);
-                    t = __fsub_rn(a.y, c.y);
-                    b1 = __fmaf_rn(t, t, b1);
-                }
-            } else {
-#pragma unroll 4
-                for (int q = 0; q < d; ++q) {
-                    const float t = __fsub_rn(xa[q], ca[q]);
-                    b1 = __fmaf_rn(t, t, b1);
-                }
-            }
-            chg += refine_decide<MODE>(X, d, C, R, j, b1, D2, idx, labels, prev, dmin, fp64_cnt);
+            const float va = dist2_smem(xa, ca, d, pairs);
+            const float vb = has_b ? dist2_smem(xa, ca + d, d, pairs) : 0.f;
+            float b1, b2;
+            int i1, i2;
+            pair_top2(va, j, vb, j + 1, has_b, b1, i1, b2, i2);
+            if (pair_certain(sb, xn, b1, v2, d))
+                chg += decide_top2<MODE>(X, d, C, R, b1, i1, b2, i2, D2, idx, labels, prev, dmin, fp64_cnt, wide_cnt);
+            else
+                fix = true;
         }
+        append_fixups(sb, fix, R);
         __syncwarp();   // the buffer is refilled two blocks later
     }
     cp_async_wait<0>();
@@ -939,13 +953,14 @@ size_t resident_smem_bytes(int cap_rows, int d, int warps) {
     return sizeof(float) * ((size_t)resident_center_floats(cap_rows, d) + (size_t)warps * 2 * resident_block_floats(d));
 }
 
-// warps per refine CTA: 64 staged rows of refine_stride(d) floats each, within 200 KB
+// warps per refine CTA: 96 staged rows (32 points, 32 pairs of centers) of
+// refine_stride(d) floats each, within 200 KB
 int refine_warps(int d) {
-    const int w = (int)((200u * 1024u) / (64u * 4u * (unsigned)refine_stride(d)));
+    const int w = (int)((200u * 1024u) / (96u * 4u * (unsigned)refine_stride(d)));
     return w > 8 ? 8 : (w < 1 ? 1 : w);
 }
 
-size_t refine_smem_bytes(int d) { return sizeof(float) * refine_warps(d) * 64 * (size_t)refine_stride(d); }
+size_t refine_smem_bytes(int d) { return sizeof(float) * refine_warps(d) * 96 * (size_t)refine_stride(d); }
 
 cudaError_t configure_refine_kernels() {
     // the tensor passes support d + 2 <= 192: refine tiles of 256 rows of up to 190 floats
@@ -980,14 +995,14 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
     p.X = c.X; p.n = c.n; p.d = c.d; p.split = split;
     p.ximg = c.tc_ximg; p.xnorm = c.tc_xnorm;
     p.Cf = C; p.cnt = k; p.st = c.st; p.bimg = c.tc_img; p.cnorm = c.tc_cnorm; p.cmax_bits = c.tc_cmax;
-    p.cand1 = c.cand1; p.v1 = c.tc_v1; p.v2 = c.tc_v2; p.fix_rows = c.fix_rows; p.fix_cnt = c.fix_cnt;
+    p.cand1 = c.cand1; p.v2 = c.tc_v2; p.fix_rows = c.fix_rows; p.fix_cnt = c.fix_cnt;
     p.fp64_cnt = &c.st->argmin_fp64; p.err = c.tc_err;
     cudaEvent_t ev = nullptr;
     if ((e = timing_begin(c, &ev)) != cudaSuccess) return e;
     if ((e = tc::launch_nearest_tc(p, mode_round, c.num_sms, c.stream)) != cudaSuccess) return e;
     if ((e = timing_end(c, ev, timing_cls)) != cudaSuccess) return e;
     ScreenBound sb{};
-    sb.xnorm = c.tc_xnorm; sb.cnorm = c.tc_cnorm; sb.cmax_bits = c.tc_cmax; sb.st = c.st;
+    sb.xnorm = c.tc_xnorm; sb.cmax_bits = c.tc_cmax; sb.st = c.st;
     sb.fix_rows = c.fix_rows; sb.fix_cnt = c.fix_cnt;
     tc::tc_bound(c.d, split, &sb.ep, &sb.en);
     const int cap_rows = mode_round ? c.cap_round : k;
@@ -998,12 +1013,12 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(c.num_sms, (nb + rw - 1) / rw));
         if (mode_round)
             refine_resident_kernel<MODE_ROUND><<<grid, 32 * rw, rsm, c.stream>>>(
-                c.X, c.n, c.d, C, cap_rows, c.cand1, c.tc_v1, c.tc_v2, sb, c.D2, c.idx, nullptr, nullptr, nullptr,
-                nullptr, &c.st->argmin_fp64);
+                c.X, c.n, c.d, C, cap_rows, c.cand1, c.tc_v2, sb, c.D2, c.idx, nullptr, nullptr, nullptr, nullptr,
+                &c.st->argmin_fp64, &c.st->argmin_wide);
         else
             refine_resident_kernel<MODE_ASSIGN><<<grid, 32 * rw, rsm, c.stream>>>(
-                c.X, c.n, c.d, C, cap_rows, c.cand1, c.tc_v1, c.tc_v2, sb, nullptr, nullptr, labels, prev, changed,
-                dmin, &c.st->argmin_fp64);
+                c.X, c.n, c.d, C, cap_rows, c.cand1, c.tc_v2, sb, nullptr, nullptr, labels, prev, changed, dmin,
+                &c.st->argmin_fp64, &c.st->argmin_wide);
         count_launches(1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = count_fixups(c)) != cudaSuccess) return e;
@@ -1013,13 +1028,13 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
     const int grid = (int)((c.n + rthreads - 1) / rthreads);
     const size_t rsm = refine_smem_bytes(c.d);
     if (mode_round)
-        refine_kernel<MODE_ROUND><<<grid, rthreads, rsm, c.stream>>>(c.X, c.n, c.d, C, c.cand1, c.tc_v1, c.tc_v2, sb,
-                                                                     c.D2, c.idx, nullptr, nullptr, nullptr, nullptr,
-                                                                     &c.st->argmin_fp64);
+        refine_kernel<MODE_ROUND><<<grid, rthreads, rsm, c.stream>>>(c.X, c.n, c.d, C, 0, c.cand1, c.tc_v2, sb, c.D2,
+                                                                     c.idx, nullptr, nullptr, nullptr, nullptr,
+                                                                     &c.st->argmin_fp64, &c.st->argmin_wide);
     else
-        refine_kernel<MODE_ASSIGN><<<grid, rthreads, rsm, c.stream>>>(c.X, c.n, c.d, C, c.cand1, c.tc_v1, c.tc_v2, sb,
+        refine_kernel<MODE_ASSIGN><<<grid, rthreads, rsm, c.stream>>>(c.X, c.n, c.d, C, k, c.cand1, c.tc_v2, sb,
                                                                       nullptr, nullptr, labels, prev, changed, dmin,
-                                                                      &c.st->argmin_fp64);
+                                                                      &c.st->argmin_fp64, &c.st->argmin_wide);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = count_fixups(c)) != cudaSuccess) return e;

@@ -139,7 +139,11 @@ KMPAR_API kmpar_status kmpar_weight(kmpar_ctx *ctx, int64_t *m_out, const int32_
  * sum exceeds the target.  Writes the k chosen rows to centers_dev (device, k x d
  * FP32, caller-owned).  Requires kmpar_weight.  Returns KMPAR_WARN_FEW_CANDIDATES
  * (centers still written, remaining draws repeat the first center) if the mass
- * ran out before k draws.  Synchronises.
+ * ran out before k draws.  Synchronises.  Candidate sets that fit one
+ * thread-block cluster's shared memory run in a cluster kernel, larger ones in a
+ * cooperative grid kernel; setting the environment variable KMPAR_RECLUSTER_GRID
+ * to 1 selects the grid kernel for every size (same draws up to reported near
+ * ties).
  */
 KMPAR_API kmpar_status kmpar_recluster(kmpar_ctx *ctx, float *centers_dev);
 

@@ -237,65 +237,95 @@ __global__ void prep_centers_kernel(const float *__restrict__ C, int d, int spli
     }
 }
 
-// One thread per (padded) point row: ||x'||^2 (FP32, ascending) and the row's
-// KA x 8 swizzled chunks of the A image [row tile][katom][128 rows][128 B]
-// (x' = x - anchor).
-__global__ void prep_points_kernel(const float *__restrict__ X, int64_t n, int64_t n_pad, int d, int split, int KA,
-                                   const float *__restrict__ anchor, uint8_t *__restrict__ img,
-                                   float *__restrict__ xnorm) {
+// One CTA per 128-row tile of the A image [row tile][katom][128 rows][128 B]: the
+// tile's rows (contiguous in X) come into shared memory with coalesced loads; then
+// eight consecutive threads build the eight 16-byte chunks of one row segment of an
+// atom (position p of row r holds logical chunk p ^ (r & 7)), so the stores are
+// coalesced too; thread r sums ||x'||^2 of row r (FP32, ascending; x' = x - anchor).
+__global__ void __launch_bounds__(128) prep_points_kernel(const float *__restrict__ X, int64_t n, int64_t n_pad, int d,
+                                                          int split, int KA, const float *__restrict__ anchor,
+                                                          uint8_t *__restrict__ img, float *__restrict__ xnorm) {
+    extern __shared__ float xsm[];   // BM x d
     const Enc e{d, split, anchor};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x) {
-        const bool valid = i < n;
-        const float *x = X + (valid ? i : 0) * (int64_t)d;
-        float xn = 0.f;
-        if (valid)
-            for (int q = 0; q < d; ++q) {
-                const float v = moved(e, x, q);
-                xn = __fmaf_rn(v, v, xn);
-            }
-        xnorm[i] = xn;
-        const int64_t t = i / BM;
-        const int r = (int)(i % BM);
+    const int64_t ntile = n_pad / BM;
+    for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+        const int64_t r0 = t * BM;
+        const int nr = (int)max((int64_t)0, min((int64_t)BM, n - r0));
+        __syncthreads();   // the previous tile's readers are done
+        for (int f = threadIdx.x; f < nr * d; f += BM) xsm[f] = __ldg(X + r0 * d + f);
+        __syncthreads();
+        {
+            const int r = threadIdx.x;
+            float xn = 0.f;
+            if (r < nr)
+                for (int q = 0; q < d; ++q) {
+                    const float v = moved(e, xsm + r * d, q);
+                    xn = __fmaf_rn(v, v, xn);
+                }
+            xnorm[r0 + r] = xn;
+        }
         uint8_t *tile = img + (size_t)t * KA * BM * 128;
-        for (int a = 0; a < KA; ++a) {
-            for (int ch = 0; ch < 8; ++ch) {
+        const int pos = threadIdx.x & 7;
+        for (int a = 0; a < KA; ++a)
+            for (int r = threadIdx.x >> 3; r < BM; r += BM / 8) {
+                const int ch = pos ^ (r & 7);
                 __nv_bfloat16 v[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = valid ? a_elem(e, x, a * 64 + ch * 8 + q) : bf(0.f);
-                *reinterpret_cast<uint4 *>(tile + (size_t)a * BM * 128 + sw128_off(r, ch)) = pack8(v);
+                for (int q = 0; q < 8; ++q) v[q] = r < nr ? a_elem(e, xsm + r * d, a * 64 + ch * 8 + q) : bf(0.f);
+                *reinterpret_cast<uint4 *>(tile + (size_t)a * BM * 128 + r * 128 + pos * 16) = pack8(v);
             }
-        }
     }
 }
 
 // ------------------------------------------------------------------ anchor
 // Column means of X, the anchor both operands are moved by.  Any anchor gives the
 // same decisions (distances do not depend on it); the mean keeps ||x'|| small.
-// Fixed row chunks per block and a fixed summation order make it deterministic.
-constexpr int kAnchorBlocks = 256;
+// kAnchorBlocks fixed row chunks; in a block, thread (ty, tx) sums column
+// cc + tx over the chunk's rows ty, ty + 4, ... (warps read 32 consecutive
+// floats of a row); the four row phases, then the chunks, are added in a fixed
+// order, so the result is deterministic.
+constexpr int kAnchorBlocks = 1024;
 
-__global__ void anchor_partial_kernel(const float *__restrict__ X, int64_t n, int d, double *__restrict__ part) {
+__global__ void __launch_bounds__(256) anchor_partial_kernel(const float *__restrict__ X, int64_t n, int d,
+                                                             double *__restrict__ part) {
+    __shared__ double ph[4][64];
     const int64_t chunk = (n + kAnchorBlocks - 1) / kAnchorBlocks;
     const int64_t r0 = (int64_t)blockIdx.x * chunk;
     const int64_t r1 = min(n, r0 + chunk);
-    for (int q = threadIdx.x; q < d; q += blockDim.x) {
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+    for (int cc = 0; cc < d; cc += 64) {
+        const int q = cc + tx;
         double s0 = 0.0, s1 = 0.0;
-        int64_t r = r0;
-        for (; r + 1 < r1; r += 2) {
-            s0 += (double)X[r * d + q];
-            s1 += (double)X[(r + 1) * d + q];
+        if (q < d) {
+            int64_t r = r0 + ty;
+            for (; r + 4 < r1; r += 8) {
+                s0 += (double)__ldg(X + r * d + q);
+                s1 += (double)__ldg(X + (r + 4) * d + q);
+            }
+            if (r < r1) s0 += (double)__ldg(X + r * d + q);
         }
-        if (r < r1) s0 += (double)X[r * d + q];
-        part[(size_t)blockIdx.x * d + q] = s0 + s1;
+        ph[ty][tx] = s0 + s1;
+        __syncthreads();
+        if (ty == 0 && q < d) part[(size_t)blockIdx.x * d + q] = ((ph[0][tx] + ph[1][tx]) + ph[2][tx]) + ph[3][tx];
+        __syncthreads();
     }
 }
 
-__global__ void anchor_final_kernel(const double *__restrict__ part, int64_t n, int d, float *__restrict__ anchor) {
-    for (int q = threadIdx.x; q < d; q += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < kAnchorBlocks; ++b) s += part[(size_t)b * d + q];
-        anchor[q] = n > 0 ? (float)(s / (double)n) : 0.f;
+// one block per column: thread t adds chunks t, t + 256, ... in order, then a fixed
+// pairwise tree over the 256 partial sums
+__global__ void __launch_bounds__(256) anchor_final_kernel(const double *__restrict__ part, int64_t n, int d,
+                                                           float *__restrict__ anchor) {
+    __shared__ double red[256];
+    const int q = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < kAnchorBlocks; b += 256) s += part[(size_t)b * d + q];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) anchor[q] = n > 0 ? (float)(red[0] / (double)n) : 0.f;
 }
 
 // ------------------------------------------------------------------ the pass
@@ -449,13 +479,20 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p) {
                     const int buf = g & 1;
                     if (!wait_bar(&sm.acc_empty[buf], ((g >> 1) & 1) ^ 1, abort, p.err, 15)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t a0 = su32(a16 + ab * C::A16_BYTES);
-                    const uint32_t b0 = su32(bst + s * C::B_BYTES);
-                    for (int ks = 0; ks < ksteps; ++ks) {
-                        const int at = ks >> 2;
-                        const uint32_t off = (uint32_t)(ks & 3) * 32u;
-                        mma_bf16(tmem + (uint32_t)(buf * BN), sw128_desc(a0 + at * (BM * 128) + off),
-                                 sw128_desc(b0 + at * (BN * 128) + off), idesc, ks > 0 ? 1u : 0u);
+                    // descriptors: the start-address field is (address >> 4) in the low
+                    // bits, so each K step adds a compile-time constant to the tile's base
+                    // descriptor (this thread shares its SMSP with ALU-heavy epilogue
+                    // warps: few ALU instructions per MMA keep the tensor pipe fed)
+                    const uint64_t ad0 = sw128_desc(su32(a16 + ab * C::A16_BYTES));
+                    const uint64_t bd0 = sw128_desc(su32(bst + s * C::B_BYTES));
+                    const uint32_t dt = tmem + (uint32_t)(buf * BN);
+#pragma unroll
+                    for (int ks = 0; ks < KA * 4; ++ks) {
+                        if (ks < ksteps) {
+                            const uint64_t ao = (uint64_t)(((ks >> 2) * (BM * 128) + (ks & 3) * 32) >> 4);
+                            const uint64_t bo = (uint64_t)(((ks >> 2) * (BN * 128) + (ks & 3) * 32) >> 4);
+                            mma_bf16(dt, ad0 + ao, bd0 + bo, idesc, ks > 0 ? 1u : 0u);
+                        }
                     }
                     mma_commit(&sm.acc_full[buf]);
                     if (!resident) { mma_commit(&sm.b_empty[s]); ++bt; }
@@ -639,8 +676,8 @@ size_t tc_points_image_bytes(int d, int split, int64_t n) {
 size_t tc_anchor_scratch_doubles(int d) { return (size_t)kAnchorBlocks * d; }
 
 cudaError_t launch_anchor(const float *X, int64_t n, int d, double *scratch, float *anchor, cudaStream_t s) {
-    anchor_partial_kernel<<<kAnchorBlocks, 64, 0, s>>>(X, n, d, scratch);
-    anchor_final_kernel<<<1, 128, 0, s>>>(scratch, n, d, anchor);
+    anchor_partial_kernel<<<kAnchorBlocks, 256, 0, s>>>(X, n, d, scratch);
+    anchor_final_kernel<<<d, 256, 0, s>>>(scratch, n, d, anchor);
     count_launches(2);
     return cudaGetLastError();
 }
@@ -648,8 +685,11 @@ cudaError_t launch_anchor(const float *X, int64_t n, int d, double *scratch, flo
 cudaError_t launch_prep_points(const float *X, int64_t n, int d, int split, const float *anchor, uint8_t *img,
                                float *xnorm, cudaStream_t s) {
     const int64_t n_pad = ((n + BM - 1) / BM) * BM;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n_pad + 127) / 128, 8192));
-    prep_points_kernel<<<grid, 128, 0, s>>>(X, n, n_pad, d, split, tc_katoms(d, split), anchor, img, xnorm);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n_pad / BM, 8192));
+    const size_t sm = sizeof(float) * BM * (size_t)d;
+    cudaError_t e = cudaFuncSetAttribute(prep_points_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    prep_points_kernel<<<grid, BM, sm, s>>>(X, n, n_pad, d, split, tc_katoms(d, split), anchor, img, xnorm);
     count_launches(1);
     return cudaGetLastError();
 }

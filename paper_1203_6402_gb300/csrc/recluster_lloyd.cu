@@ -9,6 +9,7 @@
 #include <float.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "kmpar_internal.cuh"
 
@@ -244,8 +245,287 @@ __global__ void __launch_bounds__(kRcThreads) recluster_kernel(const float *__re
     }
 }
 
+// ------------------------------------------------------------------ step 8, one cluster
+// The same draws for candidate sets whose rows fit the shared memory of one
+// thread-block cluster (kClSize CTAs of 1024 threads).  CTA r owns the fixed
+// chunk range [r cpc, (r+1) cpc) of 32-candidate chunks and keeps their rows,
+// weights and D^2 in its shared memory.  Per draw:
+//   A  warp scans of the masses of the CTA's chunks, the CTA total (chunks in
+//      order)                                             ... cluster barrier
+//   B  every CTA reads the CTA totals over distributed shared memory in rank
+//      order (FP64): total, target u_t * total, the owning CTA; the owner finds
+//      the chunk and the candidate as recluster_kernel does (same near-tie and
+//      rounding rules) and writes the pick into every CTA   ... cluster barrier
+//   C  every CTA: D^2_j <- min(D^2_j, ||c_j - c_pick||^2) for its candidates.
+// Hardware cluster barriers replace the grid barrier and the published flag;
+// every CTA takes the same branches (the totals it reads are the same), so all
+// of them reach every barrier.
+constexpr int kClSize = 8;
+constexpr int kClThreads = 1024;
+
+__device__ __forceinline__ uint32_t cl_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cl_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cl_map(const void *p, uint32_t rank) {
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(a)
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    return a;
+}
+__device__ __forceinline__ double cl_ld_f64(uint32_t a) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void cl_st_s32(uint32_t a, int v) {
+    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+// shared memory of one CTA: chunk totals, the picked row, D^2, weights (FP64), rows
+// (stride cl_stride(d): 8-byte aligned, conflict-free lane-per-row reads)
+__host__ __device__ __forceinline__ int cl_stride(int d) { return (d & 1) ? d : d + ((6 - (d & 3)) & 3); }
+__host__ __device__ __forceinline__ size_t cl_smem_bytes(int cpc, int d, bool rows) {
+    const size_t dp = (size_t)((d + 3) & ~3);
+    return sizeof(double) * cpc + sizeof(float) * dp + sizeof(float) * 32 * (size_t)cpc +
+           sizeof(double) * 32 * (size_t)cpc + (rows ? sizeof(float) * 32 * (size_t)cpc * cl_stride(d) : 0) +
+           sizeof(int) * (size_t)cpc;
+}
+
+// exact FP32 difference form, row in shared memory (8-byte loads for even d)
+__device__ __forceinline__ float cl_dist2(const float *x, const float *c, int d) {
+    float s = 0.f;
+    if ((d & 1) == 0) {
+        const float2 *x2 = reinterpret_cast<const float2 *>(x), *c2 = reinterpret_cast<const float2 *>(c);
+#pragma unroll 4
+        for (int p = 0; p < (d >> 1); ++p) {
+            const float2 a = x2[p], b = c2[p];
+            float t = __fsub_rn(a.x, b.x);
+            s = __fmaf_rn(t, t, s);
+            t = __fsub_rn(a.y, b.y);
+            s = __fmaf_rn(t, t, s);
+        }
+    } else {
+#pragma unroll 4
+        for (int q = 0; q < d; ++q) {
+            const float t = __fsub_rn(x[q], c[q]);
+            s = __fmaf_rn(t, t, s);
+        }
+    }
+    return s;
+}
+
+// FP64 sum of v[0..n) by one warp in a fixed order: lane l adds v[l], v[l + 32],
+// ... in order, then a fixed butterfly; every lane gets the total
+__device__ __forceinline__ double warp_sum_fixed(const double *v, int n, int lane) {
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+__global__ void __launch_bounds__(kClThreads, 1)
+    recluster_cluster_kernel(const float *__restrict__ C, const long long *__restrict__ w, DevState *st, int d, int k,
+                             uint64_t seed, int cpc_cap, int rows_in_smem, int32_t *chosen, float *centers) {
+    extern __shared__ __align__(16) unsigned char csm[];
+    double *cm = reinterpret_cast<double *>(csm);                       // chunk totals
+    float *cnew = reinterpret_cast<float *>(cm + cpc_cap);               // picked row
+    float *rd2 = cnew + ((d + 3) & ~3);                                  // D^2 of own candidates
+    double *wl = reinterpret_cast<double *>(rd2 + 32 * cpc_cap);         // weights
+    float *crow = reinterpret_cast<float *>(wl + 32 * cpc_cap);          // rows (rows_in_smem)
+    // per chunk: some D^2 fell in the last draw, so its masses must be scanned again
+    int *dirty = reinterpret_cast<int *>(crow + (rows_in_smem ? 32 * (size_t)cpc_cap * cl_stride(d) : 0));
+    __shared__ double s_ctot, s_pre, s_total, s_target;
+    __shared__ int s_pick, s_owner, s_miss;
+    const int rank = (int)cl_rank();
+    const int t_id = threadIdx.x, lane = t_id & 31, wid = t_id >> 5;
+    const int m = st->m;
+    const int nchunk = (m + 31) / 32;
+    const int cpc = min(cpc_cap, (nchunk + kClSize - 1) / kClSize);   // balanced over the CTAs
+    const int c0 = min(nchunk, rank * cpc), c1 = min(nchunk, c0 + cpc);
+    const int nc = c1 - c0;
+    const int j0 = c0 * 32, j1 = min(m, c1 * 32);
+    const int rs = rows_in_smem ? cl_stride(d) : d;
+    for (int j = j0 + t_id; j < j1; j += kClThreads) wl[j - j0] = (double)w[j];
+    if (rows_in_smem)
+        for (int f = t_id; f < (j1 - j0) * d; f += kClThreads) {
+            const int jr = f / d, q = f - jr * d;
+            crow[jr * rs + q] = C[(int64_t)j0 * d + f];
+        }
+    const float *rows = rows_in_smem ? crow : C + (int64_t)j0 * d;
+    for (int i = t_id; i < cpc_cap; i += kClThreads) dirty[i] = 1;
+    __syncthreads();
+    for (int step = 0; step < k; ++step) {
+        // ---- A: chunk masses and the CTA total.  A chunk none of whose D^2 fell in
+        // the last draw keeps its total: rescanning it would give the same value.
+        for (int ch = c0 + wid; ch < c1; ch += kClThreads / 32) {
+            if (!dirty[ch - c0]) continue;   // uniform per warp
+            const int j = ch * 32 + lane;
+            double e = 0.0;
+            if (j < m) e = step == 0 ? wl[j - j0] : __dmul_rn(wl[j - j0], (double)rd2[j - j0]);
+            const double incl = warp_incl_scan_f64(e, lane);
+            if (lane == 31) cm[ch - c0] = incl;
+            __syncwarp();
+            if (lane == 0) dirty[ch - c0] = 0;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            const double s = warp_sum_fixed(cm, nc, lane);
+            if (lane == 0) s_ctot = s;
+        }
+        cl_sync();
+        // ---- B: totals in rank order, the owning CTA
+        if (wid == 0) {
+            const double v = lane < kClSize ? cl_ld_f64(cl_map(&s_ctot, lane)) : 0.0;
+            const double pre = warp_incl_scan_f64(v, lane);
+            const double total = __shfl_sync(0xffffffffu, pre, kClSize - 1);
+            if (lane == 0) s_total = total;
+            if (total > 0.0) {
+                const double target = __dmul_rn(uniform53((uint64_t)step, 0, TAG_RECLUSTER, seed), total);
+                // only CTAs with positive mass can own the draw (a scan prefix is not
+                // monotone bit for bit, so the first prefix above the target could
+                // otherwise belong to an empty CTA)
+                const unsigned hit = __ballot_sync(0xffffffffu, lane < kClSize && v > 0.0 && pre > target);
+                const unsigned pos = __ballot_sync(0xffffffffu, lane < kClSize && v > 0.0);
+                const int owner = hit ? __ffs(hit) - 1 : 31 - __clz(pos);
+                const double excl = __shfl_up_sync(0xffffffffu, pre, 1);   // exclusive prefix
+                const double before = __shfl_sync(0xffffffffu, lane > 0 ? excl : 0.0, owner);
+                if (lane == 0) {
+                    s_target = target;
+                    s_owner = owner;
+                    s_miss = hit ? 0 : 1;
+                    s_pre = before;
+                }
+            }
+        }
+        __syncthreads();
+        const double total = s_total;
+        if (!(total > 0.0)) {
+            // positive mass exhausted: the remaining draws repeat the first center
+            if (rank == 0) {
+                for (int s = step + t_id; s < k; s += kClThreads) chosen[s] = step > 0 ? chosen[0] : 0;
+                if (t_id == 0) st->warn = 1;
+                __syncthreads();
+                const int src = step > 0 ? chosen[0] : 0;
+                for (int s = step; s < k; ++s)
+                    for (int qq = t_id; qq < d; qq += kClThreads) centers[(int64_t)s * d + qq] = C[(int64_t)src * d + qq];
+            }
+            cl_sync();   // no CTA leaves while another may still read its shared memory
+            return;
+        }
+        if (rank == s_owner && wid == 0) {
+            const double target = s_target;
+            bool miss = s_miss != 0;
+            // the chunk whose running prefix first exceeds the target: chunk totals in
+            // groups of 32, scanned in order (the last chunk with positive mass when
+            // rounding hides the crossing)
+            int ch = -1;
+            double pre = 0.0, run = s_pre;
+            for (int g0 = 0; g0 < nc && ch < 0 && !miss; g0 += 32) {
+                const double v = g0 + lane < nc ? cm[g0 + lane] : 0.0;
+                const double incl = run + warp_incl_scan_f64(v, lane);
+                const unsigned hit = __ballot_sync(0xffffffffu, g0 + lane < nc && v > 0.0 && incl > target);
+                if (hit) {
+                    const int l = __ffs(hit) - 1;
+                    ch = g0 + l;
+                    pre = __shfl_sync(0xffffffffu, incl - v, l);
+                }
+                run = __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (ch < 0) {
+                for (int g0 = ((nc - 1) / 32) * 32; g0 >= 0 && ch < 0; g0 -= 32) {
+                    const unsigned pos = __ballot_sync(0xffffffffu, g0 + lane < nc && cm[g0 + lane] > 0.0);
+                    if (pos) ch = g0 + 31 - __clz(pos);
+                }
+                miss = true;
+            }
+            const int chunk = c0 + ch;
+            const int j = chunk * 32 + lane;
+            double e = 0.0;
+            if (j < m) e = step == 0 ? wl[j - j0] : __dmul_rn(wl[j - j0], (double)rd2[j - j0]);
+            const double incl = warp_incl_scan_f64(e, lane);
+            const double cum = pre + incl, cum0 = pre + (incl - e);
+            const unsigned hit = miss ? 0u : __ballot_sync(0xffffffffu, j < m && e > 0.0 && cum > target);
+            const unsigned pos = __ballot_sync(0xffffffffu, j < m && e > 0.0);   // nonzero: the chunk has mass
+            const int pick = hit ? chunk * 32 + __ffs(hit) - 1 : chunk * 32 + 31 - __clz(pos);
+            if (hit) {
+                const bool near = fabs(target - cum0) <= 1e-6 * total || fabs(cum - target) <= 1e-6 * total;
+                if (lane == __ffs(hit) - 1 && near) atomicAdd(&st->recluster_near, 1ull);
+            } else if (lane == 0) {
+                atomicAdd(&st->recluster_near, 1ull);
+            }
+            if (lane < kClSize) cl_st_s32(cl_map(&s_pick, lane), pick);
+            if (lane == 0) chosen[step] = pick;
+        }
+        cl_sync();
+        // ---- C: the picked row and the D^2 update
+        const int pick = s_pick;
+        for (int qq = t_id; qq < d; qq += kClThreads) {
+            const float v = C[(int64_t)pick * d + qq];
+            cnew[qq] = v;
+            if (rank == 0) centers[(int64_t)step * d + qq] = v;
+        }
+        __syncthreads();
+        for (int j = j0 + t_id; j < j1; j += kClThreads) {
+            const float v = rows_in_smem ? cl_dist2(rows + (int64_t)(j - j0) * rs, cnew, d)
+                                         : dist2_fp32(rows + (int64_t)(j - j0) * d, cnew, d);
+            if (step == 0 || v < rd2[j - j0]) {
+                rd2[j - j0] = v;
+                dirty[(j - j0) >> 5] = 1;
+            }
+        }
+        __syncthreads();
+    }
+    cl_sync();   // no CTA leaves while another may still read its shared memory
+}
+
+// the cluster form applies when the largest candidate set's chunks fit the CTAs'
+// shared memory (rows in shared memory when they fit too)
+static bool cluster_plan(const Ctx &c, int *cpc, int *rows) {
+    const int max_chunks = (c.cap_total + 31) / 32;
+    *cpc = (max_chunks + kClSize - 1) / kClSize;
+    const size_t budget = 200u * 1024u;
+    *rows = cl_smem_bytes(*cpc, c.d, true) <= budget ? 1 : 0;
+    return cl_smem_bytes(*cpc, c.d, false) <= budget && (size_t)c.cap_total * c.d <= (4u << 20);
+}
+
+cudaError_t launch_recluster_cluster(Ctx &c, float *centers, int cpc, int rows) {
+    const size_t smem = cl_smem_bytes(cpc, c.d, rows != 0);
+    cudaError_t e = cudaFuncSetAttribute(recluster_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kClSize);
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClSize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, recluster_cluster_kernel, (const float *)c.C, (const long long *)c.w, c.st, c.d,
+                           c.k, c.seed, cpc, rows, c.chosen, centers);
+    count_launches(1);
+    return e;
+}
+
 cudaError_t launch_recluster(Ctx &c, float *centers) {
     cudaError_t e;
+    int cpc = 0, rows = 0;
+    // KMPAR_RECLUSTER_GRID=1 selects the cooperative grid form for every size (both
+    // forms are tested against the oracle)
+    const char *force_grid = std::getenv("KMPAR_RECLUSTER_GRID");
+    const bool grid_only = force_grid && force_grid[0] == '1';
+    if (!grid_only && cluster_plan(c, &cpc, &rows)) return launch_recluster_cluster(c, centers, cpc, rows);
     if ((e = cudaMemsetAsync(c.rc_sync, 0, sizeof(RcSync), c.stream)) != cudaSuccess) return e;
     const size_t smem = sizeof(float) * (size_t)c.d;
     // co-resident CTAs: one per SM at most, no more than there are chunks

@@ -539,112 +539,6 @@ __device__ __forceinline__ int decide_top2(const float *__restrict__ X, int d, c
     }
 }
 
-// Rows whose screening window held more than one center, finished exactly: a CTA
-// takes 8 listed rows (one warp each) and streams tiles of 64 centers through
-// shared memory; the lanes of a warp split each tile's centers and sum the exact
-// FP32 difference form in ascending coordinates, reading the warp's point row
-// (broadcast) and their center rows with 8-byte loads (row stride = 2 mod 4:
-// aligned and conflict-free); a lexicographic top-2 merge across lanes follows,
-// then the same decision as nearest_kernel.  Persistent: the row count is read on
-// the device.
-constexpr int kFixTile = 64;
-
-__host__ __device__ __forceinline__ int fix_stride(int d) { return d + ((6 - (d & 3)) & 3); }   // = 2 mod 4
-
-// exact FP32 difference form over two 8-byte-aligned rows
-__device__ __forceinline__ float dist2_fp32_pairs(const float *__restrict__ x, const float *__restrict__ c, int d) {
-    const float2 *x2 = reinterpret_cast<const float2 *>(x);
-    const float2 *c2 = reinterpret_cast<const float2 *>(c);
-    float s = 0.f;
-    const int dp = d >> 1;
-#pragma unroll 4
-    for (int p = 0; p < dp; ++p) {
-        const float2 a = x2[p], b = c2[p];
-        float t = __fsub_rn(a.x, b.x);
-        s = __fmaf_rn(t, t, s);
-        t = __fsub_rn(a.y, b.y);
-        s = __fmaf_rn(t, t, s);
-    }
-    if (d & 1) {
-        const float t = __fsub_rn(x[d - 1], c[d - 1]);
-        s = __fmaf_rn(t, t, s);
-    }
-    return s;
-}
-
-template <int MODE>
-__global__ void __launch_bounds__(256) fixup_tile_kernel(const float *__restrict__ X, int d,
-                                                        const float *__restrict__ C, int c_cnt, const DevState *st,
-                                                        const int32_t *__restrict__ rows, const int *rows_cnt,
-                                                        float *D2, int32_t *idx, int32_t *labels, const int32_t *prev,
-                                                        int *changed, float *dmin, unsigned long long *fp64_cnt,
-                                                        unsigned long long *wide_cnt) {
-    extern __shared__ __align__(16) float fsm[];
-    const int ds = fix_stride(d);
-    float *ct = fsm;                       // kFixTile x ds center rows
-    float *xs_all = fsm + kFixTile * ds;   // 8 x ds point rows
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nrows = *rows_cnt;
-    const int begin = MODE == MODE_ROUND ? st->batch_begin : 0;
-    const int cnt = MODE == MODE_ROUND ? st->batch_cnt : c_cnt;
-    const float FMAX = FLT_MAX;
-    for (int g0 = blockIdx.x * 8; g0 < nrows; g0 += gridDim.x * 8) {   // uniform per block
-        const int g = g0 + wid;
-        const bool valid = g < nrows;
-        const int64_t R = valid ? rows[g] : 0;
-        float *xs = xs_all + wid * ds;
-        const float *xrow = X + R * d;
-        if (valid)
-            for (int q = lane; q < d; q += 32) xs[q] = __ldg(xrow + q);
-        float b1 = FMAX, b2 = FMAX;
-        int i1 = INT_MAX, i2 = INT_MAX;
-        for (int t0 = 0; t0 < cnt; t0 += kFixTile) {
-            const int nt = min(kFixTile, cnt - t0);
-            __syncthreads();
-            stage_rows(ct, ds, C + (int64_t)(begin + t0) * d, nt, d, threadIdx.x, 256);
-            __syncthreads();
-            if (valid)
-                for (int rr = lane; rr < nt; rr += 32) {
-                    const float v = dist2_fp32_pairs(xs, ct + rr * ds, d);
-                    const int j = begin + t0 + rr;
-                    if (lex_lt(v, j, b2, i2)) {
-                        if (lex_lt(v, j, b1, i1)) { b2 = b1; i2 = i1; b1 = v; i1 = j; }
-                        else { b2 = v; i2 = j; }
-                    }
-                }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float c1 = __shfl_xor_sync(0xffffffffu, b1, o), c2 = __shfl_xor_sync(0xffffffffu, b2, o);
-            const int j1 = __shfl_xor_sync(0xffffffffu, i1, o), j2 = __shfl_xor_sync(0xffffffffu, i2, o);
-            top2_merge(b1, i1, b2, i2, c1, j1, c2, j2);
-        }
-        if (valid && lane == 0) {
-            if (i2 == INT_MAX) { i2 = -1; b2 = FMAX; }
-            if (decide_top2<MODE>(X, d, C, R, b1, i1, b2, i2, D2, idx, labels, prev, dmin, fp64_cnt, wide_cnt) &&
-                changed)
-                atomicAdd(changed, 1);
-        }
-    }
-}
-
-// fix-up rows of a tensor pass, finished exactly on CUDA cores
-cudaError_t launch_fixup(const Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
-                         int *changed, float *dmin) {
-    const int grid = c.num_sms * 8;   // persistent: the row count is only known on the device
-    const size_t sm = sizeof(float) * (size_t)(kFixTile + 8) * fix_stride(c.d);
-    if (mode_round)
-        fixup_tile_kernel<MODE_ROUND><<<grid, 256, sm, c.stream>>>(c.X, c.d, C, 0, c.st, c.fix_rows, c.fix_cnt, c.D2,
-                                                                   c.idx, nullptr, nullptr, nullptr, nullptr,
-                                                                   &c.st->argmin_fp64, &c.st->argmin_wide);
-    else
-        fixup_tile_kernel<MODE_ASSIGN><<<grid, 256, sm, c.stream>>>(c.X, c.d, C, k, c.st, c.fix_rows, c.fix_cnt,
-                                                                    nullptr, nullptr, labels, prev, changed, dmin,
-                                                                    &c.st->argmin_fp64, &c.st->argmin_wide);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
 __global__ void count_fixups_kernel(const int *fix_cnt, int64_t n, DevState *st) {
     st->screen_fallback += (unsigned long long)*fix_cnt;
     st->screen_rows += (unsigned long long)n;
@@ -962,6 +856,137 @@ int refine_warps(int d) {
 
 size_t refine_smem_bytes(int d) { return sizeof(float) * refine_warps(d) * 96 * (size_t)refine_stride(d); }
 
+// Rows the screening could not settle, scanned exactly against every center of the
+// pass.  A CTA takes tiles of 8 listed rows, one warp per row; the centers stream
+// through shared memory in chunks of 64 (asynchronous copies, double-buffered) and
+// lane l sums centers l and l + 32 of each chunk in the exact FP32 difference form
+// in ascending coordinates (bit-identical to dist2_fp32): per coordinate pair one
+// broadcast and two conflict-free 8-byte shared loads (row stride 2 mod 4) feed
+// eight FP32 operations.  Small tiles keep every SM busy when only a few thousand
+// rows need the scan.  A lexicographic top-2 per row is merged across the warp,
+// then the same decision as nearest_kernel (decide_top2).  Persistent: the row
+// count is read on the device.
+constexpr int kFxRows = 8;
+constexpr int kFxCent = 64;
+
+template <int MODE>
+__global__ void __launch_bounds__(256) fixup_kernel(const float *__restrict__ X, int d, const float *__restrict__ C,
+                                                   int c_cnt, int c_pairs, const DevState *st,
+                                                   const int32_t *__restrict__ rows, const int *rows_cnt, float *D2,
+                                                   int32_t *idx, int32_t *labels, const int32_t *prev, int *changed,
+                                                   float *dmin, unsigned long long *fp64_cnt,
+                                                   unsigned long long *wide_cnt) {
+    extern __shared__ __align__(16) float fsm[];
+    const int ds = refine_stride(d);
+    float *xs = fsm;                   // kFxRows x ds point rows
+    float *cs = fsm + kFxRows * ds;    // 2 x kFxCent x ds center rows
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nrows = *rows_cnt;
+    const int begin = MODE == MODE_ROUND ? st->batch_begin : 0;
+    const int cnt = MODE == MODE_ROUND ? st->batch_cnt : c_cnt;
+    const int nchunk = (cnt + kFxCent - 1) / kFxCent;
+    const float FMAX = FLT_MAX;
+    auto issue = [&](int ch) {
+        float *dst = cs + (ch & 1) * kFxCent * ds;
+        const int j0 = ch * kFxCent;
+        const int nc = min(kFxCent, cnt - j0);
+        for (int rr = wid; rr < nc; rr += 8) {
+            const float *src = C + (int64_t)(begin + j0 + rr) * d;
+            if (c_pairs)
+                for (int p = lane; p < (d >> 1); p += 32) cp_async8(dst + rr * ds + 2 * p, src + 2 * p);
+            for (int q = (c_pairs ? (d & ~1) : 0) + lane; q < d; q += 32) cp_async4(dst + rr * ds + q, src + q);
+        }
+    };
+    for (int t0 = blockIdx.x * kFxRows; t0 < nrows; t0 += gridDim.x * kFxRows) {   // uniform per block
+        const int nr = min(kFxRows, nrows - t0);
+        __syncthreads();   // the previous tile's readers are done with xs and cs
+        if (wid < nr) {
+            const float *src = X + (int64_t)rows[t0 + wid] * d;
+            for (int q = lane; q < d; q += 32) xs[wid * ds + q] = __ldg(src + q);
+        }
+        if (nchunk > 0) issue(0);
+        cp_async_commit();
+        float b1 = FMAX, b2 = FMAX;
+        int i1 = INT_MAX, i2 = INT_MAX;
+        const float *xa = xs + wid * ds;
+        for (int ch = 0; ch < nchunk; ++ch) {
+            if (ch + 1 < nchunk) issue(ch + 1);
+            cp_async_commit();
+            cp_async_wait<1>();
+            __syncthreads();   // chunk ch and the point rows are visible
+            const float *cb = cs + (ch & 1) * kFxCent * ds;
+            const float *c0 = cb + lane * ds, *c1 = cb + (lane + 32) * ds;
+            float a0 = 0.f, a1 = 0.f;
+            const float2 *x2 = reinterpret_cast<const float2 *>(xa);
+            const float2 *p0 = reinterpret_cast<const float2 *>(c0);
+            const float2 *p1 = reinterpret_cast<const float2 *>(c1);
+#pragma unroll 4
+            for (int p = 0; p < (d >> 1); ++p) {
+                const float2 x = x2[p], u = p0[p], v = p1[p];
+                float t = __fsub_rn(x.x, u.x);
+                a0 = __fmaf_rn(t, t, a0);
+                t = __fsub_rn(x.y, u.y);
+                a0 = __fmaf_rn(t, t, a0);
+                t = __fsub_rn(x.x, v.x);
+                a1 = __fmaf_rn(t, t, a1);
+                t = __fsub_rn(x.y, v.y);
+                a1 = __fmaf_rn(t, t, a1);
+            }
+            if (d & 1) {
+                const float xe = xa[d - 1];
+                float t = __fsub_rn(xe, c0[d - 1]);
+                a0 = __fmaf_rn(t, t, a0);
+                t = __fsub_rn(xe, c1[d - 1]);
+                a1 = __fmaf_rn(t, t, a1);
+            }
+            const int jl0 = ch * kFxCent + lane, jl1 = jl0 + 32;
+            if (jl0 < cnt && lex_lt(a0, begin + jl0, b2, i2)) {
+                if (lex_lt(a0, begin + jl0, b1, i1)) { b2 = b1; i2 = i1; b1 = a0; i1 = begin + jl0; }
+                else { b2 = a0; i2 = begin + jl0; }
+            }
+            if (jl1 < cnt && lex_lt(a1, begin + jl1, b2, i2)) {
+                if (lex_lt(a1, begin + jl1, b1, i1)) { b2 = b1; i2 = i1; b1 = a1; i1 = begin + jl1; }
+                else { b2 = a1; i2 = begin + jl1; }
+            }
+            __syncthreads();   // every reader is done with this buffer before it is refilled
+        }
+        cp_async_wait<0>();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float c1 = __shfl_xor_sync(0xffffffffu, b1, o), c2 = __shfl_xor_sync(0xffffffffu, b2, o);
+            const int j1 = __shfl_xor_sync(0xffffffffu, i1, o), j2 = __shfl_xor_sync(0xffffffffu, i2, o);
+            top2_merge(b1, i1, b2, i2, c1, j1, c2, j2);
+        }
+        if (lane == 0 && wid < nr) {
+            const int64_t R = rows[t0 + wid];
+            if (i2 == INT_MAX) { i2 = -1; b2 = FMAX; }
+            if (decide_top2<MODE>(X, d, C, R, b1, i1, b2, i2, D2, idx, labels, prev, dmin, fp64_cnt, wide_cnt) &&
+                changed)
+                atomicAdd(changed, 1);
+        }
+    }
+}
+
+size_t fixup_smem_bytes(int d) { return sizeof(float) * (size_t)(kFxRows + 2 * kFxCent) * refine_stride(d); }
+
+cudaError_t launch_fixup(const Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
+                         int *changed, float *dmin) {
+    const int grid = c.num_sms * 4;   // persistent: the row count is only known on the device
+    const size_t sm = fixup_smem_bytes(c.d);
+    // 8-byte center copies need d even and 8-byte aligned rows
+    const int pairs = (c.d % 2 == 0) && (reinterpret_cast<uintptr_t>(C) % 8 == 0);
+    if (mode_round)
+        fixup_kernel<MODE_ROUND><<<grid, 256, sm, c.stream>>>(c.X, c.d, C, 0, pairs, c.st, c.fix_rows, c.fix_cnt, c.D2,
+                                                              c.idx, nullptr, nullptr, nullptr, nullptr,
+                                                              &c.st->argmin_fp64, &c.st->argmin_wide);
+    else
+        fixup_kernel<MODE_ASSIGN><<<grid, 256, sm, c.stream>>>(c.X, c.d, C, k, pairs, c.st, c.fix_rows, c.fix_cnt,
+                                                               nullptr, nullptr, labels, prev, changed, dmin,
+                                                               &c.st->argmin_fp64, &c.st->argmin_wide);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t configure_refine_kernels() {
     // the tensor passes support d + 2 <= 192: refine tiles of 256 rows of up to 190 floats
     cudaError_t e = cudaFuncSetAttribute(refine_kernel<MODE_ROUND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -975,10 +1000,11 @@ cudaError_t configure_refine_kernels() {
     e = cudaFuncSetAttribute(refine_resident_kernel<MODE_ASSIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(fixup_tile_kernel<MODE_ROUND>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    // the tensor passes support d <= 190: fix-up tiles of 160 rows of up to 190 floats
+    const int fx = (int)fixup_smem_bytes(190);
+    e = cudaFuncSetAttribute(fixup_kernel<MODE_ROUND>, cudaFuncAttributeMaxDynamicSharedMemorySize, fx);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(fixup_tile_kernel<MODE_ASSIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                64 * 1024);
+    return cudaFuncSetAttribute(fixup_kernel<MODE_ASSIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, fx);
 }
 
 cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,

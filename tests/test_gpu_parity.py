@@ -250,6 +250,17 @@ def test_run_to_run_deterministic(km):
     assert res[0][2] == res[1][2]
 
 
+@pytest.mark.parametrize("form", ["cluster", "grid"])
+def test_recluster_forms_match_oracle(km, orc, form, monkeypatch):
+    """Weighted k-means++ (Alg. 2 step 8) in both kernel forms: one thread-block
+    cluster with distributed shared memory, and the cooperative grid."""
+    if form == "grid":
+        monkeypatch.setenv("KMPAR_RECLUSTER_GRID", "1")
+    X = datagen.kdd_like(6000, seed=41)
+    diag = run_and_compare(km, orc, X, 80, 160.0, 5, 17)
+    assert diag["parted"] is None, diag
+
+
 @pytest.mark.parametrize("k,d", [(420, 128), (37, 15)], ids=["many_wide_clusters", "few_narrow_clusters"])
 def test_lloyd_from_fixed_centers_matches_oracle(km, orc, k, d):
     """Lloyd alone (Sec. 3.1 centroid, Sec. 1 iteration) from fixed seed centers:

@@ -1,0 +1,144 @@
+"""Parity at full size: the whole path (Alg. 2 steps 1-8, then Lloyd) on the
+KDD-shaped workloads of 1,000,000 x 42 (k = 500, the benchmark's configuration
+and launch) and 4,800,000 x 42 (k = 1000), split-BF16 screening.  The oracle
+cannot run these, so sampled outputs are checked one by one against a brute-force
+FP64 scan, and properties that hold at any size are checked on every point:
+phi = sum D^2 (Sec. 3.1), sum w = n and w = counts of idx (Alg. 2 step 7), seed
+centers are candidate rows (step 8), Lloyd's cost never increases and equals the
+exact cost of its labels.  At 1e6 points the FP32 CUDA-core path must take the
+very same decisions."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1203_6402_gb300 import datagen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SAMPLE = 2000
+
+
+@pytest.fixture(scope="module")
+def km():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_6402_gb300 import kmpar
+    kmpar.load()
+    return kmpar
+
+
+def _nearest_fp64(Xs, C):
+    """Brute force: per sampled row the best and second-best exact d^2 and the best
+    center (lowest number on ties)."""
+    Xs = Xs.astype(np.float64)
+    C = C.astype(np.float64)
+    bj, b1, b2 = [], [], []
+    step = max(1, 4_000_000 // (C.shape[0] * C.shape[1]))   # rows per chunk: ~32 MB of differences
+    for i in range(0, len(Xs), step):
+        D = ((Xs[i:i + step, None, :] - C[None, :, :]) ** 2).sum(-1)
+        order = np.argsort(D, axis=1, kind="stable")[:, :2]
+        bj.append(order[:, 0])
+        b1.append(np.take_along_axis(D, order[:, :1], 1)[:, 0])
+        b2.append(np.take_along_axis(D, order[:, 1:2], 1)[:, 0] if C.shape[0] > 1 else np.full(len(D), np.inf))
+    return np.concatenate(bj), np.concatenate(b1), np.concatenate(b2)
+
+
+def _run(km, X, Xd, k, ell, rounds, seed, precision, max_iter):
+    g = km.KMeansPar(Xd, k, ell, rounds, seed, precision=precision)
+    phis = []
+    for r in range(1, rounds + 1):
+        na, phi = g.round(r, sync=True)
+        D2, _ = g.state()
+        phis.append((phi, float(D2.double().sum())))
+    D2, idx = g.state()
+    cand, w = g.candidates()
+    C, st = g.recluster()
+    out = g.lloyd(C.clone(), max_iter, labels=True, hist=True)
+    res = dict(phis=phis, D2=D2, idx=idx, cand=cand, w=w, C=C, st=st, out=out, stats=g.stats())
+    g.close()
+    return res
+
+
+def _check(X, Xd, res, k):
+    n = X.shape[0]
+    rng = np.random.default_rng(99)
+    s = np.sort(rng.choice(n, SAMPLE, replace=False))
+    # phi = sum D^2 after every round (the library sums FP32 D^2 in FP64 in a fixed tree)
+    for phi, ref in res["phis"]:
+        assert math.isclose(phi, ref, rel_tol=1e-9), (phi, ref)
+    D2 = res["D2"].cpu().numpy()
+    idx = res["idx"].cpu().numpy()
+    cand = res["cand"].cpu().numpy()
+    w = res["w"].cpu().numpy()
+    assert np.isfinite(D2).all() and (D2 >= 0).all()
+    # step 7: weights are the counts of the nearest-candidate numbers
+    assert w.sum() == n
+    assert np.array_equal(w, np.bincount(idx, minlength=len(cand)))
+    # D^2 and idx of sampled points against a brute-force scan of every candidate
+    bj, b1, b2 = _nearest_fp64(X[s], X[cand])
+    tie = b2 <= b1 * (1 + 1e-6)
+    assert np.all((idx[s] == bj) | tie), np.flatnonzero((idx[s] != bj) & ~tie)[:5]
+    np.testing.assert_allclose(D2[s], b1, rtol=1e-5, atol=1e-30)
+    # step 8: every seed center is a candidate row
+    C = res["C"].cpu().numpy()
+    rows = {X[j].tobytes() for j in cand}
+    assert all(C[i].tobytes() in rows for i in range(k))
+    # Lloyd: monotone cost, exact cost of the final labels, sampled labels nearest
+    out = res["out"]
+    hist = np.array(out["cost_hist"])
+    assert np.all(np.diff(hist) <= 1e-6 * hist[0])
+    return s, out["labels"], hist
+
+
+@pytest.mark.parametrize("name,max_iter", [("kdd_n1M_d42_k500", 100), ("kdd_n4.8M_d42_k1000", 20)])
+def test_full_size_properties_and_samples(km, name, max_iter):
+    w = datagen.WORKLOADS[name]
+    X = datagen.make(name, seed=1000)
+    Xd = torch.from_numpy(X).cuda()
+    g = km.KMeansPar(Xd, w["k"], w["ell"], w["rounds"], 7, precision="bf16x3")
+    phis = []
+    for r in range(1, w["rounds"] + 1):
+        na, phi = g.round(r, sync=True)
+        D2, _ = g.state()
+        phis.append((phi, float(D2.double().sum())))
+    D2, idx = g.state()
+    cand, wt = g.candidates()
+    C, st = g.recluster()
+    C0 = C.clone()
+    out = g.lloyd(C, max_iter, labels=True, hist=True)
+    stats = g.stats()
+    g.close()
+    res = dict(phis=phis, D2=D2, idx=idx, cand=cand, w=wt, C=C0, st=st, out=out)
+    s, lab, hist = _check(X, Xd, res, w["k"])
+    # the final cost is the exact cost of the final labels against the final centers
+    Cf = C.double()
+    labt = lab.long()
+    exact = float(((Xd.double() - Cf[labt]) ** 2).sum())
+    assert math.isclose(out["final_cost"], exact, rel_tol=1e-5), (out["final_cost"], exact)
+    # sampled labels are the nearest final centers (ties aside)
+    bj, b1, b2 = _nearest_fp64(X[s], C.cpu().numpy())
+    tie = b2 <= b1 * (1 + 1e-6)
+    labs = lab.cpu().numpy()[s]
+    assert np.all((labs == bj) | tie), np.flatnonzero((labs != bj) & ~tie)[:5]
+    assert stats["screen_rows"] > 0
+
+
+def test_full_size_tensor_path_takes_the_fp32_decisions(km):
+    """1e6 x 42, k = 500: candidates, weights, seed centers, Lloyd labels and cost
+    are identical whether the distances are screened on the tensor cores (split
+    BF16, exact refine) or computed in FP32 on CUDA cores."""
+    name = "kdd_n1M_d42_k500"
+    w = datagen.WORKLOADS[name]
+    X = datagen.make(name, seed=1000)
+    Xd = torch.from_numpy(X).cuda()
+    res = {}
+    for prec in ("fp32", "bf16x3"):
+        res[prec] = _run(km, X, Xd, w["k"], w["ell"], w["rounds"], 7, prec, 30)
+    a, b = res["fp32"], res["bf16x3"]
+    assert torch.equal(a["cand"], b["cand"]) and torch.equal(a["w"], b["w"])
+    assert torch.equal(a["idx"], b["idx"]) and torch.equal(a["D2"], b["D2"])
+    assert torch.equal(a["C"], b["C"])
+    assert torch.equal(a["out"]["labels"], b["out"]["labels"])
+    assert a["out"]["final_cost"] == b["out"]["final_cost"] and a["out"]["iters"] == b["out"]["iters"]

@@ -153,7 +153,10 @@ constexpr uint32_t kValMask = ~((1u << kColBits) - 1u);
 __device__ __forceinline__ __nv_bfloat16 bf(float v) { return __float2bfloat16_rn(v); }
 
 // element k of the A (point) row
-__device__ __forceinline__ float moved(const Enc &e, const float *x, int q) { return __fsub_rn(x[q], e.a[q]); }
+// x'_q = fl(x_q - a_q); a row already moved (e.a == nullptr) is used as it is
+__device__ __forceinline__ float moved(const Enc &e, const float *x, int q) {
+    return e.a ? __fsub_rn(x[q], e.a[q]) : x[q];
+}
 
 __device__ __forceinline__ __nv_bfloat16 a_elem(const Enc &e, const float *x, int k) {
     const int d = e.d;
@@ -199,41 +202,49 @@ __device__ __forceinline__ uint4 pack8(const __nv_bfloat16 (&v)[8]) {
 }
 
 // ------------------------------------------------------------------ center tiles
-// One thread per padded center row: ||c'||^2 (FP32, ascending), ||c'||, the
-// running max of ||c'|| and the row's KA x 8 swizzled chunks of the B image
-// [tile][katom][BN rows][128 B]  (c' = c - anchor).
-__global__ void prep_centers_kernel(const float *__restrict__ C, int d, int split, int KA, int BN, const DevState *st,
-                                    int cnt_static, int round_mode, const float *__restrict__ anchor,
-                                    uint8_t *__restrict__ img, float *cnorm, unsigned int *cmax_bits) {
+// One warp per padded center row: the moved row c' = fl(c - anchor) is staged in
+// shared memory, lane 0 sums ||c'||^2 (FP32, ascending) and records ||c'|| and the
+// running max of ||c'||, and lanes 0 .. 8 KA - 1 build the row's 16-byte chunks of
+// the B image [tile][katom][BN rows][128 B] in parallel.
+constexpr int kPrepMaxD = 192;
+
+__global__ void __launch_bounds__(256) prep_centers_kernel(const float *__restrict__ C, int d, int split, int KA, int BN,
+                                                           const DevState *st, int cnt_static, int round_mode,
+                                                           const float *__restrict__ anchor, uint8_t *__restrict__ img,
+                                                           float *cnorm, unsigned int *cmax_bits) {
+    __shared__ float crow[8][kPrepMaxD];
     const int begin = round_mode ? st->batch_begin : 0;
     const int cnt = round_mode ? st->batch_cnt : cnt_static;
     const int rows = ((cnt + BN - 1) / BN) * BN;
-    const Enc e{d, split, anchor};
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < rows; j += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const Enc em{d, split, nullptr};   // the staged row is already moved
+    float *cr = crow[w];
+    for (int j = blockIdx.x * 8 + w; j < rows; j += gridDim.x * 8) {   // uniform per warp
         const bool pad = j >= cnt;
         const float *c = C + (int64_t)(begin + (pad ? 0 : j)) * d;
+        if (!pad)
+            for (int q = lane; q < d; q += 32) cr[q] = __fsub_rn(c[q], anchor[q]);
+        __syncwarp();
         float cn = 0.f;
-        if (!pad) {
-            for (int q = 0; q < d; ++q) {
-                const float v = moved(e, c, q);
-                cn = __fmaf_rn(v, v, cn);
-            }
+        if (!pad && lane == 0) {
+            for (int q = 0; q < d; ++q) cn = __fmaf_rn(cr[q], cr[q], cn);
             const float nrm = sqrtf(cn);
             cnorm[j] = nrm;
             atomicMax(cmax_bits, __float_as_uint(nrm));
         }
+        cn = __shfl_sync(0xffffffffu, cn, 0);
         const float cn_hi = __bfloat162float(bf(cn));
         const float cn_lo = cn - cn_hi;
-        const int t = j / BN, jj = j % BN;
-        uint8_t *tile = img + (size_t)t * KA * BN * 128;
-        for (int a = 0; a < KA; ++a) {
-            for (int ch = 0; ch < 8; ++ch) {
-                __nv_bfloat16 v[8];
+        if (lane < KA * 8) {
+            const int a = lane >> 3, ch = lane & 7;
+            const int t = j / BN, jj = j % BN;
+            uint8_t *tile = img + (size_t)t * KA * BN * 128;
+            __nv_bfloat16 v[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = b_elem(e, c, cn_hi, cn_lo, pad, a * 64 + ch * 8 + q);
-                *reinterpret_cast<uint4 *>(tile + (size_t)a * BN * 128 + sw128_off(jj, ch)) = pack8(v);
-            }
+            for (int q = 0; q < 8; ++q) v[q] = b_elem(em, cr, cn_hi, cn_lo, pad, a * 64 + ch * 8 + q);
+            *reinterpret_cast<uint4 *>(tile + (size_t)a * BN * 128 + sw128_off(jj, ch)) = pack8(v);
         }
+        __syncwarp();   // the staged row is read before the next one overwrites it
     }
 }
 
@@ -717,8 +728,9 @@ cudaError_t launch_prep_centers(const float *C, int d, int split, const DevState
     if (e != cudaSuccess) return e;
     const int KA = tc_katoms(d, split), BN = tc_block_n(d, split);
     const int rows = ((cap_rows + BN - 1) / BN) * BN;
-    const int grid = std::max(1, std::min((rows + 127) / 128, 4096));
-    prep_centers_kernel<<<grid, 128, 0, s>>>(C, d, split, KA, BN, st, cnt_static, round_mode, anchor, img, cnorm,
+    if (d > kPrepMaxD) return cudaErrorInvalidValue;
+    const int grid = std::max(1, std::min((rows + 7) / 8, 4096));
+    prep_centers_kernel<<<grid, 256, 0, s>>>(C, d, split, KA, BN, st, cnt_static, round_mode, anchor, img, cnorm,
                                              cmax_bits);
     count_launches(1);
     return cudaGetLastError();

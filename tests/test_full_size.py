@@ -142,3 +142,54 @@ def test_full_size_tensor_path_takes_the_fp32_decisions(km):
     assert torch.equal(a["C"], b["C"])
     assert torch.equal(a["out"]["labels"], b["out"]["labels"])
     assert a["out"]["final_cost"] == b["out"]["final_cost"] and a["out"]["iters"] == b["out"]["iters"]
+
+
+def test_large_k_wide_rows(km):
+    """The shape of the 1e7 x 128, k = 1e4, l = 2e4 configuration at n = 2e6
+    (plain BF16 screening): 79 streamed center tiles per Lloyd pass and ~21,000
+    per round batch, per-row refine copies, ~1e5 candidates reclustered by the
+    cooperative grid kernel.  Same sampled and whole-set checks."""
+    n, d, k, ell = 2_000_000, 128, 10_000, 20_000.0
+    X = datagen.gauss_mixture(n, d, k, 100.0, seed=1234)
+    Xd = torch.from_numpy(X).cuda()
+    g = km.KMeansPar(Xd, k, ell, 5, 11, precision="bf16")
+    phis = []
+    for r in range(1, 6):
+        na, phi = g.round(r, sync=True)
+        D2, _ = g.state()
+        phis.append((phi, float(D2.double().sum())))
+    D2, idx = g.state()
+    cand, wt = g.candidates()
+    C, st = g.recluster()
+    C0 = C.clone()
+    out = g.lloyd(C, 3, labels=True, hist=True)
+    stats = g.stats()
+    g.close()
+    assert len(cand) > 50_000
+    for phi, ref in phis:
+        assert math.isclose(phi, ref, rel_tol=1e-9), (phi, ref)
+    D2h, idxh, candh, wh = D2.cpu().numpy(), idx.cpu().numpy(), cand.cpu().numpy(), wt.cpu().numpy()
+    assert np.isfinite(D2h).all() and (D2h >= 0).all()
+    assert wh.sum() == n and np.array_equal(wh, np.bincount(idxh, minlength=len(candh)))
+    rng = np.random.default_rng(5)
+    s = np.sort(rng.choice(n, 200, replace=False))
+    bj, b1, b2 = _nearest_fp64(X[s], X[candh])
+    tie = b2 <= b1 * (1 + 1e-6)
+    assert np.all((idxh[s] == bj) | tie)
+    np.testing.assert_allclose(D2h[s], b1, rtol=1e-5, atol=1e-30)
+    rows = {X[j].tobytes() for j in candh}
+    C0h = C0.cpu().numpy()
+    assert all(C0h[i].tobytes() in rows for i in range(k))
+    hist = np.array(out["cost_hist"])
+    assert np.all(np.diff(hist) <= 1e-6 * hist[0])
+    labs = out["labels"]
+    exact = float(((Xd.double() - C.double()[labs.long()]) ** 2).sum())
+    assert math.isclose(out["final_cost"], exact, rel_tol=1e-5), (out["final_cost"], exact)
+    bj, b1, b2 = _nearest_fp64(X[s], C.cpu().numpy())
+    tie = b2 <= b1 * (1 + 1e-6)
+    assert np.all((labs.cpu().numpy()[s] == bj) | tie)
+    # plain BF16 (error ~2^-6 of ||x'|| ||c'||) leaves many rows of the rounds to the
+    # exact fix-up: their candidates are data points, about two per true cluster,
+    # so the two nearest are often near ties; every row is decided exactly all the same
+    # screened rows: 5 round passes and 4 Lloyd assignments (updates 0..3)
+    assert stats["screen_rows"] == (5 + 4) * n and 0 < stats["screen_fallback"] < stats["screen_rows"]

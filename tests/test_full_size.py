@@ -128,20 +128,22 @@ def test_full_size_properties_and_samples(km, name, max_iter):
 def test_full_size_tensor_path_takes_the_fp32_decisions(km):
     """1e6 x 42, k = 500: candidates, weights, seed centers, Lloyd labels and cost
     are identical whether the distances are screened on the tensor cores (split
-    BF16, exact refine) or computed in FP32 on CUDA cores."""
+    BF16 or plain BF16, exact refine) or computed in FP32 on CUDA cores."""
     name = "kdd_n1M_d42_k500"
     w = datagen.WORKLOADS[name]
     X = datagen.make(name, seed=1000)
     Xd = torch.from_numpy(X).cuda()
     res = {}
-    for prec in ("fp32", "bf16x3"):
+    for prec in ("fp32", "bf16x3", "bf16"):
         res[prec] = _run(km, X, Xd, w["k"], w["ell"], w["rounds"], 7, prec, 30)
-    a, b = res["fp32"], res["bf16x3"]
-    assert torch.equal(a["cand"], b["cand"]) and torch.equal(a["w"], b["w"])
-    assert torch.equal(a["idx"], b["idx"]) and torch.equal(a["D2"], b["D2"])
-    assert torch.equal(a["C"], b["C"])
-    assert torch.equal(a["out"]["labels"], b["out"]["labels"])
-    assert a["out"]["final_cost"] == b["out"]["final_cost"] and a["out"]["iters"] == b["out"]["iters"]
+    a = res["fp32"]
+    for prec in ("bf16x3", "bf16"):
+        b = res[prec]
+        assert torch.equal(a["cand"], b["cand"]) and torch.equal(a["w"], b["w"]), prec
+        assert torch.equal(a["idx"], b["idx"]) and torch.equal(a["D2"], b["D2"]), prec
+        assert torch.equal(a["C"], b["C"]), prec
+        assert torch.equal(a["out"]["labels"], b["out"]["labels"]), prec
+        assert a["out"]["final_cost"] == b["out"]["final_cost"] and a["out"]["iters"] == b["out"]["iters"], prec
 
 
 def test_large_k_wide_rows(km):

@@ -55,7 +55,7 @@ cudaError_t alloc(T **p, size_t count) {
 
 void free_ctx(kmp::Ctx &c) {
     void *bufs[] = {c.st, c.D2, c.idx, c.drawn, c.cand, c.C, c.w, c.rD2, c.chosen, c.partials,
-                    c.labels[0], c.labels[1], c.perm, c.hist, c.base, c.cost_dev, c.tc_img, c.tc_cnorm,
+                    c.labels[0], c.labels[1], c.perm, c.hist, c.base, c.cost_dev, c.tc_img,
                     c.tc_cmax, c.tc_err, c.cand1, c.fix_rows, c.fix_cnt, c.dmin, c.tc_ximg, c.tc_xnorm,
                     c.piece, c.psum, c.rc_cmass, c.rc_sync, c.rc_err, c.chunk, c.tc_v2,
                     c.tc_anchor, c.tc_anchor_part, c.lloyd_rec};
@@ -199,7 +199,6 @@ kmpar_status kmpar_init(kmpar_ctx **out, const float *X, int64_t n, int32_t d, i
         const int split = precision == KMPAR_BF16X3 ? 1 : 0;
         const int rows = std::max(cap_round, k);
         KMP_INIT_CUDA(alloc(&c.tc_img, kmp::tc::tc_image_bytes(d, split, rows)), "alloc center tiles");
-        KMP_INIT_CUDA(alloc(&c.tc_cnorm, (size_t)rows + 512), "alloc center norms");
         KMP_INIT_CUDA(alloc(&c.tc_cmax, 1), "alloc cmax");
         KMP_INIT_CUDA(alloc(&c.tc_err, 1), "alloc error word");
         KMP_INIT_CUDA(alloc(&c.fix_rows, n), "alloc fix-up rows");

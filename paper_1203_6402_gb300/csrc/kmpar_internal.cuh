@@ -86,7 +86,6 @@ struct Ctx {
     float *tc_xnorm = nullptr;    // ||x'||^2 per point (x' = x - anchor)
     float *tc_anchor = nullptr;   // d column means of X
     double *tc_anchor_part = nullptr;   // per-block column sums behind the anchor
-    float *tc_cnorm = nullptr;    // ||c'|| per padded center row
     unsigned int *tc_cmax = nullptr;
     int *tc_err = nullptr;        // first timeout code of a tensor pass
     int32_t *cand1 = nullptr;     // per row: first center of the best screened pair of the last tensor pass, or -1
@@ -194,33 +193,6 @@ __device__ __forceinline__ double block_sum_f64(double v, double *sh /*32*/) {
         for (int i = 0; i < nw; ++i) r += sh[i];
     }
     return r;
-}
-
-// Copies nrows rows of d floats (contiguous in global memory) into shared memory
-// with row stride ds, using nthr cooperating threads (index tid).  Each thread
-// issues eight independent loads before its stores, so a copy costs a few memory
-// latencies rather than one per element.  Row = f / d as (f * ceil(2^32 / d)) >> 32
-// in 64-bit arithmetic, exact while f * d < 2^32 (d = 1 included).
-__device__ __forceinline__ void stage_rows(float *dst, int ds, const float *__restrict__ src, int nrows, int d,
-                                           int tid, int nthr) {
-    const unsigned long long magic = ((1ull << 32) + (unsigned long long)d - 1ull) / (unsigned long long)d;
-    const int total = nrows * d;
-    for (int f0 = tid; f0 < total; f0 += 8 * nthr) {
-        float v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int f = f0 + u * nthr;
-            if (f < total) v[u] = __ldg(src + f);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int f = f0 + u * nthr;
-            if (f < total) {
-                const int r = (int)(((unsigned long long)(uint32_t)f * magic) >> 32);
-                dst[r * ds + (f - r * d)] = v[u];
-            }
-        }
-    }
 }
 
 // ---------------------------------------------------------------- launchers

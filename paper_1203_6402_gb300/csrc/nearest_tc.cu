@@ -82,11 +82,9 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 __device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t *holder, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(holder)), "r"(ncols)
@@ -203,15 +201,15 @@ __device__ __forceinline__ uint4 pack8(const __nv_bfloat16 (&v)[8]) {
 
 // ------------------------------------------------------------------ center tiles
 // One warp per padded center row: the moved row c' = fl(c - anchor) is staged in
-// shared memory, lane 0 sums ||c'||^2 (FP32, ascending) and records ||c'|| and the
-// running max of ||c'||, and lanes 0 .. 8 KA - 1 build the row's 16-byte chunks of
-// the B image [tile][katom][BN rows][128 B] in parallel.
+// shared memory, lane 0 sums ||c'||^2 (FP32, ascending) and records the running max
+// of ||c'||, and lanes 0 .. 8 KA - 1 build the row's 16-byte chunks of the B image
+// [tile][katom][BN rows][128 B] in parallel.
 constexpr int kPrepMaxD = 192;
 
 __global__ void __launch_bounds__(256) prep_centers_kernel(const float *__restrict__ C, int d, int split, int KA, int BN,
                                                            const DevState *st, int cnt_static, int round_mode,
                                                            const float *__restrict__ anchor, uint8_t *__restrict__ img,
-                                                           float *cnorm, unsigned int *cmax_bits) {
+                                                           unsigned int *cmax_bits) {
     __shared__ float crow[8][kPrepMaxD];
     const int begin = round_mode ? st->batch_begin : 0;
     const int cnt = round_mode ? st->batch_cnt : cnt_static;
@@ -228,9 +226,7 @@ __global__ void __launch_bounds__(256) prep_centers_kernel(const float *__restri
         float cn = 0.f;
         if (!pad && lane == 0) {
             for (int q = 0; q < d; ++q) cn = __fmaf_rn(cr[q], cr[q], cn);
-            const float nrm = sqrtf(cn);
-            cnorm[j] = nrm;
-            atomicMax(cmax_bits, __float_as_uint(nrm));
+            atomicMax(cmax_bits, __float_as_uint(sqrtf(cn)));
         }
         cn = __shfl_sync(0xffffffffu, cn, 0);
         const float cn_hi = __bfloat162float(bf(cn));
@@ -364,10 +360,6 @@ struct Cfg {
 struct Bound {
     float ep, en;   // E(x, c) = ep ||x|| ||c|| + en (||x||^2 + ||c||^2)
 };
-
-__device__ __forceinline__ float err_bound(const Bound &b, float X, float c) {
-    return b.ep * X * c + b.en * (X * X + c * c);
-}
 
 // bounded wait on an mbarrier phase; false if this or another warp gave up
 __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatile int *abort, int *err, int code) {
@@ -722,7 +714,7 @@ Bound make_bound(int d, int split) {
 }
 
 cudaError_t launch_prep_centers(const float *C, int d, int split, const DevState *st, int cnt_static, int round_mode,
-                                int cap_rows, const float *anchor, uint8_t *img, float *cnorm, unsigned int *cmax_bits,
+                                int cap_rows, const float *anchor, uint8_t *img, unsigned int *cmax_bits,
                                 cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(cmax_bits, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
@@ -730,8 +722,7 @@ cudaError_t launch_prep_centers(const float *C, int d, int split, const DevState
     const int rows = ((cap_rows + BN - 1) / BN) * BN;
     if (d > kPrepMaxD) return cudaErrorInvalidValue;
     const int grid = std::max(1, std::min((rows + 7) / 8, 4096));
-    prep_centers_kernel<<<grid, 256, 0, s>>>(C, d, split, KA, BN, st, cnt_static, round_mode, anchor, img, cnorm,
-                                             cmax_bits);
+    prep_centers_kernel<<<grid, 256, 0, s>>>(C, d, split, KA, BN, st, cnt_static, round_mode, anchor, img, cmax_bits);
     count_launches(1);
     return cudaGetLastError();
 }

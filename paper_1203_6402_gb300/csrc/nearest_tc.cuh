@@ -19,7 +19,6 @@ struct TcParams {
     int cnt;                 // ASSIGN: number of centers
     const DevState *st;      // ROUND: batch range
     const uint8_t *bimg;     // swizzled BF16 center tiles
-    const float *cnorm;      // ||c'|| per padded center row of the batch
     const unsigned int *cmax_bits;
     int32_t *cand1;          // per row: first center of the best screened pair (-1: none)
     float *v2;               // per row: smallest screened value outside that pair (key-truncated)
@@ -45,8 +44,8 @@ cudaError_t launch_anchor(const float *X, int64_t n, int d, double *scratch, flo
 cudaError_t launch_prep_points(const float *X, int64_t n, int d, int split, const float *anchor, uint8_t *img,
                                float *xnorm, cudaStream_t s);
 cudaError_t launch_prep_centers(const float *C, int d, int split, const DevState *st, int cnt_static, int round_mode,
-                                int cap_rows, const float *anchor, uint8_t *img, float *cnorm,
-                                unsigned int *cmax_bits, cudaStream_t s);
+                                int cap_rows, const float *anchor, uint8_t *img, unsigned int *cmax_bits,
+                                cudaStream_t s);
 cudaError_t launch_nearest_tc(TcParams p, int mode_round, int num_sms, cudaStream_t s);
 // screening error bound E(x, c) = ep ||x'|| ||c'|| + en (||x'||^2 + ||c'||^2)
 void tc_bound(int d, int split, float *ep, float *en);

@@ -967,14 +967,104 @@ __global__ void __launch_bounds__(256) fixup_kernel(const float *__restrict__ X,
     }
 }
 
+// Fix-up with the pass's centers resident in shared memory (used when they fit):
+// persistent CTAs copy the centers once (row stride 2 mod 4: lane l reading center
+// l of a consecutive run is conflict-free with 8-byte loads); then one warp per
+// listed row: the row is staged, lane l sums centers l, l + 32, ... in the exact
+// FP32 difference form (bit-identical to dist2_fp32), a lexicographic top-2 is
+// merged across the warp and decided by decide_top2.  No center is read from
+// global memory more than once per CTA.
+template <int MODE>
+__global__ void __launch_bounds__(512) fixup_resident_kernel(const float *__restrict__ X, int d,
+                                                            const float *__restrict__ C, int c_cnt, int cap_rows,
+                                                            int c_pairs, const DevState *st,
+                                                            const int32_t *__restrict__ rows, const int *rows_cnt,
+                                                            float *D2, int32_t *idx, int32_t *labels,
+                                                            const int32_t *prev, int *changed, float *dmin,
+                                                            unsigned long long *fp64_cnt,
+                                                            unsigned long long *wide_cnt) {
+    extern __shared__ __align__(16) float fsm[];
+    const int ds = refine_stride(d);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int nrows = *rows_cnt;
+    if ((int64_t)blockIdx.x * nwarps >= nrows) return;   // uniform per block: nothing for this CTA
+    const int begin = MODE == MODE_ROUND ? st->batch_begin : 0;
+    const int cnt = MODE == MODE_ROUND ? min(st->batch_cnt, cap_rows) : c_cnt;
+    float *Cs = fsm;                                   // cap_rows x ds
+    float *xs = fsm + (size_t)cap_rows * ds + wid * ds; // this warp's point row
+    for (int rr = wid; rr < cnt; rr += nwarps) {
+        const float *src = C + (int64_t)(begin + rr) * d;
+        if (c_pairs)
+            for (int p = lane; p < (d >> 1); p += 32) cp_async8(Cs + rr * ds + 2 * p, src + 2 * p);
+        for (int q = (c_pairs ? (d & ~1) : 0) + lane; q < d; q += 32) cp_async4(Cs + rr * ds + q, src + q);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    const float FMAX = FLT_MAX;
+    for (int t = blockIdx.x * nwarps + wid; t < nrows; t += gridDim.x * nwarps) {   // uniform per warp
+        const int64_t R = rows[t];
+        for (int q = lane; q < d; q += 32) xs[q] = __ldg(X + R * d + q);
+        __syncwarp();
+        float b1 = FMAX, b2 = FMAX;
+        int i1 = INT_MAX, i2 = INT_MAX;
+        for (int jl = lane; jl < cnt; jl += 32) {
+            const float v = dist2_smem(xs, Cs + (size_t)jl * ds, d, true);
+            const int j = begin + jl;
+            if (lex_lt(v, j, b2, i2)) {
+                if (lex_lt(v, j, b1, i1)) { b2 = b1; i2 = i1; b1 = v; i1 = j; }
+                else { b2 = v; i2 = j; }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float c1 = __shfl_xor_sync(0xffffffffu, b1, o), c2 = __shfl_xor_sync(0xffffffffu, b2, o);
+            const int j1 = __shfl_xor_sync(0xffffffffu, i1, o), j2 = __shfl_xor_sync(0xffffffffu, i2, o);
+            top2_merge(b1, i1, b2, i2, c1, j1, c2, j2);
+        }
+        if (lane == 0) {
+            if (i2 == INT_MAX) { i2 = -1; b2 = FMAX; }
+            if (decide_top2<MODE>(X, d, C, R, b1, i1, b2, i2, D2, idx, labels, prev, dmin, fp64_cnt, wide_cnt) &&
+                changed)
+                atomicAdd(changed, 1);
+        }
+        __syncwarp();   // the staged row is read before the next one overwrites it
+    }
+}
+
+// warps of a resident fix-up CTA (0: the centers do not fit; use fixup_kernel)
+int fixup_resident_warps(int cap_rows, int d) {
+    const size_t budget = 200u * 1024u;
+    const size_t cbytes = sizeof(float) * (size_t)cap_rows * refine_stride(d);
+    const size_t per_warp = sizeof(float) * (size_t)refine_stride(d);
+    if (cbytes + 16 * per_warp > budget) return 0;
+    return 16;
+}
+
 size_t fixup_smem_bytes(int d) { return sizeof(float) * (size_t)(kFxRows + 2 * kFxCent) * refine_stride(d); }
 
 cudaError_t launch_fixup(const Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
                          int *changed, float *dmin) {
+    // 8-byte center copies need d even and 8-byte aligned rows
+    const int c_pairs = (c.d % 2 == 0) && (reinterpret_cast<uintptr_t>(C) % 8 == 0);
+    const int cap_rows = mode_round ? c.cap_round : k;
+    const int rw = fixup_resident_warps(cap_rows, c.d);
+    if (rw > 0) {
+        const size_t sm = sizeof(float) * ((size_t)cap_rows + rw) * refine_stride(c.d);
+        if (mode_round)
+            fixup_resident_kernel<MODE_ROUND><<<c.num_sms, 32 * rw, sm, c.stream>>>(
+                c.X, c.d, C, 0, cap_rows, c_pairs, c.st, c.fix_rows, c.fix_cnt, c.D2, c.idx, nullptr, nullptr,
+                nullptr, nullptr, &c.st->argmin_fp64, &c.st->argmin_wide);
+        else
+            fixup_resident_kernel<MODE_ASSIGN><<<c.num_sms, 32 * rw, sm, c.stream>>>(
+                c.X, c.d, C, k, cap_rows, c_pairs, c.st, c.fix_rows, c.fix_cnt, nullptr, nullptr, labels, prev,
+                changed, dmin, &c.st->argmin_fp64, &c.st->argmin_wide);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     const int grid = c.num_sms * 4;   // persistent: the row count is only known on the device
     const size_t sm = fixup_smem_bytes(c.d);
-    // 8-byte center copies need d even and 8-byte aligned rows
-    const int pairs = (c.d % 2 == 0) && (reinterpret_cast<uintptr_t>(C) % 8 == 0);
+    const int pairs = c_pairs;
     if (mode_round)
         fixup_kernel<MODE_ROUND><<<grid, 256, sm, c.stream>>>(c.X, c.d, C, 0, pairs, c.st, c.fix_rows, c.fix_cnt, c.D2,
                                                               c.idx, nullptr, nullptr, nullptr, nullptr,
@@ -1004,7 +1094,13 @@ cudaError_t configure_refine_kernels() {
     const int fx = (int)fixup_smem_bytes(190);
     e = cudaFuncSetAttribute(fixup_kernel<MODE_ROUND>, cudaFuncAttributeMaxDynamicSharedMemorySize, fx);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(fixup_kernel<MODE_ASSIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, fx);
+    e = cudaFuncSetAttribute(fixup_kernel<MODE_ASSIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, fx);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fixup_resident_kernel<MODE_ROUND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fixup_resident_kernel<MODE_ASSIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024);
 }
 
 cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
@@ -1012,7 +1108,7 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
     cudaError_t e;
     const int split = c.precision == KMPAR_BF16X3 ? 1 : 0;
     if ((e = tc::launch_prep_centers(C, c.d, split, c.st, k, mode_round, mode_round ? c.cap_round : k, c.tc_anchor,
-                                     c.tc_img, c.tc_cnorm, c.tc_cmax, c.stream)) != cudaSuccess)
+                                     c.tc_img, c.tc_cmax, c.stream)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(c.fix_cnt, 0, sizeof(int), c.stream)) != cudaSuccess) return e;
     // rows the screening does not reach (e.g. an empty batch) must not see a stale winner
@@ -1020,7 +1116,7 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
     tc::TcParams p{};
     p.X = c.X; p.n = c.n; p.d = c.d; p.split = split;
     p.ximg = c.tc_ximg; p.xnorm = c.tc_xnorm;
-    p.Cf = C; p.cnt = k; p.st = c.st; p.bimg = c.tc_img; p.cnorm = c.tc_cnorm; p.cmax_bits = c.tc_cmax;
+    p.Cf = C; p.cnt = k; p.st = c.st; p.bimg = c.tc_img; p.cmax_bits = c.tc_cmax;
     p.cand1 = c.cand1; p.v2 = c.tc_v2; p.fix_rows = c.fix_rows; p.fix_cnt = c.fix_cnt;
     p.fp64_cnt = &c.st->argmin_fp64; p.err = c.tc_err;
     cudaEvent_t ev = nullptr;

@@ -40,7 +40,7 @@ SCREEN_ALU_OPS = 2.25
 # DRAM bytes (read + write) per launch of the tensor assignment pass, from an ncu capture of the
 # same kernel on this workload (profiles/nearest_tc_assign_bf16x3_kdd_n1M.md); to be set to None
 # whenever the kernel changes until it is captured again
-TC_ASSIGN_TRAFFIC = {"bf16x3": 256.198e6 + 8.286e6}
+TC_ASSIGN_TRAFFIC = {"bf16x3": 256.201e6 + 8.731e6}
 
 
 def load_peaks():

@@ -654,6 +654,36 @@ __device__ __forceinline__ float dist2_smem(const float *xa, const float *ca, in
     return s;
 }
 
+// exact FP32 difference form of one row against several centers at once (rows in
+// shared memory, 8-byte aligned): the chains are independent, so their FMA
+// latencies overlap; each chain is still summed in ascending coordinates, so every
+// value is bit-identical to dist2_fp32
+template <int NC>
+__device__ __forceinline__ void dist2_smem_multi(const float *xa, const float *const (&ca)[NC], int d, float (&s)[NC]) {
+#pragma unroll
+    for (int u = 0; u < NC; ++u) s[u] = 0.f;
+    const float2 *x2 = reinterpret_cast<const float2 *>(xa);
+#pragma unroll 2
+    for (int p = 0; p < (d >> 1); ++p) {
+        const float2 a = x2[p];
+#pragma unroll
+        for (int u = 0; u < NC; ++u) {
+            const float2 c = reinterpret_cast<const float2 *>(ca[u])[p];
+            float t = __fsub_rn(a.x, c.x);
+            s[u] = __fmaf_rn(t, t, s[u]);
+            t = __fsub_rn(a.y, c.y);
+            s[u] = __fmaf_rn(t, t, s[u]);
+        }
+    }
+    if (d & 1) {
+#pragma unroll
+        for (int u = 0; u < NC; ++u) {
+            const float t = __fsub_rn(xa[d - 1], ca[u][d - 1]);
+            s[u] = __fmaf_rn(t, t, s[u]);
+        }
+    }
+}
+
 // the pair's exact values in (value, center number) order; i2 = -1 when the pair
 // has one real center
 __device__ __forceinline__ void pair_top2(float va, int ja, float vb, int jb, bool has_b, float &b1, int &i1,
@@ -710,8 +740,10 @@ __global__ void __launch_bounds__(256) refine_kernel(const float *__restrict__ X
     if (lane < nw && j >= 0) {
         const bool has_b = j + 1 < end;
         const float *ct = cs + 2 * lane * ds;
-        const float va = dist2_smem(xs + lane * ds, ct, d, true);
-        const float vb = has_b ? dist2_smem(xs + lane * ds, ct + ds, d, true) : 0.f;
+        const float *cp[2] = {ct, has_b ? ct + ds : ct};
+        float v[2];
+        dist2_smem_multi<2>(xs + lane * ds, cp, d, v);
+        const float va = v[0], vb = has_b ? v[1] : 0.f;
         float b1, b2;
         int i1, i2;
         pair_top2(va, j, vb, j + 1, has_b, b1, i1, b2, i2);
@@ -811,8 +843,17 @@ __global__ void __launch_bounds__(512) refine_resident_kernel(
             const bool has_b = j + 1 - begin < cnt;
             const float *xa = cur + lane * d;
             const float *ca = Cs + (int64_t)(j - begin) * d;
-            const float va = dist2_smem(xa, ca, d, pairs);
-            const float vb = has_b ? dist2_smem(xa, ca + d, d, pairs) : 0.f;
+            float va, vb = 0.f;
+            if (pairs) {
+                const float *cp[2] = {ca, has_b ? ca + d : ca};
+                float v[2];
+                dist2_smem_multi<2>(xa, cp, d, v);
+                va = v[0];
+                if (has_b) vb = v[1];
+            } else {
+                va = dist2_smem(xa, ca, d, false);
+                if (has_b) vb = dist2_smem(xa, ca + d, d, false);
+            }
             float b1, b2;
             int i1, i2;
             pair_top2(va, j, vb, j + 1, has_b, b1, i1, b2, i2);
@@ -1008,12 +1049,23 @@ __global__ void __launch_bounds__(512) fixup_resident_kernel(const float *__rest
         __syncwarp();
         float b1 = FMAX, b2 = FMAX;
         int i1 = INT_MAX, i2 = INT_MAX;
-        for (int jl = lane; jl < cnt; jl += 32) {
-            const float v = dist2_smem(xs, Cs + (size_t)jl * ds, d, true);
-            const int j = begin + jl;
-            if (lex_lt(v, j, b2, i2)) {
-                if (lex_lt(v, j, b1, i1)) { b2 = b1; i2 = i1; b1 = v; i1 = j; }
-                else { b2 = v; i2 = j; }
+        // lane l: centers l, l + 32, l + 64, l + 96 summed together, then the next 128
+        for (int j0 = lane; j0 < cnt; j0 += 128) {
+            const float *cp[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) cp[u] = Cs + (size_t)min(j0 + 32 * u, cnt - 1) * ds;
+            float v[4];
+            dist2_smem_multi<4>(xs, cp, d, v);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int jl = j0 + 32 * u;
+                if (jl < cnt) {
+                    const int j = begin + jl;
+                    if (lex_lt(v[u], j, b2, i2)) {
+                        if (lex_lt(v[u], j, b1, i1)) { b2 = b1; i2 = i1; b1 = v[u]; i1 = j; }
+                        else { b2 = v[u]; i2 = j; }
+                    }
+                }
             }
         }
 #pragma unroll

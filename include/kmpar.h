@@ -104,7 +104,9 @@ typedef struct {
  * difference form), idx(x) = 0 and psi = sum D^2 (FP64).  k is the number of
  * centers the reclustering produces; ell is the oversampling factor l; rounds is
  * the number of calls to kmpar_round that will follow; stream is a cudaStream_t
- * (NULL = legacy default stream).  On error *out is NULL.
+ * (NULL = legacy default stream).  On error *out is NULL.  The device buffers
+ * come, in stream order, from a memory pool the library keeps per device; memory
+ * a destroyed context returned to it is reused without mapping new pages.
  */
 KMPAR_API kmpar_status kmpar_init(kmpar_ctx **out, const float *X, int64_t n, int32_t d, int32_t k,
                         double ell, int32_t rounds, uint64_t seed, int32_t precision,
@@ -226,7 +228,15 @@ KMPAR_API kmpar_status kmpar_set_timing(kmpar_ctx *ctx, int32_t enable);
 /* Number of CUDA kernels this library has launched in the process so far. */
 KMPAR_API int64_t kmpar_launch_count(void);
 
+/* Waits for the context's stream, then returns the context's buffers to the
+ * library's pool (stream-ordered, no device-wide synchronisation).  Device
+ * pointers the context handed out (kmpar_weight) are invalid afterwards, and no
+ * work on another stream may still read them.  NULL is a no-op. */
 KMPAR_API void kmpar_destroy(kmpar_ctx *ctx);
+
+/* Hands the pool memory that no live context uses back to the driver, on every
+ * device the library has used.  KMPAR_ERR_CUDA if the driver refuses. */
+KMPAR_API kmpar_status kmpar_release_cached_memory(void);
 KMPAR_API const char *kmpar_status_string(kmpar_status s);
 /* Last error message of ctx, or of the calling thread's last context-free call
  * when ctx is NULL. */

@@ -5,8 +5,11 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <stdint.h>
+
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <string>
 
 #include "kmpar_internal.cuh"
@@ -48,9 +51,54 @@ int round_capacity(double ell) {
     return (int)ceil(c);
 }
 
+// Context buffers come from one stream-ordered memory pool per device, owned by
+// the library.  Its release threshold is unbounded, so the memory a destroyed
+// context freed stays mapped for the next context: creating and destroying a
+// context then maps no pages and, unlike cudaFree, does not synchronise the device.
+// kmpar_release_cached_memory hands the unused part back to the driver.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+cudaError_t ctx_pool(int dev, cudaMemPool_t *out) {
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = UINT64_MAX;
+        if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
+// count elements of T on the context's stream, in whole 256-byte units; the bulk
+// and vector copies of the kernels need 16-byte aligned buffers
 template <typename T>
-cudaError_t alloc(T **p, size_t count) {
-    return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1));
+cudaError_t alloc(const kmp::Ctx &c, T **p, size_t count) {
+    *p = nullptr;
+    cudaMemPool_t pool;
+    cudaError_t e = ctx_pool(c.dev, &pool);
+    if (e != cudaSuccess) return e;
+    const size_t bytes = (sizeof(T) * (count ? count : 1) + 255) & ~(size_t)255;
+    void *q = nullptr;
+    if ((e = cudaMallocFromPoolAsync(&q, bytes, pool, c.stream)) != cudaSuccess) return e;
+    if (reinterpret_cast<uintptr_t>(q) & 15u) {
+        cudaFreeAsync(q, c.stream);
+        return cudaErrorMisalignedAddress;
+    }
+    *p = static_cast<T *>(q);
+    return cudaSuccess;
 }
 
 void free_ctx(kmp::Ctx &c) {
@@ -59,8 +107,9 @@ void free_ctx(kmp::Ctx &c) {
                     c.tc_cmax, c.tc_err, c.cand1, c.fix_rows, c.fix_cnt, c.dmin, c.tc_ximg, c.tc_xnorm,
                     c.piece, c.psum, c.rc_cmass, c.rc_sync, c.rc_err, c.chunk, c.tc_v2,
                     c.tc_anchor, c.tc_anchor_part, c.lloyd_rec};
+    // stream-ordered: the memory returns to the pool once the context's work is done
     for (void *b : bufs)
-        if (b) cudaFree(b);
+        if (b) cudaFreeAsync(b, c.stream);
 }
 
 int sort_pow2(int cap) {
@@ -182,36 +231,38 @@ kmpar_status kmpar_init(kmpar_ctx **out, const float *X, int64_t n, int32_t d, i
     KMP_INIT_CUDA(cudaGetDevice(&c.dev), "cudaGetDevice");
     KMP_INIT_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.dev), "sm count");
     KMP_INIT_CUDA(kmp::configure_kernels(sort_pow2(cap_round), k), "configure kernels");
-    KMP_INIT_CUDA(alloc(&c.st, 1), "alloc state");
-    KMP_INIT_CUDA(alloc(&c.D2, n), "alloc D2");
-    KMP_INIT_CUDA(alloc(&c.idx, n), "alloc idx");
-    KMP_INIT_CUDA(alloc(&c.drawn, cap_round), "alloc draws");
-    KMP_INIT_CUDA(alloc(&c.cand, c.cap_total), "alloc candidates");
-    KMP_INIT_CUDA(alloc(&c.C, (size_t)c.cap_total * d), "alloc candidate rows");
-    KMP_INIT_CUDA(alloc(&c.w, c.cap_total), "alloc weights");
-    KMP_INIT_CUDA(alloc(&c.rD2, c.cap_total), "alloc recluster D2");
-    KMP_INIT_CUDA(alloc(&c.chosen, k), "alloc chosen");
-    KMP_INIT_CUDA(alloc(&c.rc_cmass, 2 * (size_t)((c.cap_total + 31) / 32)), "alloc recluster masses");
-    KMP_INIT_CUDA(cudaMalloc(&c.rc_sync, kmp::recluster_sync_bytes()), "alloc recluster sync");
-    KMP_INIT_CUDA(alloc(&c.rc_err, 1), "alloc recluster error");
-    KMP_INIT_CUDA(alloc(&c.partials, c.num_partials), "alloc partials");
+    KMP_INIT_CUDA(alloc(c, &c.st, 1), "alloc state");
+    KMP_INIT_CUDA(alloc(c, &c.D2, n), "alloc D2");
+    KMP_INIT_CUDA(alloc(c, &c.idx, n), "alloc idx");
+    KMP_INIT_CUDA(alloc(c, &c.drawn, cap_round), "alloc draws");
+    KMP_INIT_CUDA(alloc(c, &c.cand, c.cap_total), "alloc candidates");
+    KMP_INIT_CUDA(alloc(c, &c.C, (size_t)c.cap_total * d), "alloc candidate rows");
+    KMP_INIT_CUDA(alloc(c, &c.w, c.cap_total), "alloc weights");
+    KMP_INIT_CUDA(alloc(c, &c.rD2, c.cap_total), "alloc recluster D2");
+    KMP_INIT_CUDA(alloc(c, &c.chosen, k), "alloc chosen");
+    KMP_INIT_CUDA(alloc(c, &c.rc_cmass, 2 * (size_t)((c.cap_total + 31) / 32)), "alloc recluster masses");
+    unsigned char *rc_sync = nullptr;
+    KMP_INIT_CUDA(alloc(c, &rc_sync, kmp::recluster_sync_bytes()), "alloc recluster sync");
+    c.rc_sync = rc_sync;
+    KMP_INIT_CUDA(alloc(c, &c.rc_err, 1), "alloc recluster error");
+    KMP_INIT_CUDA(alloc(c, &c.partials, c.num_partials), "alloc partials");
     if (precision != KMPAR_FP32) {
         const int split = precision == KMPAR_BF16X3 ? 1 : 0;
         const int rows = std::max(cap_round, k);
-        KMP_INIT_CUDA(alloc(&c.tc_img, kmp::tc::tc_image_bytes(d, split, rows)), "alloc center tiles");
-        KMP_INIT_CUDA(alloc(&c.tc_cmax, 1), "alloc cmax");
-        KMP_INIT_CUDA(alloc(&c.tc_err, 1), "alloc error word");
-        KMP_INIT_CUDA(alloc(&c.fix_rows, n), "alloc fix-up rows");
-        KMP_INIT_CUDA(alloc(&c.cand1, n), "alloc screening winners");
-        KMP_INIT_CUDA(alloc(&c.tc_v2, n), "alloc screening values");
-        KMP_INIT_CUDA(alloc(&c.tc_ximg, kmp::tc::tc_points_image_bytes(d, split, n)), "alloc points image");
-        KMP_INIT_CUDA(alloc(&c.tc_xnorm, (size_t)((n + 127) / 128) * 128), "alloc point norms");
-        KMP_INIT_CUDA(alloc(&c.tc_anchor, d), "alloc anchor");
-        KMP_INIT_CUDA(alloc(&c.tc_anchor_part, kmp::tc::tc_anchor_scratch_doubles(d)), "alloc anchor sums");
+        KMP_INIT_CUDA(alloc(c, &c.tc_img, kmp::tc::tc_image_bytes(d, split, rows)), "alloc center tiles");
+        KMP_INIT_CUDA(alloc(c, &c.tc_cmax, 1), "alloc cmax");
+        KMP_INIT_CUDA(alloc(c, &c.tc_err, 1), "alloc error word");
+        KMP_INIT_CUDA(alloc(c, &c.fix_rows, n), "alloc fix-up rows");
+        KMP_INIT_CUDA(alloc(c, &c.cand1, n), "alloc screening winners");
+        KMP_INIT_CUDA(alloc(c, &c.tc_v2, n), "alloc screening values");
+        KMP_INIT_CUDA(alloc(c, &c.tc_ximg, kmp::tc::tc_points_image_bytes(d, split, n)), "alloc points image");
+        KMP_INIT_CUDA(alloc(c, &c.tc_xnorm, (size_t)((n + 127) / 128) * 128), "alloc point norms");
+        KMP_INIT_CUDA(alloc(c, &c.tc_anchor, d), "alloc anchor");
+        KMP_INIT_CUDA(alloc(c, &c.tc_anchor_part, kmp::tc::tc_anchor_scratch_doubles(d)), "alloc anchor sums");
         KMP_INIT_CUDA(kmp::tc::launch_anchor(X, n, d, c.tc_anchor_part, c.tc_anchor, c.stream), "anchor");
         KMP_INIT_CUDA(kmp::tc::launch_prep_points(X, n, d, split, c.tc_anchor, c.tc_ximg, c.tc_xnorm, c.stream),
                       "points image");
-        KMP_INIT_CUDA(alloc(&c.fix_cnt, 1), "alloc fix-up count");
+        KMP_INIT_CUDA(alloc(c, &c.fix_cnt, 1), "alloc fix-up count");
         KMP_INIT_CUDA(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream), "memset error word");
     }
     KMP_INIT_CUDA(cudaMemsetAsync(c.st, 0, sizeof(kmp::DevState), c.stream), "memset state");
@@ -289,18 +340,18 @@ kmpar_status kmpar_recluster(kmpar_ctx *ctx, float *centers_dev) {
 static kmpar_status ensure_lloyd_buffers(kmp::Ctx &c) {
     if (c.labels[0]) return KMPAR_OK;
     cudaError_t e;
-    if ((e = alloc(&c.labels[0], c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc labels");
-    if ((e = alloc(&c.labels[1], c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc labels");
-    if ((e = alloc(&c.perm, c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc perm");
-    if ((e = alloc(&c.hist, (size_t)c.nsb * c.k)) != cudaSuccess) return cuda_fail(&c, e, "alloc hist");
-    if ((e = alloc(&c.base, (size_t)c.k + 1)) != cudaSuccess) return cuda_fail(&c, e, "alloc base");
-    if ((e = alloc(&c.piece, (size_t)c.k + 1)) != cudaSuccess) return cuda_fail(&c, e, "alloc pieces");
-    if ((e = alloc(&c.chunk, (size_t)kmp::scan_chunks(c.nsb) * c.k)) != cudaSuccess)
+    if ((e = alloc(c, &c.labels[0], c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc labels");
+    if ((e = alloc(c, &c.labels[1], c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc labels");
+    if ((e = alloc(c, &c.perm, c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc perm");
+    if ((e = alloc(c, &c.hist, (size_t)c.nsb * c.k)) != cudaSuccess) return cuda_fail(&c, e, "alloc hist");
+    if ((e = alloc(c, &c.base, (size_t)c.k + 1)) != cudaSuccess) return cuda_fail(&c, e, "alloc base");
+    if ((e = alloc(c, &c.piece, (size_t)c.k + 1)) != cudaSuccess) return cuda_fail(&c, e, "alloc pieces");
+    if ((e = alloc(c, &c.chunk, (size_t)kmp::scan_chunks(c.nsb) * c.k)) != cudaSuccess)
         return cuda_fail(&c, e, "alloc scan chunks");
-    if ((e = alloc(&c.psum, (size_t)kmp::max_pieces(c.n, c.k) * c.d)) != cudaSuccess)
+    if ((e = alloc(c, &c.psum, (size_t)kmp::max_pieces(c.n, c.k) * c.d)) != cudaSuccess)
         return cuda_fail(&c, e, "alloc piece sums");
-    if ((e = alloc(&c.cost_dev, 4)) != cudaSuccess) return cuda_fail(&c, e, "alloc cost");
-    if (c.precision != KMPAR_FP32 && (e = alloc(&c.dmin, c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc dmin");
+    if ((e = alloc(c, &c.cost_dev, 4)) != cudaSuccess) return cuda_fail(&c, e, "alloc cost");
+    if (c.precision != KMPAR_FP32 && (e = alloc(c, &c.dmin, c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc dmin");
     return KMPAR_OK;
 }
 
@@ -320,10 +371,12 @@ kmpar_status kmpar_lloyd(kmpar_ctx *ctx, float *centers_dev, int32_t max_iter, i
     struct Rec { double cost; int changed; int pad; };
     static_assert(sizeof(Rec) == 16, "record layout");
     if (c.lloyd_rec_cap < max_iter + 1) {
-        if (c.lloyd_rec) cudaFree(c.lloyd_rec);
+        if (c.lloyd_rec) cudaFreeAsync(c.lloyd_rec, c.stream);
         c.lloyd_rec = nullptr;
         c.lloyd_rec_cap = 0;
-        KMP_CUDA(&c, cudaMalloc(&c.lloyd_rec, sizeof(Rec) * (size_t)(max_iter + 1)), "alloc Lloyd records");
+        Rec *r = nullptr;
+        KMP_CUDA(&c, alloc(c, &r, (size_t)(max_iter + 1)), "alloc Lloyd records");
+        c.lloyd_rec = r;
         c.lloyd_rec_cap = max_iter + 1;
     }
     Rec *rec = reinterpret_cast<Rec *>(c.lloyd_rec);
@@ -522,6 +575,16 @@ kmpar_status kmpar_set_timing(kmpar_ctx *ctx, int32_t enable) {
 }
 
 int64_t kmpar_launch_count(void) { return (int64_t)kmp::g_launches.load(); }
+
+kmpar_status kmpar_release_cached_memory(void) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (int dev = 0; dev < kMaxDevices; ++dev) {
+        if (!g_pool[dev]) continue;
+        const cudaError_t e = cudaMemPoolTrimTo(g_pool[dev], 0);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "release cached memory");
+    }
+    return KMPAR_OK;
+}
 
 void kmpar_destroy(kmpar_ctx *ctx) {
     if (!ctx) return;

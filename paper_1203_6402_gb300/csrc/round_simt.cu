@@ -1014,7 +1014,9 @@ __global__ void __launch_bounds__(256) fixup_kernel(const float *__restrict__ X,
 // listed row: the row is staged, lane l sums centers l, l + 32, ... in the exact
 // FP32 difference form (bit-identical to dist2_fp32), a lexicographic top-2 is
 // merged across the warp and decided by decide_top2.  No center is read from
-// global memory more than once per CTA.
+// global memory more than once per CTA.  Listed row t goes to CTA t mod G (G CTAs),
+// so when the rows outnumber the warps the warps that take a second row are spread
+// one or two per SM instead of filling the first SMs.
 template <int MODE>
 __global__ void __launch_bounds__(512) fixup_resident_kernel(const float *__restrict__ X, int d,
                                                             const float *__restrict__ C, int c_cnt, int cap_rows,
@@ -1028,7 +1030,7 @@ __global__ void __launch_bounds__(512) fixup_resident_kernel(const float *__rest
     const int ds = refine_stride(d);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nrows = *rows_cnt;
-    if ((int64_t)blockIdx.x * nwarps >= nrows) return;   // uniform per block: nothing for this CTA
+    if ((int)blockIdx.x >= nrows) return;   // uniform per block: nothing for this CTA
     const int begin = MODE == MODE_ROUND ? st->batch_begin : 0;
     const int cnt = MODE == MODE_ROUND ? min(st->batch_cnt, cap_rows) : c_cnt;
     float *Cs = fsm;                                   // cap_rows x ds
@@ -1043,7 +1045,7 @@ __global__ void __launch_bounds__(512) fixup_resident_kernel(const float *__rest
     cp_async_wait<0>();
     __syncthreads();
     const float FMAX = FLT_MAX;
-    for (int t = blockIdx.x * nwarps + wid; t < nrows; t += gridDim.x * nwarps) {   // uniform per warp
+    for (int t = wid * gridDim.x + blockIdx.x; t < nrows; t += gridDim.x * nwarps) {   // uniform per warp
         const int64_t R = rows[t];
         for (int q = lane; q < d; q += 32) xs[q] = __ldg(X + R * d + q);
         __syncwarp();

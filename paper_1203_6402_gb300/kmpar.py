@@ -22,7 +22,7 @@ PRECISIONS = {"fp32": KMPAR_FP32, "bf16": KMPAR_BF16, "bf16x3": KMPAR_BF16X3}
 
 EXPORTED = ["kmpar_init", "kmpar_round", "kmpar_weight", "kmpar_recluster", "kmpar_lloyd", "kmpar_cost",
             "kmpar_fit", "kmpar_state", "kmpar_get_stats", "kmpar_uniforms", "kmpar_set_timing",
-            "kmpar_launch_count", "kmpar_cost_noalloc", "kmpar_destroy",
+            "kmpar_launch_count", "kmpar_cost_noalloc", "kmpar_destroy", "kmpar_release_cached_memory",
             "kmpar_status_string", "kmpar_last_error"]
 
 
@@ -86,6 +86,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kmpar_launch_count": (i64, []),
         "kmpar_cost_noalloc": (i32, [P, i64, i32, P, i32, ctypes.POINTER(f64), P]),
         "kmpar_destroy": (None, [P]),
+        "kmpar_release_cached_memory": (i32, []),
         "kmpar_status_string": (ctypes.c_char_p, [i32]),
         "kmpar_last_error": (ctypes.c_char_p, [P]),
     }
@@ -186,6 +187,10 @@ def kmpar_launch_count() -> int:
 
 def kmpar_destroy(ctx: int) -> None:
     load().kmpar_destroy(ctx)
+
+
+def kmpar_release_cached_memory() -> None:
+    _check(load().kmpar_release_cached_memory())
 
 
 # ------------------------------------------------------------------ torch convenience

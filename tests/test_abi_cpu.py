@@ -54,6 +54,8 @@ def test_argument_errors_need_no_gpu(lib):
     assert kmpar._lib.kmpar_status_string(kmpar.KMPAR_ERR_CAPACITY) == b"round drew more points than its capacity"
     with pytest.raises(kmpar.KmparError):
         kmpar.kmpar_init(1, 10, 0, 2, 4.0, 2, 0, kmpar.KMPAR_FP32)
+    # no context has allocated, so there is no pool to trim
+    assert kmpar._lib.kmpar_release_cached_memory() == kmpar.KMPAR_OK
 
 
 def test_missing_library_fails_loudly(tmp_path):

@@ -237,7 +237,7 @@ def test_run_to_run_deterministic(km):
     X = datagen.kdd_like(30000, seed=12)
     Xd = _dev(X)
     res = []
-    for _ in range(2):
+    for _ in range(3):
         g = km.KMeansPar(Xd, 50, 100.0, 5, 21)
         for r in range(1, 6):
             g.round(r)
@@ -246,8 +246,13 @@ def test_run_to_run_deterministic(km):
         out = g.lloyd(C, 30)
         res.append((C.cpu().numpy(), out["labels"].cpu().numpy(), out["final_cost"]))
         g.close()
+        # the second context reuses the pooled buffers of the first; before the
+        # third, the pool hands its memory back to the driver
+        if len(res) == 2:
+            km.kmpar_release_cached_memory()
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
-    assert res[0][2] == res[1][2]
+    assert np.array_equal(res[0][0], res[2][0]) and np.array_equal(res[0][1], res[2][1])
+    assert res[0][2] == res[1][2] == res[2][2]
 
 
 @pytest.mark.parametrize("form", ["cluster", "grid"])

@@ -759,30 +759,37 @@ __global__ void __launch_bounds__(256) refine_kernel(const float *__restrict__ X
     }
 }
 
-// Centers resident in shared memory (used when they fit and lane-per-row reads are
-// conflict-free: d odd or d = 2 mod 4).  Persistent CTAs copy the pass's centers
-// once; each warp then walks 32-row blocks of X.  A block is contiguous in X, so
-// flat 16-byte asynchronous copies bring it in, double-buffered per warp, and the
-// next block's screening results are loaded while the current block is summed.
+// Centers resident in shared memory (used when lane-per-row reads are conflict-free:
+// d odd or d = 2 mod 4).  Persistent CTAs copy the pass's centers once; each warp
+// then walks 32-row blocks of X.  A block is contiguous in X, so flat 16-byte
+// asynchronous copies bring it in, double-buffered per warp, and the next block's
+// screening results are loaded while the current block is summed.  A pass whose
+// centers exceed shared memory runs as a few launches, each holding the slice
+// [part_lo, part_lo + part_rows) of the centers (plus the next row, the partner of
+// a pair that ends the slice): a row is refined by the launch whose slice holds its
+// screened pair, and rows without one are listed for the fix-up by the first.
 __host__ __device__ __forceinline__ int resident_center_floats(int cap_rows, int d) { return (cap_rows * d + 3) & ~3; }
 __host__ __device__ __forceinline__ int resident_block_floats(int d) { return (32 * d + 3) & ~3; }
 
 template <int MODE>
 __global__ void __launch_bounds__(512) refine_resident_kernel(
-    const float *__restrict__ X, int64_t n, int d, const float *__restrict__ C, int cap_rows,
-    const int32_t *__restrict__ cand1, const float *__restrict__ v2s, ScreenBound sb, float *D2, int32_t *idx,
-    int32_t *labels, const int32_t *prev, int *changed, float *dmin, unsigned long long *fp64_cnt,
-    unsigned long long *wide_cnt) {
+    const float *__restrict__ X, int64_t n, int d, const float *__restrict__ C, int cap_rows, int part_lo,
+    int part_rows, int hold_rows, const int32_t *__restrict__ cand1, const float *__restrict__ v2s, ScreenBound sb,
+    float *D2, int32_t *idx, int32_t *labels, const int32_t *prev, int *changed, float *dmin,
+    unsigned long long *fp64_cnt, unsigned long long *wide_cnt) {
     extern __shared__ __align__(16) float rsm[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int begin = MODE == MODE_ROUND ? sb.st->batch_begin : 0;
     const int cnt = MODE == MODE_ROUND ? min(sb.st->batch_cnt, cap_rows) : cap_rows;
+    const int lo = part_lo, hi = min(cnt, part_lo + part_rows);
+    if (lo > 0 && lo >= hi) return;   // uniform per block: the batch ends before this slice
+    const int nhold = max(0, min(cnt, hi + 1) - lo);   // <= hold_rows
     const int xfl = resident_block_floats(d);
     float *Cs = rsm;
-    float *xb = rsm + resident_center_floats(cap_rows, d) + wid * 2 * xfl;
+    float *xb = rsm + resident_center_floats(hold_rows, d) + wid * 2 * xfl;
     {
-        const float *src = C + (int64_t)begin * d;
-        const int nf = cnt * d;
+        const float *src = C + (int64_t)(begin + lo) * d;
+        const int nf = nhold * d;
         if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
             for (int f = threadIdx.x; f < (nf >> 2); f += blockDim.x) cp_async16(Cs + 4 * f, src + 4 * f);
             for (int f = (nf & ~3) + threadIdx.x; f < nf; f += blockDim.x) cp_async4(Cs + f, src + f);
@@ -838,11 +845,13 @@ __global__ void __launch_bounds__(512) refine_resident_kernel(
         const bool valid = R < n;
         cp_async_wait<1>();   // this block is in (the next one may be pending)
         __syncwarp();
-        bool fix = valid && (j < 0 || j - begin >= cnt);
-        if (valid && !fix) {
-            const bool has_b = j + 1 - begin < cnt;
+        const int jl = j - begin;   // batch-local pair start (j = -1: none)
+        const bool screened = j >= 0 && jl >= 0 && jl < cnt;
+        bool fix = valid && !screened && lo == 0;
+        if (valid && screened && jl >= lo && jl < hi) {
+            const bool has_b = jl + 1 < cnt;
             const float *xa = cur + lane * d;
-            const float *ca = Cs + (int64_t)(j - begin) * d;
+            const float *ca = Cs + (int64_t)(jl - lo) * d;
             float va, vb = 0.f;
             if (pairs) {
                 const float *cp[2] = {ca, has_b ? ca + d : ca};
@@ -872,8 +881,8 @@ __global__ void __launch_bounds__(512) refine_resident_kernel(
     }
 }
 
-// warps of a resident refine CTA (0: the centers do not fit, or the stride is not
-// conflict-free: use refine_kernel)
+// warps of a resident refine CTA holding all cap_rows centers (0: they do not fit,
+// or the stride is not conflict-free)
 int resident_warps(int cap_rows, int d) {
     if (!((d & 1) || (d & 3) == 2)) return 0;
     const size_t budget = 200u * 1024u;
@@ -886,6 +895,31 @@ int resident_warps(int cap_rows, int d) {
 
 size_t resident_smem_bytes(int cap_rows, int d, int warps) {
     return sizeof(float) * ((size_t)resident_center_floats(cap_rows, d) + (size_t)warps * 2 * resident_block_floats(d));
+}
+
+// How the resident refine covers a pass of cap_rows centers: `parts` launches of
+// `rows` centers each (`hold` rows of shared memory, `warps` warps per CTA).
+// parts = 0: the per-row kernel (refine_kernel) is used instead.
+struct ResidentPlan {
+    int parts, rows, hold, warps;
+};
+
+ResidentPlan resident_plan(int cap_rows, int d) {
+    const int w1 = resident_warps(cap_rows, d);
+    if (w1 > 0) return {1, cap_rows, cap_rows, w1};
+    if (!((d & 1) || (d & 3) == 2)) return {0, 0, 0, 0};
+    // slices: 8 warps, the rest of the 200 KB for one slice of centers plus the
+    // partner row; each launch reads X once, so at most 3 of them
+    const int warps = 8;
+    const size_t per_warp = sizeof(float) * 2 * (size_t)resident_block_floats(d);
+    if (warps * per_warp + sizeof(float) * 66 * (size_t)d + 16 > 200u * 1024u) return {0, 0, 0, 0};
+    const size_t cfloats = (200u * 1024u - warps * per_warp) / sizeof(float);
+    const int hold = (int)((cfloats - 3) / (size_t)d);   // resident_center_floats adds at most 3
+    const int rows = (hold - 1) & ~1;
+    if (rows < 64) return {0, 0, 0, 0};
+    const int parts = (cap_rows + rows - 1) / rows;
+    if (parts > 3) return {0, 0, 0, 0};
+    return {parts, rows, rows + 1, warps};
 }
 
 // warps per refine CTA: 96 staged rows (32 points, 32 pairs of centers) of
@@ -1182,21 +1216,25 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
     sb.fix_rows = c.fix_rows; sb.fix_cnt = c.fix_cnt;
     tc::tc_bound(c.d, split, &sb.ep, &sb.en);
     const int cap_rows = mode_round ? c.cap_round : k;
-    const int rw = resident_warps(cap_rows, c.d);
-    if (rw > 0) {
-        const size_t rsm = resident_smem_bytes(cap_rows, c.d, rw);
+    const ResidentPlan rp = resident_plan(cap_rows, c.d);
+    if (rp.parts > 0) {
+        const int rw = rp.warps;
+        const size_t rsm = resident_smem_bytes(rp.hold, c.d, rw);
         const int64_t nb = (c.n + 31) / 32;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(c.num_sms, (nb + rw - 1) / rw));
-        if (mode_round)
-            refine_resident_kernel<MODE_ROUND><<<grid, 32 * rw, rsm, c.stream>>>(
-                c.X, c.n, c.d, C, cap_rows, c.cand1, c.tc_v2, sb, c.D2, c.idx, nullptr, nullptr, nullptr, nullptr,
-                &c.st->argmin_fp64, &c.st->argmin_wide);
-        else
-            refine_resident_kernel<MODE_ASSIGN><<<grid, 32 * rw, rsm, c.stream>>>(
-                c.X, c.n, c.d, C, cap_rows, c.cand1, c.tc_v2, sb, nullptr, nullptr, labels, prev, changed, dmin,
-                &c.st->argmin_fp64, &c.st->argmin_wide);
-        count_launches(1);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        for (int part = 0; part < rp.parts; ++part) {
+            const int lo = part * rp.rows;
+            if (mode_round)
+                refine_resident_kernel<MODE_ROUND><<<grid, 32 * rw, rsm, c.stream>>>(
+                    c.X, c.n, c.d, C, cap_rows, lo, rp.rows, rp.hold, c.cand1, c.tc_v2, sb, c.D2, c.idx, nullptr,
+                    nullptr, nullptr, nullptr, &c.st->argmin_fp64, &c.st->argmin_wide);
+            else
+                refine_resident_kernel<MODE_ASSIGN><<<grid, 32 * rw, rsm, c.stream>>>(
+                    c.X, c.n, c.d, C, cap_rows, lo, rp.rows, rp.hold, c.cand1, c.tc_v2, sb, nullptr, nullptr, labels,
+                    prev, changed, dmin, &c.st->argmin_fp64, &c.st->argmin_wide);
+            count_launches(1);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         if ((e = count_fixups(c)) != cudaSuccess) return e;
         return launch_fixup(c, mode_round, C, k, labels, prev, changed, dmin);
     }

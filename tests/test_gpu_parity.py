@@ -147,6 +147,8 @@ def test_parity_fp32(km, orc, name, mk, k, ell, rounds, seed):
 TC_CASES = [c for c in CASES if c[0] != "d130_generic"] + [
     ("gmm_d42_multi_tile", lambda: datagen.gauss_mixture(9000, 42, 40, 10.0, seed=13), 300, 600.0, 3, 9),
     ("kdd_ragged_3001", lambda: datagen.kdd_like(3001, seed=14), 40, 80.0, 4, 10),
+    # round batches of ~1,500 candidates: the resident refine runs in three slices
+    ("kdd_sliced_batches", lambda: datagen.kdd_like(6000, seed=16), 100, 1500.0, 2, 11),
 ]
 
 
@@ -266,14 +268,16 @@ def test_recluster_forms_match_oracle(km, orc, form, monkeypatch):
     assert diag["parted"] is None, diag
 
 
-@pytest.mark.parametrize("k,d", [(420, 128), (37, 15)], ids=["many_wide_clusters", "few_narrow_clusters"])
-def test_lloyd_from_fixed_centers_matches_oracle(km, orc, k, d):
+@pytest.mark.parametrize("k,d,precision", [(420, 128, "fp32"), (37, 15, "fp32"), (1000, 42, "bf16x3")],
+                         ids=["many_wide_clusters", "few_narrow_clusters", "sliced_resident_refine"])
+def test_lloyd_from_fixed_centers_matches_oracle(km, orc, k, d, precision):
     """Lloyd alone (Sec. 3.1 centroid, Sec. 1 iteration) from fixed seed centers:
     the segmented centroid sums and the assignment agree with the oracle, also
-    with many clusters of wide rows (k = 420, d = 128)."""
+    with many clusters of wide rows (k = 420, d = 128) and with 1,000 centers
+    screened on the tensor cores (their refine runs in two shared-memory slices)."""
     X = datagen.gauss_mixture(2500, d, 40, 100.0, seed=33)
     C0 = np.ascontiguousarray(X[:k])
-    g = km.KMeansPar(_dev(X), k, 2.0 * k, 1, 5)
+    g = km.KMeansPar(_dev(X), k, 2.0 * k, 1, 5, precision=precision)
     C = _dev(C0)
     out = g.lloyd(C, 15, labels=True, hist=True)
     lab = out["labels"].cpu().numpy()

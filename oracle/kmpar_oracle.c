@@ -14,6 +14,7 @@
  *   - Algorithm 2 (k-means||) steps 1-2 (init), 4-5 (rounds),
  *     7 (weights), 8 (recluster with k-means++, Sec. 4.2)       Sec. 3.3
  *   - Algorithm 1 (k-means++), in its weighted form, for step 8 Sec. 3.1
+ *   - the exactly-l-per-round variant of step 4                  Sec. 5.3
  *   - Lloyd's iteration                                         Sec. 1, Sec. 3.1
  *
  * Arithmetic: coordinates are read as FP32 and widened to FP64; every distance,
@@ -45,6 +46,7 @@
 #define ORC_TAG_INIT 1u
 #define ORC_TAG_SAMPLE 2u
 #define ORC_TAG_RECLUSTER 3u
+#define ORC_TAG_EXACT 4u
 
 /* ---------------------------------------------------------------------------
  * Philox4x32-10 (SC'11).  Each of the ten rounds multiplies the even words by the
@@ -190,6 +192,68 @@ int64_t orc_sample(const double *D2, int64_t n, double phi, double ell, uint32_t
             cnt++;
         }
     }
+    return cnt;
+}
+
+/* ---------------------------------------------------------------------------
+ * Sec. 5.3 variant of Algorithm 2 step 4 (the runs of Fig. 5.1): exactly
+ * L = floor(l) points per round from the D^2 distribution, without replacement.
+ * Written as exponential clocks: point x rings at kappa_x = -ln(u_x) / D^2(x),
+ * u_x from counter (x, round, EXACT).  The order in which the clocks ring is the
+ * order of successive draws, each proportional to D^2 among the points not drawn
+ * yet (D^2 as at the start of the round), so the L earliest clocks are the
+ * sample.  Equal times go to the lower x.  Points with D^2 = 0 never ring: when
+ * fewer than L points have D^2 > 0, all of those are drawn.  Drawn points are
+ * written in ascending x.  *near (optional) is set to 1 when another clock rings
+ * within w * kappa of the L-th one (only when more than L points can ring).
+ * Returns the number drawn.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double key;
+    int64_t x;
+} orc_clock;
+
+static int orc_clock_cmp(const void *pa, const void *pb) {
+    const orc_clock *a = (const orc_clock *)pa, *b = (const orc_clock *)pb;
+    if (a->key < b->key) return -1;
+    if (a->key > b->key) return 1;
+    return (a->x > b->x) - (a->x < b->x);
+}
+
+static int orc_i64_cmp(const void *pa, const void *pb) {
+    const int64_t a = *(const int64_t *)pa, b = *(const int64_t *)pb;
+    return (a > b) - (a < b);
+}
+
+int64_t orc_sample_exact(const double *D2, int64_t n, double ell, uint32_t round, uint64_t seed, double w,
+                         int64_t *out, int8_t *near) {
+    if (near) *near = 0;
+    const int64_t L = (int64_t)floor(ell);
+    if (L < 1 || n < 1) return 0;
+    orc_clock *cl = (orc_clock *)malloc(sizeof(orc_clock) * (size_t)n);
+    if (!cl) return -1;
+    int64_t npos = 0;
+    for (int64_t x = 0; x < n; ++x) {
+        if (D2[x] > 0.0) {
+            double u = orc_uniform((uint64_t)x, round, ORC_TAG_EXACT, seed);
+            cl[npos].key = -log(u) / D2[x];
+            cl[npos].x = x;
+            npos++;
+        }
+    }
+    qsort(cl, (size_t)npos, sizeof(orc_clock), orc_clock_cmp);
+    const int64_t cnt = npos < L ? npos : L;
+    if (near && npos > L) {
+        const double t = cl[L - 1].key;
+        for (int64_t j = 0; j < npos; ++j)
+            if (j != L - 1 && fabs(cl[j].key - t) <= w * t) {
+                *near = 1;
+                break;
+            }
+    }
+    for (int64_t j = 0; j < cnt; ++j) out[j] = cl[j].x;
+    qsort(out, (size_t)cnt, sizeof(int64_t), orc_i64_cmp);
+    free(cl);
     return cnt;
 }
 

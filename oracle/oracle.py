@@ -26,7 +26,7 @@ _SRC = os.path.join(_HERE, "kmpar_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
-TAG_INIT, TAG_SAMPLE, TAG_RECLUSTER = 1, 2, 3
+TAG_INIT, TAG_SAMPLE, TAG_RECLUSTER, TAG_EXACT = 1, 2, 3, 4
 
 _lib = None
 
@@ -59,6 +59,7 @@ def _load():
         "orc_init_index": (i64, [i64, u64]),
         "orc_init": (f64, [P, i64, i32, i64, P, P]),
         "orc_sample": (i64, [P, i64, f64, f64, u32, u64, P, i64, P, P]),
+        "orc_sample_exact": (i64, [P, i64, f64, u32, u64, f64, P, P]),
         "orc_update": (f64, [P, i64, i32, P, i64, i64, P, P, P]),
         "orc_weights": (None, [P, i64, i64, P]),
         "orc_recluster": (i32, [P, P, i64, i32, i64, u64, P, P]),
@@ -142,6 +143,21 @@ def sample(D2, phi: float, ell: float, rnd: int, seed: int):
     return out[:cnt].copy(), p, near.astype(bool)
 
 
+def sample_exact(D2, ell: float, rnd: int, seed: int, w: float = 0.0):
+    """Sec. 5.3 variant of step 4: exactly floor(l) draws without replacement,
+    proportional to D^2 (the earliest exponential clocks -ln(u)/D^2).  Returns the
+    drawn points (ascending) and whether another clock rings within w (relative)
+    of the last drawn one."""
+    D2 = np.ascontiguousarray(D2, dtype=np.float64)
+    n = D2.shape[0]
+    out = np.empty(max(n, 1), np.int64)
+    near = ctypes.c_int8(0)
+    cnt = _load().orc_sample_exact(_p(D2), n, ell, rnd, seed, w, _p(out), ctypes.byref(near))
+    if cnt < 0:
+        raise MemoryError("oracle: out of host memory")
+    return out[:cnt].copy(), bool(near.value)
+
+
 def update(X, sel, first_id: int, D2, idx):
     """Algorithm 2 step 5: union with the rows sel of X; D^2/idx updated in place."""
     X = _f32(X)
@@ -190,8 +206,8 @@ def lloyd(X, C, max_iter: int):
 @dataclass
 class RoundState:
     sel: np.ndarray          # rows of X drawn this round, ascending
-    p: np.ndarray            # p_x used for the draw
-    near_sample: np.ndarray  # |u - p| <= 1e-6
+    p: np.ndarray            # p_x used for the draw (None for exactly-l rounds)
+    near_sample: np.ndarray  # |u - p| <= 1e-6 (exactly-l rounds: the boundary flag)
     D2: np.ndarray           # after the union/update
     idx: np.ndarray
     phi: float
@@ -215,8 +231,11 @@ class KMeansParResult:
     seed_cost: float = 0.0
 
 
-def kmeans_par(X, k: int, ell: float, rounds: int, seed: int) -> KMeansParResult:
-    """Algorithm 2 steps 1-8, with per-round snapshots."""
+def kmeans_par(X, k: int, ell: float, rounds: int, seed: int, sampling: str = "bernoulli",
+               w: float = 0.0) -> KMeansParResult:
+    """Algorithm 2 steps 1-8, with per-round snapshots.  sampling="exact" draws
+    exactly floor(l) points per round without replacement (Sec. 5.3); w is the
+    relative window of its boundary flag."""
     X = _f32(X)
     n = X.shape[0]
     i0 = init_index(n, seed)
@@ -225,7 +244,11 @@ def kmeans_par(X, k: int, ell: float, rounds: int, seed: int) -> KMeansParResult
     cand = [i0]
     phi = psi
     for r in range(1, rounds + 1):
-        sel, p, nsamp = sample(D2, phi, ell, r, seed)
+        if sampling == "exact":
+            sel, bnear = sample_exact(D2, ell, r, seed, w)
+            p, nsamp = None, np.array([bnear])
+        else:
+            sel, p, nsamp = sample(D2, phi, ell, r, seed)
         phi, narg = update(X, sel, len(cand), D2, idx)
         cand.extend(int(s) for s in sel)
         res.rounds.append(RoundState(sel, p, nsamp, D2.copy(), idx.copy(), phi, narg))
@@ -239,8 +262,8 @@ def kmeans_par(X, k: int, ell: float, rounds: int, seed: int) -> KMeansParResult
     return res
 
 
-def fit(X, k: int, ell: float, rounds: int, seed: int, max_iter: int):
+def fit(X, k: int, ell: float, rounds: int, seed: int, max_iter: int, sampling: str = "bernoulli"):
     """k-means|| seeding followed by Lloyd's iteration."""
-    par = kmeans_par(X, k, ell, rounds, seed)
+    par = kmeans_par(X, k, ell, rounds, seed, sampling)
     C, labels, it, fc, hist, near = lloyd(X, par.seed_centers, max_iter)
     return par, dict(centers=C, labels=labels, iters=it, final_cost=fc, cost_hist=hist, near=near)

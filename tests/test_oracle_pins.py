@@ -4,6 +4,7 @@ the paper's theorems and the paper's printed Table 1.
 
 Paper: Bahmani et al., "Scalable K-Means++" (arXiv:1203.6402).
 """
+import collections
 import itertools
 import json
 import math
@@ -156,6 +157,88 @@ def test_sample_inclusion_frequency(orc):
 
 
 # ----------------------------------------------------------------- Algorithm 2 steps 5, 7
+# ----------------------------------------------------------------- Sec. 5.3 variant
+def _successive_pair_law(D2):
+    """P({a, b}) when two points are drawn one after the other, each draw
+    proportional to D^2 among the points not drawn yet (the plain definition)."""
+    W = float(np.sum(D2))
+    law = collections.defaultdict(float)
+    for a, b in itertools.permutations(range(len(D2)), 2):
+        if D2[a] > 0 and D2[b] > 0:
+            law[(min(a, b), max(a, b))] += D2[a] / W * D2[b] / (W - D2[a])
+    return dict(law)
+
+
+def test_exact_sample_law_is_successive_d2_draws(orc):
+    """Exactly-l rounds (Sec. 5.3): for 5 points (one with D^2 = 0) and l = 2 the
+    frequency of every drawn pair over 20,000 independent rounds matches the law
+    of two successive D^2-proportional draws without replacement (chi-square).
+    Keys u/D^2 or -ln(u) D^2 in place of -ln(u)/D^2 fail this."""
+    D2 = np.array([1.0, 2.0, 3.0, 4.0, 0.0])
+    law = _successive_pair_law(D2)
+    N = 20000
+    cnt = collections.Counter()
+    for r in range(1, N + 1):
+        sel, _ = orc.sample_exact(D2, 2.0, r, 77)
+        assert len(sel) == 2 and sel[0] < sel[1] and 4 not in sel
+        cnt[(int(sel[0]), int(sel[1]))] += 1
+    pairs = sorted(law)
+    assert set(cnt) <= set(pairs)
+    obs = np.array([cnt[p] for p in pairs], np.float64)
+    ex = np.array([law[p] * N for p in pairs])
+    chi2 = float(((obs - ex) ** 2 / ex).sum())
+    assert stats.chi2.sf(chi2, len(pairs) - 1) > 1e-3, (chi2, obs, ex)
+
+
+def test_exact_sample_uniform_inclusion_and_counts(orc):
+    """Equal D^2: each point is drawn with probability l/n (z-test over 6,000
+    rounds); exactly floor(l) distinct points in ascending order; when fewer points
+    than l have D^2 > 0, all of those and no other."""
+    n, L, N = 10, 3, 6000
+    hits = np.zeros(n)
+    for r in range(1, N + 1):
+        sel, _ = orc.sample_exact(np.ones(n), float(L), r, 5)
+        assert len(sel) == L and np.all(np.diff(sel) > 0)
+        hits[sel] += 1
+    p = L / n
+    z = (hits - N * p) / math.sqrt(N * p * (1 - p))
+    assert np.all(np.abs(z) < 4.5), z
+    sel, near = orc.sample_exact(np.array([0.0, 2.0, 0.0, 5.0, 0.0]), 4.0, 1, 9)
+    assert list(sel) == [1, 3] and not near
+    assert len(orc.sample_exact(np.zeros(4), 2.0, 1, 9)[0]) == 0
+    assert len(orc.sample_exact(np.ones(4), 0.5, 1, 9)[0]) == 0
+    assert len(orc.sample_exact(np.ones(50), 7.9, 1, 9)[0]) == 7
+
+
+def test_exact_sample_tie_and_boundary_flag(orc):
+    """D^2 set so that two clocks ring at exactly the same time: with l = 1 the
+    lower point is drawn and the boundary is flagged; moved apart, no flag."""
+    seed, rnd = 3, 1
+    e = [-math.log(orc.uniform(x, rnd, orc.TAG_EXACT, seed)) for x in range(3)]
+    D2 = np.array([e[0], e[1], e[2] / 10.0])          # kappa = 1, 1, ~10
+    sel, near = orc.sample_exact(D2, 1.0, rnd, seed, 1e-9)
+    assert list(sel) == [0] and near
+    D2 = np.array([e[0], e[1] / 2.0, e[2] / 10.0])    # kappa = 1, 2, ~10
+    sel, near = orc.sample_exact(D2, 1.0, rnd, seed, 1e-3)
+    assert list(sel) == [0] and not near
+    D2 = np.array([e[0] / 3.0, e[1] / 2.0, e[2] / 10.0])   # kappa = 3, 2, ~10: point 1 first
+    sel, near = orc.sample_exact(D2, 2.0, rnd, seed, 1e-3)
+    assert list(sel) == [0, 1] and not near
+
+
+def test_exact_rounds_add_exactly_l(orc):
+    """The whole seeding with exactly-l rounds: 1 + r l candidates, sum w = n, and
+    D^2/idx the brute-force nearest candidate."""
+    X = datagen.kdd_like(3000, seed=71)
+    par = orc.kmeans_par(X, 20, 50.0, 4, 13, sampling="exact")
+    assert len(par.cand) == 1 + 4 * 50 and len(set(par.cand.tolist())) == len(par.cand)
+    assert par.w.sum() == len(X)
+    j, dmin = nearest_lowest(X, X[par.cand])
+    np.testing.assert_allclose(par.D2, dmin, rtol=1e-12, atol=1e-9)
+    assert np.all((par.idx == j) | np.isclose(par.D2, np.partition(
+        cdist(X.astype(np.float64), X[par.cand].astype(np.float64), "sqeuclidean"), 1, axis=1)[:, 1], rtol=1e-9))
+
+
 def test_rounds_keep_nearest_center_and_weights(orc):
     X = datagen.kdd_like(3000, seed=4)  # heavy tails and 20% duplicated rows
     res = orc.kmeans_par(X, k=20, ell=40.0, rounds=4, seed=11)

@@ -141,7 +141,7 @@ def run_ours(args, rank, world):
     prec = km.PRECISIONS[args.precision]
 
     def step(timing=False):
-        g = km.KMeansPar(X, k, ell, rounds, seed=7 + rank, precision=prec, stream=stream)
+        g = km.KMeansPar(X, k, ell, rounds, seed=7 + rank, precision=prec, stream=stream, sampling=args.sampling)
         if timing:
             km.kmpar_set_timing(g.ctx, True)
         for i in range(1, rounds + 1):
@@ -190,6 +190,7 @@ def run_ours(args, rank, world):
 
     # end to end through the public API with host buffers (pinned), copies inside the timer
     Xpin = torch.from_numpy(Xh).pin_memory()
+    fit_flags = km.KMPAR_EXACT_SAMPLING if args.sampling == "exact" else 0
     Cpin = torch.empty(k, d, dtype=torch.float32).pin_memory()
     Lpin = torch.empty(n, dtype=torch.int32).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
@@ -198,7 +199,7 @@ def run_ours(args, rank, world):
     e2e_evals = 0
     for _ in range(e2e_steps):
         r = km.kmpar_fit(Xpin.data_ptr(), n, d, k, ell, rounds, 7 + rank, prec, max_iter, Cpin.data_ptr(),
-                         Lpin.data_ptr(), flags=km.KMPAR_HOST_BUFFERS, stream=stream.cuda_stream)
+                         Lpin.data_ptr(), flags=km.KMPAR_HOST_BUFFERS | fit_flags, stream=stream.cuda_stream)
         assert r["iters"] == out_t["iters"], "end-to-end run took a different trajectory"
         e2e_evals += evals
     torch.cuda.synchronize()
@@ -259,7 +260,8 @@ def run_ours(args, rank, world):
         "dtype": "f32" if args.precision == "fp32" else "bf16 (split hi/lo) screening, f32 refine, f64 sums",
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: n={n} d={d} k={k} l={ell:g} r={rounds} Lloyd<={max_iter}",
-                   "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "precision": args.precision, "sampling": args.sampling,
+                   "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 (X {n * d * 4 / 1e6:.0f} MB > 129 MB)"},
         "init_lloyd_s": ms_max / args.steps / 1e3,
         "dist_evals_per_step": evals, "dist_evals_parts": parts,
@@ -286,7 +288,7 @@ def oracle_sample_run(args, n_s: int, lloyd_iters: int):
     k, ell, rounds = w["k"], w["ell"], w["rounds"]
     Xs = datagen.make(args.workload, seed=1000, n=n_s)
     t0 = time.perf_counter()
-    par = oracle.kmeans_par(Xs, k, ell, rounds, seed=7)
+    par = oracle.kmeans_par(Xs, k, ell, rounds, seed=7, sampling=getattr(args, "sampling", "bernoulli"))
     _, _, it, _, _, _ = oracle.lloyd(Xs, par.seed_centers, lloyd_iters)
     dt = time.perf_counter() - t0
     evals = n_s + n_s * (len(par.cand) - 1) + k * len(par.cand) + (it + 1) * n_s * k
@@ -370,6 +372,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16", "bf16x3"])
     ap.add_argument("--workload", default="kdd_n1M_d42_k500")
+    ap.add_argument("--sampling", default="bernoulli", choices=["bernoulli", "exact"],
+                    help="round draws: independent (Alg. 2 step 4) or exactly l per round (Sec. 5.3)")
     ap.add_argument("--n", type=int, default=0, help="override n (same recipe)")
     ap.add_argument("--ell-factor", type=float, default=0.0, help="override l as a multiple of k")
     ap.add_argument("--cpu-sample-n", type=int, default=40000)

@@ -8,6 +8,7 @@
  *   kmpar_init       Alg. 2 steps 1-2  first center uniform over X; psi = phi_X(C)
  *   kmpar_round      Alg. 2 steps 4-5  draw each x with p = min(1, l D^2(x)/phi),
  *                                       C <- C u C', update D^2 and phi
+ *   kmpar_set_sampling  Sec. 5.3       or draw exactly floor(l) points per round
  *   kmpar_weight     Alg. 2 step 7     w_c = #points nearest to candidate c
  *   kmpar_recluster  Alg. 2 step 8     weighted k-means++ (Alg. 1, Sec. 4.2) to k
  *   kmpar_lloyd      Sec. 1, Sec. 3.1  Lloyd's iteration to a stable assignment
@@ -27,7 +28,7 @@
  *
  * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = seed and
  * counter = (i_lo, i_hi, round, tag); tag 1 = first center, 2 = round draws,
- * 3 = reclustering draws; a uniform double is (a 2^26 + b) / 2^53 with
+ * 3 = reclustering draws, 4 = exactly-l round clocks; a uniform double is (a 2^26 + b) / 2^53 with
  * a = word0 >> 5, b = word1 >> 6.  Results are a pure function of
  * (X, k, l, rounds, seed, precision).
  *
@@ -81,7 +82,9 @@ typedef struct {
     int32_t d, k, rounds_done, lloyd_iters;
     int64_t round_added[64];      /* |C'_i| for i = 1..rounds (index i-1)            */
     double  phi[65];              /* psi, then phi after each round                  */
-    int64_t sample_near;          /* draws with |u - p| <= 1e-6                      */
+    int64_t sample_near;          /* draws with |u - p| <= 1e-6; exactly-l rounds:
+                                     rounds whose last drawn clock has another
+                                     within (2d+16) 2^-24 (relative) of it           */
     int64_t sample_refined;       /* draws re-decided with an FP64 D^2                */
     int64_t argmin_fp64;          /* argmin decisions re-decided in FP64              */
     int64_t argmin_wide;          /* screening windows that held more than 2 centers  */
@@ -200,14 +203,34 @@ KMPAR_API kmpar_status kmpar_cost_noalloc(const float *X, int64_t n, int32_t d, 
 /*
  * The whole path in one call: init, rounds 1..r, weight, recluster, Lloyd.
  * flags & KMPAR_HOST_BUFFERS: X, centers_out and labels_out are HOST pointers
- * (copied in and out inside the call); otherwise device pointers.  seed_cost,
- * final_cost and iters are host pointers (nullable).  labels_out is nullable.
+ * (copied in and out inside the call); otherwise device pointers.
+ * flags & KMPAR_EXACT_SAMPLING: exactly floor(l) draws per round (see
+ * kmpar_set_sampling).  seed_cost, final_cost and iters are host pointers
+ * (nullable).  labels_out is nullable.
  */
 #define KMPAR_HOST_BUFFERS 1
+#define KMPAR_EXACT_SAMPLING 2
 KMPAR_API kmpar_status kmpar_fit(const float *X, int64_t n, int32_t d, int32_t k, double ell, int32_t rounds,
                        uint64_t seed, int32_t precision, int32_t max_iter, float *centers_out,
                        int32_t *labels_out, double *seed_cost, double *final_cost, int32_t *iters,
                        int32_t flags, void *stream);
+
+/*
+ * How Alg. 2 step 4 draws.  KMPAR_SAMPLE_BERNOULLI (the default): every x is
+ * drawn independently with p = min(1, l D^2(x)/phi).  KMPAR_SAMPLE_EXACT: the
+ * variant of Sec. 5.3 (Fig. 5.1), exactly L = floor(l) points per round without
+ * replacement, each successive draw proportional to D^2 among the points not
+ * drawn yet (D^2 as at the start of the round); fewer only when fewer than L
+ * points have D^2 > 0, and then all of those.  It is computed as the L smallest
+ * clocks -ln(u_x) / D^2(x) with u_x from counter (x, 0, round, 4), clocks in
+ * FP32 from the stored D^2, equal clocks to the lower x; a round whose L-th clock
+ * has another within (2d+16) 2^-24 (relative) of it adds one to sample_near.
+ * Call before round 1 (KMPAR_ERR_STATE otherwise).  KMPAR_ERR_ARG for an unknown
+ * mode, or l < 1 with KMPAR_SAMPLE_EXACT.  The exact mode allocates 4 n bytes.
+ */
+#define KMPAR_SAMPLE_BERNOULLI 0
+#define KMPAR_SAMPLE_EXACT 1
+KMPAR_API kmpar_status kmpar_set_sampling(kmpar_ctx *ctx, int32_t mode);
 
 /* Device pointers to the context's D^2 (n FP32) and idx (n int32) arrays, valid
  * until the next call on the context; either out pointer may be NULL. */

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkmpar.so")
-SOURCES = ["kmpar_api.cu", "round_simt.cu", "recluster_lloyd.cu", "cost_noalloc.cu", "nearest_tc.cu"]
+SOURCES = ["kmpar_api.cu", "round_simt.cu", "recluster_lloyd.cu", "cost_noalloc.cu", "nearest_tc.cu",
+           "exact_sample.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

@@ -106,7 +106,7 @@ void free_ctx(kmp::Ctx &c) {
                     c.labels[0], c.labels[1], c.perm, c.hist, c.base, c.cost_dev, c.tc_img,
                     c.tc_cmax, c.tc_err, c.cand1, c.fix_rows, c.fix_cnt, c.dmin, c.tc_ximg, c.tc_xnorm,
                     c.piece, c.psum, c.rc_cmass, c.rc_sync, c.rc_err, c.chunk, c.tc_v2,
-                    c.tc_anchor, c.tc_anchor_part, c.lloyd_rec};
+                    c.tc_anchor, c.tc_anchor_part, c.lloyd_rec, c.ex_keys, c.ex_ws, c.ex_ties};
     // stream-ordered: the memory returns to the pool once the context's work is done
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, c.stream);
@@ -299,6 +299,29 @@ kmpar_status kmpar_round(kmpar_ctx *ctx, int32_t i, int64_t *n_added, double *ph
         if (n_added) *n_added = st.round_added[i - 1];
         if (phi) *phi = st.phi;
     }
+    return KMPAR_OK;
+}
+
+kmpar_status kmpar_set_sampling(kmpar_ctx *ctx, int32_t mode) {
+    if (!ctx) return fail(nullptr, KMPAR_ERR_ARG, "ctx is NULL");
+    kmp::Ctx &c = ctx->c;
+    if (c.rounds_done > 0) return fail(&c, KMPAR_ERR_STATE, "sampling is set before round 1");
+    if (mode != KMPAR_SAMPLE_BERNOULLI && mode != KMPAR_SAMPLE_EXACT)
+        return fail(&c, KMPAR_ERR_ARG, "unknown sampling mode");
+    if (mode == KMPAR_SAMPLE_EXACT && !(c.ell >= 1.0))
+        return fail(&c, KMPAR_ERR_ARG, "exactly-l rounds need l >= 1");
+    if (mode == KMPAR_SAMPLE_EXACT && !c.ex_keys) {
+        uint32_t *keys = nullptr;
+        unsigned char *ws = nullptr;
+        int32_t *ties = nullptr;
+        KMP_CUDA(&c, alloc(c, &keys, (size_t)c.n), "alloc clocks");
+        c.ex_keys = keys;
+        KMP_CUDA(&c, alloc(c, &ws, kmp::exact_work_bytes()), "alloc select state");
+        c.ex_ws = ws;
+        KMP_CUDA(&c, alloc(c, &ties, (size_t)kmp::exact_tie_cap()), "alloc tie list");
+        c.ex_ties = ties;
+    }
+    c.sampling = mode == KMPAR_SAMPLE_EXACT ? 1 : 0;
     return KMPAR_OK;
 }
 
@@ -539,6 +562,7 @@ kmpar_status kmpar_fit(const float *X, int64_t n, int32_t d, int32_t k, double e
     }
     kmpar_ctx *ctx = nullptr;
     kmpar_status st = kmpar_init(&ctx, Xd, n, d, k, ell, rounds, seed, precision, stream);
+    if (st == KMPAR_OK && (flags & KMPAR_EXACT_SAMPLING)) st = kmpar_set_sampling(ctx, KMPAR_SAMPLE_EXACT);
     for (int i = 1; st == KMPAR_OK && i <= rounds; ++i) st = kmpar_round(ctx, i, nullptr, nullptr);
     if (st == KMPAR_OK) st = kmpar_weight(ctx, nullptr, nullptr, nullptr);
     kmpar_status warn = KMPAR_OK;

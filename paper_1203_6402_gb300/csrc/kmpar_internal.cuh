@@ -93,6 +93,11 @@ struct Ctx {
     int32_t *fix_rows = nullptr;  // rows left to the exact CUDA-core pass
     int *fix_cnt = nullptr;
     float *dmin = nullptr;        // Lloyd: exact d^2 of each point's chosen center
+    // exactly-l rounds (Sec. 5.3): 0 = independent draws, 1 = floor(l) per round
+    int sampling = 0;
+    uint32_t *ex_keys = nullptr;  // per point: FP32 clock bits
+    void *ex_ws = nullptr;        // radix-select state
+    int32_t *ex_ties = nullptr;   // points whose clock equals the last drawn one
     // CUDA-event timing of the distance passes (0 = rounds, 1 = Lloyd assign)
     bool timing = false;
     struct Pending { cudaEvent_t a, b; int cls; };
@@ -106,6 +111,11 @@ struct Ctx {
 // process-wide count of kernel launches made by this library
 extern std::atomic<long long> g_launches;
 inline void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// exactly-l rounds (exact_sample.cu)
+size_t exact_work_bytes();
+int exact_tie_cap();
+cudaError_t launch_sample_exact(Ctx &c, int round);
 
 // timing helpers (no-ops unless c.timing)
 cudaError_t timing_begin(Ctx &c, cudaEvent_t *a);

@@ -363,10 +363,15 @@ cudaError_t launch_phi_finalize(Ctx &c, int nparts, double *out, double *hist_sl
 
 cudaError_t launch_round(Ctx &c, int round) {
     cudaError_t e;
-    const int sgrid = c.num_sms * 8;
-    sample_kernel<<<sgrid, 256, 0, c.stream>>>(c.D2, c.idx, c.X, c.C, c.n, c.d, c.ell, (uint32_t)round,
-                                               c.seed, c.st, c.drawn, c.cap_round);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (c.sampling == 1) {
+        if ((e = launch_sample_exact(c, round)) != cudaSuccess) return e;
+    } else {
+        const int sgrid = c.num_sms * 8;
+        sample_kernel<<<sgrid, 256, 0, c.stream>>>(c.D2, c.idx, c.X, c.C, c.n, c.d, c.ell, (uint32_t)round,
+                                                   c.seed, c.st, c.drawn, c.cap_round);
+        count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     int P = 1;
     while (P < c.cap_round) P <<= 1;
     sort_batch_kernel<<<1, 1024, P * sizeof(int32_t), c.stream>>>(c.drawn, c.cap_round, round, c.st, c.cand);
@@ -375,7 +380,7 @@ cudaError_t launch_round(Ctx &c, int round) {
     const int ggrid = (int)std::min<int64_t>((gtot + 255) / 256, (int64_t)c.num_sms * 16);
     gather_kernel<<<ggrid, 256, 0, c.stream>>>(c.X, c.d, c.st, c.cand, c.C);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    count_launches(3);
+    count_launches(2);
     return launch_round_distance(c, round);
 }
 

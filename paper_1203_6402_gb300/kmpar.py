@@ -17,12 +17,15 @@ LIB_PATH = os.path.join(_HERE, "_build", "libkmpar.so")
 KMPAR_OK, KMPAR_ERR_ARG, KMPAR_ERR_CUDA, KMPAR_ERR_OOM, KMPAR_ERR_CAPACITY = 0, 1, 2, 3, 4
 KMPAR_ERR_TIMEOUT, KMPAR_ERR_STATE, KMPAR_WARN_FEW_CANDIDATES, KMPAR_ERR_UNSUPPORTED = 5, 6, 7, 8
 KMPAR_FP32, KMPAR_BF16, KMPAR_BF16X3 = 0, 1, 2
-KMPAR_HOST_BUFFERS = 1
+KMPAR_HOST_BUFFERS, KMPAR_EXACT_SAMPLING = 1, 2
+KMPAR_SAMPLE_BERNOULLI, KMPAR_SAMPLE_EXACT = 0, 1
+SAMPLINGS = {"bernoulli": KMPAR_SAMPLE_BERNOULLI, "exact": KMPAR_SAMPLE_EXACT}
 PRECISIONS = {"fp32": KMPAR_FP32, "bf16": KMPAR_BF16, "bf16x3": KMPAR_BF16X3}
 
 EXPORTED = ["kmpar_init", "kmpar_round", "kmpar_weight", "kmpar_recluster", "kmpar_lloyd", "kmpar_cost",
             "kmpar_fit", "kmpar_state", "kmpar_get_stats", "kmpar_uniforms", "kmpar_set_timing",
             "kmpar_launch_count", "kmpar_cost_noalloc", "kmpar_destroy", "kmpar_release_cached_memory",
+            "kmpar_set_sampling",
             "kmpar_status_string", "kmpar_last_error"]
 
 
@@ -83,6 +86,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kmpar_get_stats": (i32, [P, ctypes.POINTER(kmpar_stats)]),
         "kmpar_uniforms": (i32, [i64, u32, u32, u64, P, P]),
         "kmpar_set_timing": (i32, [P, i32]),
+        "kmpar_set_sampling": (i32, [P, i32]),
         "kmpar_launch_count": (i64, []),
         "kmpar_cost_noalloc": (i32, [P, i64, i32, P, i32, ctypes.POINTER(f64), P]),
         "kmpar_destroy": (None, [P]),
@@ -181,6 +185,10 @@ def kmpar_set_timing(ctx: int, enable: bool) -> None:
     _check(load().kmpar_set_timing(ctx, 1 if enable else 0), ctx)
 
 
+def kmpar_set_sampling(ctx: int, mode: int) -> None:
+    _check(load().kmpar_set_sampling(ctx, mode), ctx)
+
+
 def kmpar_launch_count() -> int:
     return load().kmpar_launch_count()
 
@@ -198,7 +206,7 @@ class KMeansPar:
     """A k-means|| context over a CUDA float32 tensor X (n x d), borrowed."""
 
     def __init__(self, X, k: int, ell: float, rounds: int, seed: int, precision: str | int = "fp32",
-                 stream=None):
+                 stream=None, sampling: str | int = "bernoulli"):
         import torch
         if not (X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.is_contiguous()):
             raise ValueError("X must be a contiguous CUDA float32 n x d tensor")
@@ -209,6 +217,14 @@ class KMeansPar:
         self.ctx = kmpar_init(X.data_ptr(), self.n, self.d, k, ell, rounds, seed, self.precision,
                               self.stream.cuda_stream)
         self.rounds = rounds
+        mode = SAMPLINGS[sampling] if isinstance(sampling, str) else sampling
+        if mode != KMPAR_SAMPLE_BERNOULLI:
+            try:
+                kmpar_set_sampling(self.ctx, mode)
+            except KmparError:
+                kmpar_destroy(self.ctx)
+                self.ctx = None
+                raise
 
     def round(self, i: int, sync: bool = False):
         return kmpar_round(self.ctx, i, sync)

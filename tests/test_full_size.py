@@ -195,3 +195,44 @@ def test_large_k_wide_rows(km):
     # so the two nearest are often near ties; every row is decided exactly all the same
     # screened rows: 5 round passes and 4 Lloyd assignments (updates 0..3)
     assert stats["screen_rows"] == (5 + 4) * n and 0 < stats["screen_fallback"] < stats["screen_rows"]
+
+
+def test_full_size_exact_rounds(km):
+    """Exactly-l rounds (Sec. 5.3) at 1e6 x 42, l = 1000: every round adds exactly
+    1000 points never drawn before, phi = sum D^2, sum w = n; round 1 draws what
+    the oracle draws from its own FP64 D^2 (no boundary near-tie); the split-BF16
+    path takes the FP32 path's draws, D^2 and idx."""
+    from oracle import oracle as orc
+    name = "kdd_n1M_d42_k500"
+    w = datagen.WORKLOADS[name]
+    X = datagen.make(name, seed=1000)
+    n, d = X.shape
+    L = int(w["ell"])
+    Xd = torch.from_numpy(X).cuda()
+    res = {}
+    for prec in ("fp32", "bf16x3"):
+        g = km.KMeansPar(Xd, w["k"], w["ell"], w["rounds"], 7, precision=prec, sampling="exact")
+        rounds = []
+        for r in range(1, w["rounds"] + 1):
+            na, phi = g.round(r, sync=True)
+            D2, _ = g.state()
+            rounds.append((na, phi, float(D2.double().sum())))
+        cand, wt = g.candidates()
+        D2, idx = g.state()
+        res[prec] = (cand.cpu().numpy(), wt.cpu().numpy(), D2.cpu().numpy(), idx.cpu().numpy(), rounds)
+        g.close()
+    cand, wt, D2, idx, rounds = res["fp32"]
+    assert [r[0] for r in rounds] == [L] * w["rounds"]
+    for _, phi, ref in rounds:
+        assert math.isclose(phi, ref, rel_tol=1e-9), (phi, ref)
+    assert len(cand) == 1 + L * w["rounds"] and len(np.unique(cand)) == len(cand)
+    assert wt.sum() == n and np.array_equal(wt, np.bincount(idx, minlength=len(cand)))
+    for a, b in zip(res["fp32"][:4], res["bf16x3"][:4]):
+        assert np.array_equal(a, b)
+    # round 1 against the oracle: its own first center, FP64 D^2 and clocks
+    i0 = orc.init_index(n, 7)
+    assert cand[0] == i0
+    D2o, _, _ = orc.init(X, i0)
+    sel, near = orc.sample_exact(D2o, w["ell"], 1, 7, (2 * d + 16) * 2.0 ** -24)
+    if not near:
+        assert np.array_equal(cand[1:1 + L], sel)

@@ -39,15 +39,17 @@ def _close_d2(gpu, ref):
     return np.abs(gpu - ref) <= D2_RTOL * np.abs(ref) + 1e-30
 
 
-def run_and_compare(km, orc, X, k, ell, rounds, seed, precision="fp32", max_iter=100):
+def run_and_compare(km, orc, X, k, ell, rounds, seed, precision="fp32", max_iter=100, sampling="bernoulli"):
     """Runs the GPU path step by step and the oracle beside it; asserts the bar.
 
     Returns a dict of diagnostics.  If the trajectories part at a reported near
     tie, the remaining steps are checked for validity only (diag['parted'])."""
     n, d = X.shape
     Xd = _dev(X)
-    g = km.KMeansPar(Xd, k, ell, rounds, seed, precision=precision)
-    diag = dict(parted=None)
+    g = km.KMeansPar(Xd, k, ell, rounds, seed, precision=precision, sampling=sampling)
+    diag = dict(parted=None, boundary_near=[])
+    # exactly-l rounds: the relative window in which FP32 and exact clocks may swap
+    wwin = (2 * d + 16) * 2.0 ** -24
     # Alg. 2 steps 1-2
     i0 = orc.init_index(n, seed)
     D2, idx, psi = orc.init(X, i0)
@@ -57,7 +59,11 @@ def run_and_compare(km, orc, X, k, ell, rounds, seed, precision="fp32", max_iter
     cand = [i0]
     phi = psi
     for r in range(1, rounds + 1):
-        sel, p, nsamp = orc.sample(D2, phi, ell, r, seed)
+        if sampling == "exact":
+            sel, bnear = orc.sample_exact(D2, ell, r, seed, wwin)
+            diag["boundary_near"].append(bnear)
+        else:
+            sel, p, nsamp = orc.sample(D2, phi, ell, r, seed)
         phi, narg = orc.update(X, sel, len(cand), D2, idx)
         na, gphi = g.round(r, sync=True)
         cand.extend(int(s) for s in sel)
@@ -170,6 +176,45 @@ def test_parity_tensor_screening(km, orc, name, mk, k, ell, rounds, seed, precis
     if precision == "bf16x3" and name.startswith("gmm"):
         # well-separated data: nearly every row is decided by the screening alone
         assert st["screen_fallback"] <= 0.05 * st["screen_rows"], st
+
+
+EXACT_CASES = [
+    # name, X maker, k, ell, rounds, seed, precision
+    ("gmm_small", lambda: datagen.gauss_mixture(3000, 15, 20, 10.0, seed=1), 20, 40.0, 5, 3, "fp32"),
+    ("kdd_like", lambda: datagen.kdd_like(2500, seed=2), 30, 60.0, 5, 4, "bf16x3"),
+    ("kdd_sliced_batches", lambda: datagen.kdd_like(6000, seed=16), 100, 1500.0, 2, 11, "bf16x3"),
+    # 30 drawn, then the 9 points left with D^2 > 0, then none
+    ("tiny_all_drawn", lambda: datagen.uniform_box(40, 3, seed=21), 5, 30.0, 3, 6, "fp32"),
+]
+
+
+@pytest.mark.parametrize("name,mk,k,ell,rounds,seed,precision", EXACT_CASES, ids=[c[0] for c in EXACT_CASES])
+def test_parity_exact_rounds(km, orc, name, mk, k, ell, rounds, seed, precision):
+    """Exactly-l rounds (Sec. 5.3): floor(l) draws per round without replacement,
+    proportional to D^2 -- the same draws as the oracle's exponential clocks, then
+    the same union, weights, recluster and Lloyd."""
+    X = mk()
+    diag = run_and_compare(km, orc, X, k, ell, rounds, seed, precision=precision, sampling="exact")
+    assert not any(diag["boundary_near"]), diag["boundary_near"]
+    assert diag["parted"] is None, diag   # so every round drew what the oracle drew
+
+
+def test_exact_sampling_arguments(km):
+    X = _dev(datagen.uniform_box(100, 2, seed=1))
+    g = km.KMeansPar(X, 3, 5.0, 2, 1)
+    g.round(1)
+    with pytest.raises(km.KmparError) as e:
+        km.kmpar_set_sampling(g.ctx, km.KMPAR_SAMPLE_EXACT)
+    assert e.value.status == km.KMPAR_ERR_STATE
+    g.close()
+    with pytest.raises(km.KmparError) as e:
+        km.KMeansPar(X, 3, 0.5, 2, 1, sampling="exact")
+    assert e.value.status == km.KMPAR_ERR_ARG
+    g = km.KMeansPar(X, 3, 5.0, 2, 1)
+    with pytest.raises(km.KmparError) as e:
+        km.kmpar_set_sampling(g.ctx, 7)
+    assert e.value.status == km.KMPAR_ERR_ARG
+    g.close()
 
 
 def test_tensor_paths_match_fp32_path(km):

@@ -30,7 +30,7 @@
  * counter = (i_lo, i_hi, round, tag); tag 1 = first center, 2 = round draws,
  * 3 = reclustering draws, 4 = exactly-l round clocks; a uniform double is (a 2^26 + b) / 2^53 with
  * a = word0 >> 5, b = word1 >> 6.  Results are a pure function of
- * (X, k, l, rounds, seed, precision).
+ * (X, k, l, rounds, seed, precision, sampling mode).
  *
  * Ties: an argmin goes to the lowest center number; candidates are numbered in
  * insertion order (initial center 0, then each round's draws in ascending point

@@ -31,6 +31,9 @@
  *   - Lloyd stops when no label changes; an empty cluster keeps its center.
  *   - if the reclustering runs out of positive mass (total w*D^2 = 0), the
  *     remaining centers repeat the first chosen one and a warning flag is set.
+ *   - "exactly l points per round" (Sec. 5.3) is floor(l) successive draws
+ *     without replacement, each proportional to D^2 among the points not drawn
+ *     yet, with D^2 held at its value at the start of the round.
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel Random
  * Numbers: As Easy as 1, 2, 3", SC'11), implemented here from its published

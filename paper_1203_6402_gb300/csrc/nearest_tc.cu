@@ -289,8 +289,10 @@ __global__ void __launch_bounds__(128) prep_points_kernel(const float *__restric
 // same decisions (distances do not depend on it); the mean keeps ||x'|| small.
 // kAnchorBlocks fixed row chunks; in a block, thread (ty, tx) sums column
 // cc + tx over the chunk's rows ty, ty + 4, ... (warps read 32 consecutive
-// floats of a row); the four row phases, then the chunks, are added in a fixed
-// order, so the result is deterministic.
+// floats of a row) in four FP32 chains of at most ~31 rows each (FP64 adds run
+// at a small fraction of the FP32 rate here, and the anchor needs no more than
+// FP32 accuracy); the chains, the four row phases, then the chunks, are added in
+// FP64 in a fixed order, so the result is deterministic.
 constexpr int kAnchorBlocks = 1024;
 
 __global__ void __launch_bounds__(256) anchor_partial_kernel(const float *__restrict__ X, int64_t n, int d,
@@ -302,16 +304,18 @@ __global__ void __launch_bounds__(256) anchor_partial_kernel(const float *__rest
     const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
     for (int cc = 0; cc < d; cc += 64) {
         const int q = cc + tx;
-        double s0 = 0.0, s1 = 0.0;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
         if (q < d) {
             int64_t r = r0 + ty;
-            for (; r + 4 < r1; r += 8) {
-                s0 += (double)__ldg(X + r * d + q);
-                s1 += (double)__ldg(X + (r + 4) * d + q);
+            for (; r + 12 < r1; r += 16) {
+                s0 += __ldg(X + r * d + q);
+                s1 += __ldg(X + (r + 4) * d + q);
+                s2 += __ldg(X + (r + 8) * d + q);
+                s3 += __ldg(X + (r + 12) * d + q);
             }
-            if (r < r1) s0 += (double)__ldg(X + r * d + q);
+            for (; r < r1; r += 4) s0 += __ldg(X + r * d + q);
         }
-        ph[ty][tx] = s0 + s1;
+        ph[ty][tx] = (((double)s0 + (double)s1) + (double)s2) + (double)s3;
         __syncthreads();
         if (ty == 0 && q < d) part[(size_t)blockIdx.x * d + q] = ((ph[0][tx] + ph[1][tx]) + ph[2][tx]) + ph[3][tx];
         __syncthreads();

@@ -454,14 +454,29 @@ __global__ void __launch_bounds__(256) sum_rows_kernel(const float *__restrict__
     const int64_t b0 = (int64_t)blockIdx.x * per_block;
     const int64_t b1 = min(n, b0 + per_block);
     double acc = 0.0;
-    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) acc += (double)v[i];
+    if ((per_block & 3) == 0 && (reinterpret_cast<uintptr_t>(v) & 15u) == 0) {
+        // four consecutive values per thread and step, added in index order
+        for (int64_t i = b0 + 4 * threadIdx.x; i < b1; i += 4 * blockDim.x) {
+            if (i + 4 <= b1) {
+                const float4 q = __ldg(reinterpret_cast<const float4 *>(v + i));
+                acc += (double)q.x;
+                acc += (double)q.y;
+                acc += (double)q.z;
+                acc += (double)q.w;
+            } else {
+                for (int64_t j = i; j < b1; ++j) acc += (double)v[j];
+            }
+        }
+    } else {
+        for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) acc += (double)v[i];
+    }
     const double s = block_sum_f64(acc, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
 cudaError_t launch_sum_rows(const float *v, int64_t n, double *partials, int max_parts, double *out, double *copy,
                             cudaStream_t s) {
-    int64_t per = 4096;
+    int64_t per = 1024;
     int64_t nb = (n + per - 1) / per;
     if (nb > max_parts) {
         per = (n + max_parts - 1) / max_parts;

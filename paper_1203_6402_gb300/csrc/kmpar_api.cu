@@ -310,16 +310,15 @@ kmpar_status kmpar_set_sampling(kmpar_ctx *ctx, int32_t mode) {
         return fail(&c, KMPAR_ERR_ARG, "unknown sampling mode");
     if (mode == KMPAR_SAMPLE_EXACT && !(c.ell >= 1.0))
         return fail(&c, KMPAR_ERR_ARG, "exactly-l rounds need l >= 1");
-    if (mode == KMPAR_SAMPLE_EXACT && !c.ex_keys) {
-        uint32_t *keys = nullptr;
-        unsigned char *ws = nullptr;
-        int32_t *ties = nullptr;
-        KMP_CUDA(&c, alloc(c, &keys, (size_t)c.n), "alloc clocks");
-        c.ex_keys = keys;
-        KMP_CUDA(&c, alloc(c, &ws, kmp::exact_work_bytes()), "alloc select state");
-        c.ex_ws = ws;
-        KMP_CUDA(&c, alloc(c, &ties, (size_t)kmp::exact_tie_cap()), "alloc tie list");
-        c.ex_ties = ties;
+    if (mode == KMPAR_SAMPLE_EXACT) {
+        // each buffer once; after a failed call the next one allocates what is missing
+        if (!c.ex_keys) KMP_CUDA(&c, alloc(c, &c.ex_keys, (size_t)c.n), "alloc clocks");
+        if (!c.ex_ws) {
+            unsigned char *ws = nullptr;
+            KMP_CUDA(&c, alloc(c, &ws, kmp::exact_work_bytes()), "alloc select state");
+            c.ex_ws = ws;
+        }
+        if (!c.ex_ties) KMP_CUDA(&c, alloc(c, &c.ex_ties, (size_t)kmp::exact_tie_cap()), "alloc tie list");
     }
     c.sampling = mode == KMPAR_SAMPLE_EXACT ? 1 : 0;
     return KMPAR_OK;
@@ -360,21 +359,26 @@ kmpar_status kmpar_recluster(kmpar_ctx *ctx, float *centers_dev) {
     return warn ? KMPAR_WARN_FEW_CANDIDATES : KMPAR_OK;
 }
 
+// Each buffer is allocated once.  A call that failed part way (out of memory)
+// leaves the buffers it got in place; the next call allocates the missing ones, and
+// Lloyd runs only once all of them exist.
 static kmpar_status ensure_lloyd_buffers(kmp::Ctx &c) {
-    if (c.labels[0]) return KMPAR_OK;
+    if (c.lloyd_ready) return KMPAR_OK;
     cudaError_t e;
-    if ((e = alloc(c, &c.labels[0], c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc labels");
-    if ((e = alloc(c, &c.labels[1], c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc labels");
-    if ((e = alloc(c, &c.perm, c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc perm");
-    if ((e = alloc(c, &c.hist, (size_t)c.nsb * c.k)) != cudaSuccess) return cuda_fail(&c, e, "alloc hist");
-    if ((e = alloc(c, &c.base, (size_t)c.k + 1)) != cudaSuccess) return cuda_fail(&c, e, "alloc base");
-    if ((e = alloc(c, &c.piece, (size_t)c.k + 1)) != cudaSuccess) return cuda_fail(&c, e, "alloc pieces");
-    if ((e = alloc(c, &c.chunk, (size_t)kmp::scan_chunks(c.nsb) * c.k)) != cudaSuccess)
-        return cuda_fail(&c, e, "alloc scan chunks");
-    if ((e = alloc(c, &c.psum, (size_t)kmp::max_pieces(c.n, c.k) * c.d)) != cudaSuccess)
-        return cuda_fail(&c, e, "alloc piece sums");
-    if ((e = alloc(c, &c.cost_dev, 4)) != cudaSuccess) return cuda_fail(&c, e, "alloc cost");
-    if (c.precision != KMPAR_FP32 && (e = alloc(c, &c.dmin, c.n)) != cudaSuccess) return cuda_fail(&c, e, "alloc dmin");
+#define KMP_ENSURE(ptr, count, what) \
+    if (!(ptr) && (e = alloc(c, &(ptr), (count))) != cudaSuccess) return cuda_fail(&c, e, what)
+    KMP_ENSURE(c.labels[0], (size_t)c.n, "alloc labels");
+    KMP_ENSURE(c.labels[1], (size_t)c.n, "alloc labels");
+    KMP_ENSURE(c.perm, (size_t)c.n, "alloc perm");
+    KMP_ENSURE(c.hist, (size_t)c.nsb * c.k, "alloc hist");
+    KMP_ENSURE(c.base, (size_t)c.k + 1, "alloc base");
+    KMP_ENSURE(c.piece, (size_t)c.k + 1, "alloc pieces");
+    KMP_ENSURE(c.chunk, (size_t)kmp::scan_chunks(c.nsb) * c.k, "alloc scan chunks");
+    KMP_ENSURE(c.psum, (size_t)kmp::max_pieces(c.n, c.k) * c.d, "alloc piece sums");
+    KMP_ENSURE(c.cost_dev, 4, "alloc cost");
+    if (c.precision != KMPAR_FP32) KMP_ENSURE(c.dmin, (size_t)c.n, "alloc dmin");
+#undef KMP_ENSURE
+    c.lloyd_ready = true;
     return KMPAR_OK;
 }
 

@@ -77,6 +77,7 @@ struct Ctx {
     int32_t *chunk = nullptr;     // column-scan chunk totals
     double *psum = nullptr;       // FP64 piece sums
     int nsb = 0, sort_block = 0;
+    bool lloyd_ready = false;     // every Lloyd buffer below is allocated
     void *lloyd_rec = nullptr;    // per Lloyd iteration: (cost, labels changed), 16 bytes
     int lloyd_rec_cap = 0;
     double *cost_dev = nullptr;   // one FP64

@@ -476,7 +476,6 @@ kmpar_status kmpar_lloyd(kmpar_ctx *ctx, float *centers_dev, int32_t max_iter, i
 kmpar_status kmpar_cost(const float *X, int64_t n, int32_t d, const float *C, int32_t k, int32_t precision,
                         double *phi, void *stream) {
     // every precision yields the same exact-FP32 cost; the CUDA-core pass computes it
-
     if (!X || !C || !phi) return fail(nullptr, KMPAR_ERR_ARG, "NULL pointer");
     if (n < 1 || n >= (int64_t)INT32_MAX || d < 1 || d > 4096 || k < 1)
         return fail(nullptr, KMPAR_ERR_ARG, "size out of range");
@@ -552,17 +551,27 @@ kmpar_status kmpar_fit(const float *X, int64_t n, int32_t d, int32_t k, double e
     cudaStream_t s = (cudaStream_t)stream;
     const bool host = (flags & KMPAR_HOST_BUFFERS) != 0;
     const float *Xd = X;
-    float *Xbuf = nullptr, *Cd = centers_out;
+    float *Cd = centers_out;
     int32_t *Ld = labels_out;
+    float *Xbuf = nullptr, *Cbuf = nullptr;   // device staging of the host buffers
+    int32_t *Lbuf = nullptr;
     cudaError_t e = cudaSuccess;
     if (host) {
         e = cudaMallocAsync(reinterpret_cast<void **>(&Xbuf), sizeof(float) * (size_t)n * d, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(Xbuf, X, sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&Cd), sizeof(float) * (size_t)k * d, s);
+        if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&Cbuf), sizeof(float) * (size_t)k * d, s);
         if (e == cudaSuccess && labels_out)
-            e = cudaMallocAsync(reinterpret_cast<void **>(&Ld), sizeof(int32_t) * (size_t)n, s);
-        if (e != cudaSuccess) return cuda_fail(nullptr, e, "fit staging");
+            e = cudaMallocAsync(reinterpret_cast<void **>(&Lbuf), sizeof(int32_t) * (size_t)n, s);
+        if (e != cudaSuccess) {
+            // hand back what the staging got before the failure
+            if (Xbuf) cudaFreeAsync(Xbuf, s);
+            if (Cbuf) cudaFreeAsync(Cbuf, s);
+            if (Lbuf) cudaFreeAsync(Lbuf, s);
+            return cuda_fail(nullptr, e, "fit staging");
+        }
         Xd = Xbuf;
+        Cd = Cbuf;
+        Ld = Lbuf;
     }
     kmpar_ctx *ctx = nullptr;
     kmpar_status st = kmpar_init(&ctx, Xd, n, d, k, ell, rounds, seed, precision, stream);
@@ -587,8 +596,8 @@ kmpar_status kmpar_fit(const float *X, int64_t n, int32_t d, int32_t k, double e
                 e = cudaMemcpyAsync(labels_out, Ld, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s);
         }
         cudaFreeAsync(Xbuf, s);
-        cudaFreeAsync(Cd, s);
-        if (Ld) cudaFreeAsync(Ld, s);
+        cudaFreeAsync(Cbuf, s);
+        if (Lbuf) cudaFreeAsync(Lbuf, s);
         cudaError_t e2 = cudaStreamSynchronize(s);
         if (e == cudaSuccess) e = e2;
         if (st == KMPAR_OK && e != cudaSuccess) return cuda_fail(nullptr, e, "fit copy-out");

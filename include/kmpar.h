@@ -5,14 +5,14 @@
  * (arXiv:1203.6402).  The library runs the data-parallel path of Algorithm 2
  * (Sec. 3.3) on one GPU:
  *
- *   kmpar_init       Alg. 2 steps 1-2  first center uniform over X; psi = phi_X(C)
- *   kmpar_round      Alg. 2 steps 4-5  draw each x with p = min(1, l D^2(x)/phi),
- *                                       C <- C u C', update D^2 and phi
- *   kmpar_set_sampling  Sec. 5.3       or draw exactly floor(l) points per round
- *   kmpar_weight     Alg. 2 step 7     w_c = #points nearest to candidate c
- *   kmpar_recluster  Alg. 2 step 8     weighted k-means++ (Alg. 1, Sec. 4.2) to k
- *   kmpar_lloyd      Sec. 1, Sec. 3.1  Lloyd's iteration to a stable assignment
- *   kmpar_cost       Sec. 3.1          phi_X(C) = sum_x min_i ||x - c_i||^2
+ *   kmpar_init          Alg. 2 steps 1-2  first center uniform over X; psi = phi_X(C)
+ *   kmpar_round         Alg. 2 steps 4-5  draw each x with p = min(1, l D^2(x)/phi),
+ *                                          C <- C u C', update D^2 and phi
+ *   kmpar_set_sampling  Sec. 5.3          or draw exactly floor(l) points per round
+ *   kmpar_weight        Alg. 2 step 7     w_c = #points nearest to candidate c
+ *   kmpar_recluster     Alg. 2 step 8     weighted k-means++ (Alg. 1, Sec. 4.2) to k
+ *   kmpar_lloyd         Sec. 1, Sec. 3.1  Lloyd's iteration to a stable assignment
+ *   kmpar_cost          Sec. 3.1          phi_X(C) = sum_x min_i ||x - c_i||^2
  *
  * Conventions (all entry points):
  *   - X is row-major FP32, n rows of d coordinates (row stride d floats), in

@@ -101,6 +101,12 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
+        return self.parse(out)
+
+    @staticmethod
+    def parse(out: str):
+        """Median SM clock, maximum clock and the throttle reasons seen in the CSV
+        lines of ``nvidia-smi --query-gpu=FIELDS --format=csv,noheader,nounits``."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():

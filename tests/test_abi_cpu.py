@@ -77,3 +77,23 @@ def test_product_never_imports_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", src, re.M), f
                 assert "kmpar_oracle" not in src and "liboracle" not in src, f
+
+
+def header_constants():
+    """KMPAR_* values from the header: enum members and #define'd integers."""
+    hdr = open(os.path.join(ROOT, "include", "kmpar.h")).read()
+    vals = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(KMPAR_[A-Z0-9_]+)\s*=\s*(\d+)", hdr)}
+    vals.update({m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(KMPAR_[A-Z0-9_]+)\s+(\d+)\b", hdr)})
+    return vals
+
+
+def test_binding_constants_match_the_header():
+    from paper_1203_6402_gb300 import kmpar
+    consts = header_constants()
+    assert len(consts) >= 15
+    for name, value in consts.items():
+        assert getattr(kmpar, name) == value, name
+    assert kmpar.PRECISIONS == {"fp32": consts["KMPAR_FP32"], "bf16": consts["KMPAR_BF16"],
+                                "bf16x3": consts["KMPAR_BF16X3"]}
+    assert kmpar.SAMPLINGS == {"bernoulli": consts["KMPAR_SAMPLE_BERNOULLI"],
+                               "exact": consts["KMPAR_SAMPLE_EXACT"]}

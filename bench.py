@@ -38,8 +38,8 @@ ALU_LANES_PER_SM = 64          # integer/min-max/logic pipe: half the FP32 lane 
 # = 2.25 ALU ops per distance
 SCREEN_ALU_OPS = 2.25
 # DRAM bytes (read + write) per launch of the tensor assignment pass, from an ncu capture of the
-# same kernel on this workload (profiles/nearest_tc_assign_bf16x3_kdd_n1M.md); to be set to None
-# whenever the kernel changes until it is captured again
+# same kernel on this workload; to be set to None whenever the kernel changes until it is
+# captured again
 TC_ASSIGN_TRAFFIC = {"bf16x3": 256.201e6 + 8.731e6}
 
 

@@ -183,7 +183,7 @@ KMPAR_API kmpar_status kmpar_cost(const float *X, int64_t n, int32_t d, const fl
  * they need it: for instance a host framework that has reserved all of the GPU's
  * memory for its own pool, or a latency-critical loop in which an allocation,
  * which can synchronise the device, is not allowed.  The paper has no
- * counterpart; this is a packaging variant of the Sec. 3.1 cost.
+ * counterpart.
  *
  * No allocation: the per-block FP64 partial sums live in a fixed array inside the
  * library (65,539 doubles, about 512 KB, held on every GPU that loads the library
@@ -191,11 +191,14 @@ KMPAR_API kmpar_status kmpar_cost(const float *X, int64_t n, int32_t d, const fl
  * (host).  n is limited to 8,388,608 points (65,536 blocks of 128); larger n
  * returns KMPAR_ERR_ARG with a message in kmpar_last_error(NULL).
  *
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call shares the one array, which keeps the last call's
- * contents: calls whose work overlaps on the GPU (other streams, other host
- * threads) race on it and must be serialised by the caller.  Synchronises.
+ * Every call looks up the array's device address in the current context with
+ * cudaGetSymbolAddress (which allocates nothing), so the address is never stale
+ * after a device reset or a context switch.  The first call in a process may
+ * load the library's device code: make it before any stream capture.  Every
+ * call shares the one array,
+ * which keeps the last call's contents: calls whose work overlaps on the GPU
+ * (other streams, other host threads) race on it and must be serialised by the
+ * caller.  Synchronises.
  */
 KMPAR_API kmpar_status kmpar_cost_noalloc(const float *X, int64_t n, int32_t d, const float *C, int32_t k,
                                           double *phi, void *stream);

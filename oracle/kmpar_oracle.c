@@ -22,7 +22,7 @@
  * -ffp-contract=off so that "s = s + t*t" is a rounded multiply followed by a
  * rounded add, exactly as written.
  *
- * Readings where the paper is silent (also listed in the design notes):
+ * Readings where the paper is silent:
  *   - p_x is capped at 1 (p = min(1, l*D^2/phi)); p = 0 when phi = 0.
  *   - ties in an argmin go to the lowest center index; candidates are numbered in
  *     insertion order (initial center 0, then each round's sample in ascending

@@ -3,12 +3,11 @@
 // The per-block FP64 partial sums, the final sum and a statistics counter live in
 // one file-scope device array (kNoAllocScratchDoubles doubles, 512 KB + 24 B),
 // which every GPU that loads the library holds until the process exits.  Host
-// code cannot use the array's name as a device address, so the address is looked
-// up once per device with cudaGetSymbolAddress (with that device current) and
-// cached.  All calls share the array: calls whose kernels overlap on the GPU race
-// on it.
-#include <mutex>
-
+// code cannot use the array's name as a device address, so every call looks the
+// address up with cudaGetSymbolAddress on the current device (the lookup
+// allocates nothing); nothing is cached, so a call after cudaDeviceReset, or
+// from another context, still gets the array of the context it runs in.  All
+// calls share the array: calls whose kernels overlap on the GPU race on it.
 #include "kmpar_internal.cuh"
 
 namespace kmp {
@@ -22,29 +21,18 @@ static __device__ __align__(256) double g_cost_scratch[kNoAllocScratchDoubles];
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double *g_scratch_ptr[kMaxDevices] = {};
-
 kmpar_status noalloc_fail(kmpar_status s, const std::string &m) {
     kmp::set_thread_error(m);
     return s;
 }
 
-// device address of g_cost_scratch on the current device (looked up once per device)
+// device address of g_cost_scratch in the current context, looked up on every
+// call (no cache that a device reset or a context switch could leave stale)
 cudaError_t scratch_address(double **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_cost_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_cost_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    *out = static_cast<double *>(p);
     return cudaSuccess;
 }
 

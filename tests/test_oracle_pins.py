@@ -425,7 +425,9 @@ def test_table1_gaussmixture_final_costs(orc):
 
     Reading: R is the standard deviation of the center distribution (variance
     R^2); only under that reading does the Random column come out near the
-    printed values.  The printed seed column is not pinned (see the design notes).
+    printed values.  The printed seed column is not pinned: it lies below what
+    weighted k-means++ on the candidates (Alg. 2 step 8, Sec. 4.2) gives under
+    either reading of R.
     """
     with open(os.path.join(GOLDEN, "table1_gaussmixture.json")) as f:
         t1 = json.load(f)

@@ -2,12 +2,17 @@
 
 A step is one pass of the whole path over one synthetic batch: init (Alg. 2
 steps 1-2), r rounds of draw + union/update (steps 4-5), weights (step 7),
-weighted k-means++ recluster (step 8), then Lloyd's iteration to a stable
-assignment (at most max_iter updates).  The default workload is the
-KDDCUP1999-shaped stand-in n = 1,000,000, d = 42, k = 500, l = 2k, r = 5.
+weighted k-means++ recluster (step 8), then Lloyd's iteration (until no label
+changes, at most the workload's cap of updates).  The default workload is the
+largest single-GPU configuration: a GAUSSMIXTURE of 10,000 components, n =
+10,000,000 points in d = 128 (centers ~ N(0, 100 I)), k = 10,000, l = 2k, r = 5,
+Lloyd capped at 10 updates.
 
 value = algorithmic distance evaluations per second over the whole job
-(init n, each round n |C'_i|, recluster k m, Lloyd n k per assignment).
+(init n, each round n |C'_i|, recluster k m, Lloyd n k per assignment).  The
+same line carries the plain FP32 CUDA-core path on the same data and seed
+(``fp32_arm``): its time per step, its final cost and the relative difference to
+this arm's final cost (the metric compares the two at equal cost).
 Multi-GPU runs are independent replicas (one per rank, weak scaling).
 
 --impl reference times the FP64 CPU oracle instead (rank 0 only), on a bounded
@@ -33,14 +38,6 @@ UNIT = "dist-evals/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
 SMS = 152
 FP32_LANES_PER_SM = 128
-ALU_LANES_PER_SM = 64          # integer/min-max/logic pipe: half the FP32 lane count
-# screening epilogue: per 8 distances 4 pair minima + 4 key builds + 10 top-2 min/max
-# = 2.25 ALU ops per distance
-SCREEN_ALU_OPS = 2.25
-# DRAM bytes (read + write) per launch of the tensor assignment pass, from an ncu capture of the
-# same kernel on this workload; to be set to None whenever the kernel changes until it is
-# captured again
-TC_ASSIGN_TRAFFIC = {"bf16x3": 256.201e6 + 8.731e6}
 
 
 def load_peaks():
@@ -63,6 +60,13 @@ def workload(args):
     if args.ell_factor:
         w["ell"] = args.ell_factor * w["k"]
     return w
+
+
+def default_precision(name: str) -> str:
+    """Split BF16 where its K = 3d + 2 fits the screening kernel (d <= 62), else plain BF16."""
+    from paper_1203_6402_gb300 import datagen
+    d = datagen.WORKLOADS[name]["d"]
+    return "bf16x3" if 3 * d + 2 <= 192 else "bf16"
 
 
 def count_dist_evals(n, k, stats, lloyd_iters):
@@ -128,6 +132,61 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ our arm
+def _phase_events(torch, stream, names):
+    ev = {nm: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for nm in names}
+    return ev
+
+
+def run_step(km, torch, X, k, ell, rounds, seed, prec, stream, sampling, max_iter, timing=False, phases=None):
+    """One pass of the whole path through the C ABI; returns (stats, lloyd output)."""
+    def mark(nm, i):
+        if phases is not None:
+            phases[nm][i].record(stream)
+    mark("init", 0)
+    g = km.KMeansPar(X, k, ell, rounds, seed=seed, precision=prec, stream=stream, sampling=sampling)
+    if timing:
+        km.kmpar_set_timing(g.ctx, True)
+    mark("init", 1)
+    mark("rounds", 0)
+    for i in range(1, rounds + 1):
+        g.round(i)
+    mark("rounds", 1)
+    mark("weight", 0)
+    g.weight()
+    mark("weight", 1)
+    mark("recluster", 0)
+    C, _ = g.recluster()
+    mark("recluster", 1)
+    mark("lloyd", 0)
+    out = g.lloyd(C, max_iter, labels=True)
+    mark("lloyd", 1)
+    st = g.stats()
+    g.close()
+    return st, out
+
+
+def traffic_record(kernel: str, workload: str, precision: str):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary, used only
+    while the kernel's source is the one that was captured (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    src = os.path.join(ROOT, "paper_1203_6402_gb300", "csrc", "nearest_tc.cu")
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None, None
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    with open(path) as f:
+        for line in f:
+            parts = [p.strip() for p in line.strip().strip("|").split("|")]
+            if len(parts) >= 5 and parts[0] == kernel and parts[1] == workload and parts[2] == precision:
+                try:
+                    val = float(parts[3])
+                except ValueError:
+                    continue
+                return (val, parts[4]) if parts[4] == sha else (None, parts[4])
+    return None, None
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_1203_6402_gb300 import datagen
@@ -145,25 +204,19 @@ def run_ours(args, rank, world):
     X = torch.from_numpy(Xh).to(dev)
     stream = torch.cuda.current_stream()
     prec = km.PRECISIONS[args.precision]
+    seed = 7 + rank
 
-    def step(timing=False):
-        g = km.KMeansPar(X, k, ell, rounds, seed=7 + rank, precision=prec, stream=stream, sampling=args.sampling)
-        if timing:
-            km.kmpar_set_timing(g.ctx, True)
-        for i in range(1, rounds + 1):
-            g.round(i)
-        g.weight()
-        C, _ = g.recluster()
-        out = g.lloyd(C, max_iter, labels=True)
-        st = g.stats()
-        g.close()
-        return st, out
+    def step(timing=False, phases=None, precision=prec):
+        return run_step(km, torch, X, k, ell, rounds, seed, precision, stream, args.sampling, max_iter, timing, phases)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    # one timed step with the kernel-level events, outside the job timer
-    st_t, out_t = step(timing=True)
+    # one timed step with the kernel-level and phase events, outside the job timer
+    phases = _phase_events(torch, stream, ["init", "rounds", "weight", "recluster", "lloyd"])
+    st_t, out_t = step(timing=True, phases=phases)
+    torch.cuda.synchronize()
+    phase_ms = {nm: a.elapsed_time(b) for nm, (a, b) in phases.items()}
     evals, parts = count_dist_evals(n, k, st_t, out_t["iters"])
 
     barrier(world)
@@ -176,7 +229,7 @@ def run_ours(args, rank, world):
     ev0.record(stream)
     total_evals = 0
     kern = {"round": [0.0, 0], "assign": [0.0, 0]}
-    iters = []
+    iters, finals = [], []
     for _ in range(args.steps):
         st, out = step(timing=True)
         e, _ = count_dist_evals(n, k, st, out["iters"])
@@ -184,6 +237,7 @@ def run_ours(args, rank, world):
         kern["round"][0] += st["kernel_ms"][0]; kern["round"][1] += st["kernel_launches"][0]
         kern["assign"][0] += st["kernel_ms"][1]; kern["assign"][1] += st["kernel_launches"][1]
         iters.append(out["iters"])
+        finals.append(out["final_cost"])
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -204,13 +258,40 @@ def run_ours(args, rank, world):
     t0 = time.perf_counter()
     e2e_evals = 0
     for _ in range(e2e_steps):
-        r = km.kmpar_fit(Xpin.data_ptr(), n, d, k, ell, rounds, 7 + rank, prec, max_iter, Cpin.data_ptr(),
+        r = km.kmpar_fit(Xpin.data_ptr(), n, d, k, ell, rounds, seed, prec, max_iter, Cpin.data_ptr(),
                          Lpin.data_ptr(), flags=km.KMPAR_HOST_BUFFERS | fit_flags, stream=stream.cuda_stream)
         assert r["iters"] == out_t["iters"], "end-to-end run took a different trajectory"
         e2e_evals += evals
     torch.cuda.synchronize()
     e2e_s = allreduce_max(time.perf_counter() - t0, world)
     e2e_value = allreduce_sum(float(e2e_evals), world) / e2e_s
+    del Xpin, Cpin, Lpin
+
+    # the plain FP32 CUDA-core path on the same data and seed: the metric's comparison arm
+    fp32_arm = None
+    if args.precision != "fp32" and args.fp32_steps > 0:
+        for _ in range(args.fp32_warmup):
+            step(precision=km.KMPAR_FP32)
+        torch.cuda.synchronize()
+        fa, fb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fa.record(stream)
+        f_out, f_st = [], None
+        for _ in range(args.fp32_steps):
+            f_st, o = step(precision=km.KMPAR_FP32)
+            f_out.append(o)
+        fb.record(stream)
+        torch.cuda.synchronize()
+        f_ms = fa.elapsed_time(fb) / args.fp32_steps
+        f_evals, _ = count_dist_evals(n, k, f_st, f_out[-1]["iters"])
+        f_cost = f_out[-1]["final_cost"]
+        fp32_arm = {"ms_per_step": f_ms, "value": f_evals / (f_ms / 1e3), "unit": UNIT,
+                    "steps": args.fp32_steps, "warmup": args.fp32_warmup,
+                    "final_cost": f_cost, "candidates": f_st["m"], "lloyd_iters": f_out[-1]["iters"],
+                    "final_cost_rel_diff": abs(out_t["final_cost"] - f_cost) / max(abs(f_cost), 1e-300),
+                    "equal_cost": abs(out_t["final_cost"] - f_cost) <= 1e-4 * abs(f_cost),
+                    "same_decisions": (out_t["final_cost"] == f_cost and st_t["m"] == f_st["m"]
+                                       and out_t["iters"] == f_out[-1]["iters"]),
+                    "speedup": f_ms / (ms_max / args.steps)}
 
     # roofline of the dominant kernel (the distance pass with the most time)
     peaks = load_peaks()
@@ -219,8 +300,10 @@ def run_ours(args, rank, world):
     per_launch_ms = kms / max(kl, 1)
     if cls == "assign":
         units = n * k                              # dist-evals per Lloyd assignment pass
+        centers_per_pass = k
     else:
-        units = n * (sum(st_t["round_added"]) / max(len(st_t["round_added"]), 1))
+        centers_per_pass = sum(st_t["round_added"]) / max(len(st_t["round_added"]), 1)
+        units = n * centers_per_pass
     clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     secs = per_launch_ms / 1e3
     if args.precision == "fp32":
@@ -232,102 +315,159 @@ def run_ours(args, rank, world):
                     "frac": achieved / peak, "traffic": None, "kernel": f"nearest_kernel ({cls} pass)",
                     "peak_source": f"derived: 128 FP32 lanes x 152 SMs x {peaks.get('sm_max_mhz', 2070.0)} MHz"}
     else:
-        # tcgen05 screening: the MMA path binds (ncu: tensor pipe ~45% active, ALU ~62%; an
-        # instrumented copy shows the epilogue waiting on the accumulator every tile).
-        # achieved = algorithmic GEMM-form flops 2 d per distance; the kernel is timed inside a
-        # long step, so the peak is the measured sustained BF16 figure
+        # tcgen05 screening: achieved = algorithmic GEMM-form flops 2 d per distance; the
+        # kernel is timed inside a long step, so the peak is the measured sustained figure
+        # for its operand type (FP8 = 2 x BF16, the nominal ratio)
         tflops = units * 2 * d / secs / 1e12
-        peak = float(peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]))
-        # what the tensor cores execute: 3 split products (K = 3 d + 2 padded to 16) for every
-        # padded 128-row x 256-column tile
-        kk = ((3 * d + 2 if args.precision == "bf16x3" else d + 2) + 15) // 16 * 16
-        bn = 256 if kk <= 128 else 128
-        npad, kpad = -(-n // 128) * 128, -(-int(units // n) // bn) * bn
+        ratio = 2.0 if args.precision == "fp8" else 1.0
+        peak = ratio * float(peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]))
+        kk, bn = screen_shape(args.precision, d)
+        npad, kpad = -(-n // 128) * 128, -(-int(centers_per_pass) // bn) * bn
         exec_tflops = 2.0 * npad * kpad * kk / secs / 1e12
-        alu = units * SCREEN_ALU_OPS / secs / 1e12
-        alu_peak = ALU_LANES_PER_SM * SMS * clk / 1e12
-        traffic = TC_ASSIGN_TRAFFIC.get(args.precision) if cls == "assign" and args.workload == "kdd_n1M_d42_k500" \
-            and not args.n else None
+        kernel_name = "tc::nearest_tc_kernel"
+        traffic, cap_sha = traffic_record(f"{kernel_name} ({cls})", args.workload, args.precision) \
+            if not args.n else (None, None)
         roofline = {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
                     "frac": tflops / peak, "traffic": traffic,
-                    "kernel": f"nearest_tc_kernel ({cls} pass)",
-                    "peak_source": f"{peaks.get('source')} bf16 sustained (kernel timed inside the step)",
+                    "kernel": f"{kernel_name} ({cls} pass)",
+                    "peak_source": (f"{peaks.get('source')} bf16 sustained" + (" x 2 (FP8 nominal ratio)"
+                                    if ratio == 2.0 else "") + " (kernel timed inside the step)"),
                     "executed": {"tflops": exec_tflops, "frac": exec_tflops / peak,
-                                 "note": "MMA flops issued: split products, K and k padded"},
-                    "alu": {"achieved": alu, "peak": alu_peak, "unit": "T ALU ops/s", "frac": alu / alu_peak,
-                            "peak_source": f"derived: 64 ALU lanes x 152 SMs x {peaks.get('sm_max_mhz', 2070.0)} MHz"},
+                                 "note": "MMA flops issued: K and the center count padded to the tile"},
                     "hbm": {"gbs": (traffic or 0) / secs / 1e9, "peak_gbs": peaks.get("hbm_gbs")}}
+        if traffic is None:
+            roofline["traffic_note"] = ("no ncu capture of the current kernel source" if cap_sha is None else
+                                        f"capture taken on kernel source {cap_sha}, which has changed since")
     roofline.update({"avg_launch_ms": per_launch_ms, "launches": kl})
 
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else "bf16 (split hi/lo) screening, f32 refine, f64 sums",
+        "dtype": DTYPES[args.precision],
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: n={n} d={d} k={k} l={ell:g} r={rounds} Lloyd<={max_iter}",
+        "config": {"workload": (f"{args.workload}: n={n} d={d} k={k} l={ell:g} r={rounds}, "
+                                f"Lloyd until no label changes, capped at {max_iter} updates"),
                    "precision": args.precision, "sampling": args.sampling,
                    "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 (X {n * d * 4 / 1e6:.0f} MB > 129 MB)"},
         "init_lloyd_s": ms_max / args.steps / 1e3,
         "dist_evals_per_step": evals, "dist_evals_parts": parts,
+        "phase_ms": phase_ms, "recluster_ms": phase_ms["recluster"],
         "lloyd_iters": iters, "final_cost": out_t["final_cost"], "candidates": st_t["m"],
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * d * 4,
                 "d2h_bytes_per_step": k * d * 4 + n * 4, "steps": e2e_steps},
+        "fp32_arm": fp32_arm,
         "roofline": roofline, "clocks": clocks,
         "refine": {key: st_t[key] for key in ("sample_near", "sample_refined", "argmin_fp64", "argmin_wide",
-                                             "screen_rows", "screen_fallback",
+                                             "screen_rows", "screen_fallback", "screen_exact",
                                              "recluster_near")},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(args, seconds_hint=20)
+        res["cpu_baseline"] = cpu_baseline(args)
     return res
 
 
+def screen_shape(precision: str, d: int):
+    """(K columns the MMA executes, centers per tile) of the screening pass."""
+    if precision == "bf16x3":
+        kk = (3 * d + 2 + 15) // 16 * 16
+    elif precision == "fp8":
+        kk = (d + 31) // 32 * 32
+    else:
+        kk = (d + 2 + 15) // 16 * 16
+    bn = 256 if kk <= 128 or precision == "fp8" else 128
+    return kk, bn
+
+
+DTYPES = {"fp32": "f32",
+          "bf16": "bf16 screening, f32 refine, f64 sums",
+          "bf16x3": "bf16 (split hi/lo) screening, f32 refine, f64 sums",
+          "fp8": "fp8 e4m3 (per-row scaled) screening, f32 refine, f64 sums"}
+
+
 # ------------------------------------------------------------------ CPU oracle arms
-def oracle_sample_run(args, n_s: int, lloyd_iters: int):
-    """The oracle on a bounded sample of the workload; returns (seconds, dist-evals)."""
+def oracle_sample(args):
+    """A bounded sample of the workload for the FP64 oracle: the same generator and
+    dimension, n_s points and k_s = k n_s / n clusters (the workload's points per
+    cluster; at least 10), l_s = l k_s / k, the same r, Lloyd capped at the
+    --cpu-lloyd-iters updates."""
+    w = workload(args)
+    n_s = min(args.cpu_sample_n, w["n"])
+    k_s = max(10, min(w["k"], int(round(w["k"] * n_s / w["n"]))))
+    ell_s = w["ell"] * k_s / w["k"]
+    return dict(n=n_s, k=k_s, ell=ell_s, rounds=w["rounds"], lloyd=args.cpu_lloyd_iters)
+
+
+def _oracle_job(argv):
+    """Runs in a child process: one oracle pass of the sample; (seconds, dist-evals, info)."""
+    root, wname, smp, data_seed, run_seed, sampling = argv
+    if root not in sys.path:
+        sys.path.insert(0, root)
     from oracle import oracle
     from paper_1203_6402_gb300 import datagen
-    w = workload(args)
-    k, ell, rounds = w["k"], w["ell"], w["rounds"]
-    Xs = datagen.make(args.workload, seed=1000, n=n_s)
+    w = datagen.WORKLOADS[wname]
+    if w["kind"] == "gmm":
+        Xs = datagen.gauss_mixture(smp["n"], w["d"], smp["k"], w["R"], data_seed)
+    else:
+        Xs = datagen.kdd_like(smp["n"], data_seed)
     t0 = time.perf_counter()
-    par = oracle.kmeans_par(Xs, k, ell, rounds, seed=7, sampling=getattr(args, "sampling", "bernoulli"))
-    _, _, it, _, _, _ = oracle.lloyd(Xs, par.seed_centers, lloyd_iters)
+    par = oracle.kmeans_par(Xs, smp["k"], smp["ell"], smp["rounds"], seed=run_seed, sampling=sampling)
+    _, _, it, _, _, _ = oracle.lloyd(Xs, par.seed_centers, smp["lloyd"])
     dt = time.perf_counter() - t0
-    evals = n_s + n_s * (len(par.cand) - 1) + k * len(par.cand) + (it + 1) * n_s * k
-    return dt, evals, dict(n=n_s, k=k, l=ell, r=rounds, lloyd_iters=it, candidates=len(par.cand))
+    n_s, k_s = smp["n"], smp["k"]
+    evals = n_s + n_s * (len(par.cand) - 1) + k_s * len(par.cand) + (it + 1) * n_s * k_s
+    return dt, evals, dict(lloyd_iters=it, candidates=len(par.cand))
 
 
-def cpu_baseline(args, seconds_hint: float = 20.0):
+def _sample_text(args, smp, threads):
+    w = workload(args)
+    return (f"FP64 C oracle, {threads}: same generator (d={w['d']}), n={smp['n']} points, "
+            f"k={smp['k']} (the workload's {w['n'] // w['k']} points per cluster), l={smp['ell']:g}, "
+            f"r={smp['rounds']}, Lloyd capped at {smp['lloyd']} updates")
+
+
+def cpu_baseline(args):
+    """The oracle as it stands: one process (1 thread), then one process per host
+    core each on its own seeded sample (all cores busy; it is single-threaded)."""
+    import multiprocessing as mp
     from oracle import oracle
     oracle.build()
-    n_s = args.cpu_sample_n
-    dt, evals, info = oracle_sample_run(args, n_s, args.cpu_lloyd_iters)
-    return {"value": evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": dt,
-            "sample": (f"FP64 C oracle, 1 thread: same generator, n={info['n']} of the workload's points, "
-                       f"k={info['k']}, l={info['l']:g}, r={info['r']}, Lloyd capped at "
-                       f"{args.cpu_lloyd_iters} updates ({info['lloyd_iters']} made), {info['candidates']} candidates")}
+    smp = oracle_sample(args)
+    dt, evals, info = _oracle_job((ROOT, args.workload, smp, 1000, 7, args.sampling))
+    res = {"value": evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": dt,
+           "sample": _sample_text(args, smp, "1 thread") + f" ({info['lloyd_iters']} updates made, "
+                                                          f"{info['candidates']} candidates)"}
+    cores = os.cpu_count() or 1
+    if cores > 1 and not args.no_cpu_all_cores:
+        ctx = mp.get_context("spawn")
+        jobs = [(ROOT, args.workload, smp, 1000 + j, 7 + j, args.sampling) for j in range(cores)]
+        t0 = time.perf_counter()
+        with ctx.Pool(cores) as pool:
+            outs = pool.map(_oracle_job, jobs)
+        wall = time.perf_counter() - t0
+        tot = sum(o[1] for o in outs)
+        res["all_cores"] = {"value": tot / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "seconds": wall,
+                            "sample": _sample_text(args, smp, f"{cores} processes x 1 thread") +
+                            ", one seeded sample per process; wall time includes process start-up"}
+    return res
 
 
 def run_reference(args, rank, world):
     from oracle import oracle
     oracle.build()
-    n_s = args.ref_sample_n
+    smp = oracle_sample(argparse.Namespace(**{**vars(args), "cpu_sample_n": args.ref_sample_n}))
     for _ in range(args.warmup):
-        oracle_sample_run(args, n_s, args.cpu_lloyd_iters)
+        _oracle_job((ROOT, args.workload, smp, 1000, 7, args.sampling))
     tot_t, tot_e = 0.0, 0
-    info = None
     for _ in range(args.steps):
-        dt, e, info = oracle_sample_run(args, n_s, args.cpu_lloyd_iters)
+        dt, e, _ = _oracle_job((ROOT, args.workload, smp, 1000, 7, args.sampling))
         tot_t += dt
         tot_e += e
     value = tot_e / tot_t
-    w = workload(args)
-    sample = (f"FP64 C oracle, 1 thread, per step: n={n_s} points of the workload's generator, k={w['k']}, "
-              f"l={w['ell']:g}, r={w['rounds']}, Lloyd capped at {args.cpu_lloyd_iters} updates")
+    sample = _sample_text(args, smp, "1 thread") + ", per step"
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True,
@@ -377,17 +517,23 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16", "bf16x3"])
-    ap.add_argument("--workload", default="kdd_n1M_d42_k500")
+    ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3", "fp8"],
+                    help="screening arithmetic (default: the fastest one built for the workload's d)")
+    ap.add_argument("--workload", default="gmm_n10M_d128_k10000")
     ap.add_argument("--sampling", default="bernoulli", choices=["bernoulli", "exact"],
                     help="round draws: independent (Alg. 2 step 4) or exactly l per round (Sec. 5.3)")
     ap.add_argument("--n", type=int, default=0, help="override n (same recipe)")
     ap.add_argument("--ell-factor", type=float, default=0.0, help="override l as a multiple of k")
-    ap.add_argument("--cpu-sample-n", type=int, default=40000)
-    ap.add_argument("--ref-sample-n", type=int, default=8000)
-    ap.add_argument("--cpu-lloyd-iters", type=int, default=5)
+    ap.add_argument("--cpu-sample-n", type=int, default=50000)
+    ap.add_argument("--ref-sample-n", type=int, default=20000)
+    ap.add_argument("--cpu-lloyd-iters", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-all-cores", action="store_true")
+    ap.add_argument("--fp32-steps", type=int, default=1, help="timed steps of the FP32 comparison arm (0: off)")
+    ap.add_argument("--fp32-warmup", type=int, default=1)
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = default_precision(args.workload)
     if args.warmup < 3:
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -26,6 +26,16 @@
  *   - Limits: 1 <= d <= 4096, 1 <= n < 2^31, 1 <= k, l > 0, 0 <= rounds,
  *     per-round sample capacity l + 10 sqrt(l) + 64 <= 32768.
  *
+ * Fault injection (environment variables, read when the limit applies; for
+ * tests of the error paths, none of them is needed in normal use):
+ *   KMPAR_ROUND_CAPACITY   lowers the per-round draw capacity (read by kmpar_init)
+ *   KMPAR_CTX_LIMIT_BYTES  most device memory one context may hold; a larger
+ *                          allocation fails with KMPAR_ERR_OOM (read at every one)
+ *   KMPAR_WAIT_CYCLES      clock-cycle budget of the grid barrier of the
+ *                          cooperative reclustering kernel (default ~2 s); a wait
+ *                          that runs out returns KMPAR_ERR_TIMEOUT
+ *   KMPAR_RECLUSTER_GRID   1: use the cooperative grid form of step 8 at any size
+ *
  * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = seed and
  * counter = (i_lo, i_hi, round, tag); tag 1 = first center, 2 = round draws,
  * 3 = reclustering draws, 4 = exactly-l round clocks; a uniform double is (a 2^26 + b) / 2^53 with
@@ -73,7 +83,9 @@ typedef enum {
 typedef enum {
     KMPAR_FP32 = 0,     /* CUDA-core FP32 difference form for every pair          */
     KMPAR_BF16 = 1,     /* tcgen05 BF16 GEMM-form screening + exact FP32 refine    */
-    KMPAR_BF16X3 = 2    /* tcgen05 split-BF16 (hi/lo, 3 products) screening+refine */
+    KMPAR_BF16X3 = 2,   /* tcgen05 split-BF16 (hi/lo, 3 products) screening+refine */
+    KMPAR_FP8E4M3 = 3   /* tcgen05 e4m3 screening, per-row power-of-two scales of X
+                           and per-tile scales of the centers, + exact FP32 refine */
 } kmpar_precision;
 
 /* Counters gathered on the device (kmpar_get_stats synchronises). */
@@ -96,8 +108,10 @@ typedef struct {
     double  kernel_ms[2];
     int64_t kernel_launches[2];
     int64_t screen_rows;          /* tensor-core passes: rows screened                 */
-    int64_t screen_fallback;      /* rows whose screening window held 2+ centers and
-                                     that the exact CUDA-core pass decided            */
+    int64_t screen_fallback;      /* rows the pair screening left undecided (they go
+                                     to the list pass, or, in BF16X3, to the exact
+                                     CUDA-core scan)                                 */
+    int64_t screen_exact;         /* rows the exact CUDA-core scan decided             */
 } kmpar_stats;
 
 /*

@@ -40,15 +40,28 @@ kmpar_status cuda_fail(kmp::Ctx *c, cudaError_t e, const char *where) {
 
 bool precision_supported(int p, int d) {
     if (p == KMPAR_FP32) return true;
-    if (p == KMPAR_BF16) return kmp::tc::tc_supported(d, 0);
-    if (p == KMPAR_BF16X3) return kmp::tc::tc_supported(d, 1);
-    return false;
+    const int fmt = kmp::tc::tc_format(p, d);
+    return fmt >= 0 && kmp::tc::tc_supported(d, fmt);
+}
+
+// A positive integer from the environment (0 when unset or malformed).
+uint64_t env_limit(const char *name) {
+    const char *v = getenv(name);
+    if (!v || !*v) return 0;
+    char *end = nullptr;
+    const unsigned long long x = strtoull(v, &end, 10);
+    return (end && *end == 0) ? (uint64_t)x : 0;
 }
 
 int round_capacity(double ell) {
     double c = ell + 10.0 * sqrt(ell) + 64.0;
     if (c > 2.0e9) c = 2.0e9;
-    return (int)ceil(c);
+    int cap = (int)ceil(c);
+    // KMPAR_ROUND_CAPACITY lowers the per-round capacity (fault injection: a round
+    // that draws more returns KMPAR_ERR_CAPACITY)
+    const uint64_t lim = env_limit("KMPAR_ROUND_CAPACITY");
+    if (lim > 0 && lim < (uint64_t)cap) cap = (int)lim;
+    return cap;
 }
 
 // Context buffers come from one stream-ordered memory pool per device, owned by
@@ -84,13 +97,18 @@ cudaError_t ctx_pool(int dev, cudaMemPool_t *out) {
 
 // count elements of T on the context's stream, in whole 256-byte units; the bulk
 // and vector copies of the kernels need 16-byte aligned buffers
+// KMPAR_CTX_LIMIT_BYTES caps the device memory one context may hold (read at every
+// allocation; fault injection: an allocation past it fails as out of memory,
+// without asking the driver).
 template <typename T>
-cudaError_t alloc(const kmp::Ctx &c, T **p, size_t count) {
+cudaError_t alloc(kmp::Ctx &c, T **p, size_t count) {
     *p = nullptr;
     cudaMemPool_t pool;
     cudaError_t e = ctx_pool(c.dev, &pool);
     if (e != cudaSuccess) return e;
     const size_t bytes = (sizeof(T) * (count ? count : 1) + 255) & ~(size_t)255;
+    const uint64_t lim = env_limit("KMPAR_CTX_LIMIT_BYTES");
+    if (lim > 0 && c.alloc_bytes + bytes > lim) return cudaErrorMemoryAllocation;
     void *q = nullptr;
     if ((e = cudaMallocFromPoolAsync(&q, bytes, pool, c.stream)) != cudaSuccess) return e;
     if (reinterpret_cast<uintptr_t>(q) & 15u) {
@@ -98,6 +116,7 @@ cudaError_t alloc(const kmp::Ctx &c, T **p, size_t count) {
         return cudaErrorMisalignedAddress;
     }
     *p = static_cast<T *>(q);
+    c.alloc_bytes += bytes;
     return cudaSuccess;
 }
 
@@ -106,7 +125,9 @@ void free_ctx(kmp::Ctx &c) {
                     c.labels[0], c.labels[1], c.perm, c.hist, c.base, c.cost_dev, c.tc_img,
                     c.tc_cmax, c.tc_err, c.cand1, c.fix_rows, c.fix_cnt, c.dmin, c.tc_ximg, c.tc_xnorm,
                     c.piece, c.psum, c.rc_cmass, c.rc_sync, c.rc_err, c.chunk, c.tc_v2,
-                    c.tc_anchor, c.tc_anchor_part, c.lloyd_rec, c.ex_keys, c.ex_ws, c.ex_ties};
+                    c.tc_anchor, c.tc_anchor_part, c.lloyd_rec, c.ex_keys, c.ex_ws, c.ex_ties,
+                    c.tc_ncol, c.tc_tscale, c.tc_xscale, c.tc_ub, c.tc_cimg, c.tc_cscale, c.tc_thr,
+                    c.tc_lst, c.tc_lcnt, c.fix_rows2, c.fix_cnt2, c.rCT};
     // stream-ordered: the memory returns to the pool once the context's work is done
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, c.stream);
@@ -240,27 +261,45 @@ kmpar_status kmpar_init(kmpar_ctx **out, const float *X, int64_t n, int32_t d, i
     KMP_INIT_CUDA(alloc(c, &c.w, c.cap_total), "alloc weights");
     KMP_INIT_CUDA(alloc(c, &c.rD2, c.cap_total), "alloc recluster D2");
     KMP_INIT_CUDA(alloc(c, &c.chosen, k), "alloc chosen");
-    KMP_INIT_CUDA(alloc(c, &c.rc_cmass, 2 * (size_t)((c.cap_total + 31) / 32)), "alloc recluster masses");
+    KMP_INIT_CUDA(alloc(c, &c.rc_cmass, 2 * (size_t)((c.cap_total + 31) / 32) + 2048), "alloc recluster masses");
     unsigned char *rc_sync = nullptr;
     KMP_INIT_CUDA(alloc(c, &rc_sync, kmp::recluster_sync_bytes()), "alloc recluster sync");
     c.rc_sync = rc_sync;
     KMP_INIT_CUDA(alloc(c, &c.rc_err, 1), "alloc recluster error");
     KMP_INIT_CUDA(alloc(c, &c.partials, c.num_partials), "alloc partials");
     if (precision != KMPAR_FP32) {
-        const int split = precision == KMPAR_BF16X3 ? 1 : 0;
+        namespace tc = kmp::tc;
+        const int fmt = tc::tc_format(precision, d);
+        c.tc_fmt = fmt;
+        c.tc_list = fmt != tc::FMT_BF16X3;
         const int rows = std::max(cap_round, k);
-        KMP_INIT_CUDA(alloc(c, &c.tc_img, kmp::tc::tc_image_bytes(d, split, rows)), "alloc center tiles");
+        const size_t n128 = (size_t)((n + 127) / 128) * 128;
+        KMP_INIT_CUDA(alloc(c, &c.tc_img, tc::tc_image_bytes(d, fmt, rows)), "alloc center tiles");
+        KMP_INIT_CUDA(alloc(c, &c.tc_ncol, (size_t)tc::tc_center_tiles(d, fmt, rows) * tc::tc_block_n(d, fmt)),
+                      "alloc center norms");
+        KMP_INIT_CUDA(alloc(c, &c.tc_tscale, (size_t)tc::tc_center_tiles(d, fmt, rows)), "alloc tile scales");
         KMP_INIT_CUDA(alloc(c, &c.tc_cmax, 1), "alloc cmax");
         KMP_INIT_CUDA(alloc(c, &c.tc_err, 1), "alloc error word");
         KMP_INIT_CUDA(alloc(c, &c.fix_rows, n), "alloc fix-up rows");
         KMP_INIT_CUDA(alloc(c, &c.cand1, n), "alloc screening winners");
         KMP_INIT_CUDA(alloc(c, &c.tc_v2, n), "alloc screening values");
-        KMP_INIT_CUDA(alloc(c, &c.tc_ximg, kmp::tc::tc_points_image_bytes(d, split, n)), "alloc points image");
-        KMP_INIT_CUDA(alloc(c, &c.tc_xnorm, (size_t)((n + 127) / 128) * 128), "alloc point norms");
+        KMP_INIT_CUDA(alloc(c, &c.tc_ub, n), "alloc row bounds");
+        KMP_INIT_CUDA(alloc(c, &c.tc_ximg, tc::tc_points_image_bytes(d, fmt, n)), "alloc points image");
+        KMP_INIT_CUDA(alloc(c, &c.tc_xnorm, n128), "alloc point norms");
+        KMP_INIT_CUDA(alloc(c, &c.tc_xscale, n128), "alloc point scales");
+        if (c.tc_list) {
+            KMP_INIT_CUDA(alloc(c, &c.tc_cimg, tc::tc_points_image_bytes(d, fmt, n)), "alloc list image");
+            KMP_INIT_CUDA(alloc(c, &c.tc_cscale, n128), "alloc list scales");
+            KMP_INIT_CUDA(alloc(c, &c.tc_thr, n128), "alloc list thresholds");
+            KMP_INIT_CUDA(alloc(c, &c.tc_lst, (size_t)n * 4 * tc::kListSlots), "alloc lists");
+            KMP_INIT_CUDA(alloc(c, &c.tc_lcnt, (size_t)n * 4), "alloc list counts");
+            KMP_INIT_CUDA(alloc(c, &c.fix_rows2, n), "alloc exact-scan rows");
+            KMP_INIT_CUDA(alloc(c, &c.fix_cnt2, 1), "alloc exact-scan count");
+        }
         KMP_INIT_CUDA(alloc(c, &c.tc_anchor, d), "alloc anchor");
-        KMP_INIT_CUDA(alloc(c, &c.tc_anchor_part, kmp::tc::tc_anchor_scratch_doubles(d)), "alloc anchor sums");
-        KMP_INIT_CUDA(kmp::tc::launch_anchor(X, n, d, c.tc_anchor_part, c.tc_anchor, c.stream), "anchor");
-        KMP_INIT_CUDA(kmp::tc::launch_prep_points(X, n, d, split, c.tc_anchor, c.tc_ximg, c.tc_xnorm, c.stream),
+        KMP_INIT_CUDA(alloc(c, &c.tc_anchor_part, tc::tc_anchor_scratch_doubles(d)), "alloc anchor sums");
+        KMP_INIT_CUDA(tc::launch_anchor(X, n, d, c.tc_anchor_part, c.tc_anchor, c.stream), "anchor");
+        KMP_INIT_CUDA(tc::launch_prep_points(X, n, d, fmt, c.tc_anchor, c.tc_ximg, c.tc_xnorm, c.tc_xscale, c.stream),
                       "points image");
         KMP_INIT_CUDA(alloc(c, &c.fix_cnt, 1), "alloc fix-up count");
         KMP_INIT_CUDA(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream), "memset error word");
@@ -348,6 +387,10 @@ kmpar_status kmpar_recluster(kmpar_ctx *ctx, float *centers_dev) {
     kmp::Ctx &c = ctx->c;
     if (!centers_dev) return fail(&c, KMPAR_ERR_ARG, "centers_dev is NULL");
     if (!c.weighted) return fail(&c, KMPAR_ERR_STATE, "recluster before weight");
+    if (!c.rCT) {
+        const size_t nf = kmp::recluster_grid_floats(c);
+        if (nf) KMP_CUDA(&c, alloc(c, &c.rCT, nf), "alloc transposed candidates");
+    }
     KMP_CUDA(&c, cudaMemsetAsync(&c.st->warn, 0, sizeof(int32_t), c.stream), "memset warn");
     KMP_CUDA(&c, cudaMemsetAsync(c.rc_err, 0, sizeof(int), c.stream), "memset recluster error");
     KMP_CUDA(&c, kmp::launch_recluster(c, centers_dev), "recluster kernel");
@@ -526,6 +569,7 @@ kmpar_status kmpar_get_stats(kmpar_ctx *ctx, kmpar_stats *out) {
     out->recluster_warn = st.warn;
     out->screen_rows = (int64_t)st.screen_rows;
     out->screen_fallback = (int64_t)st.screen_fallback;
+    out->screen_exact = (int64_t)st.screen_exact;
     KMP_CUDA(&c, kmp::timing_drain(c), "timing");
     for (int i = 0; i < 2; ++i) {
         out->kernel_ms[i] = c.kernel_ms[i];

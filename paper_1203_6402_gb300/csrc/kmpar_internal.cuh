@@ -35,7 +35,8 @@ struct DevState {
     double phi_hist[kMaxRounds + 1];
     int32_t round_added[kMaxRounds];
     unsigned long long sample_near, sample_refined, argmin_fp64, argmin_wide, recluster_near;
-    unsigned long long screen_rows, screen_fallback;   // tensor passes: rows screened, rows sent to fix-up
+    unsigned long long screen_rows, screen_fallback;   // tensor passes: rows screened, rows the pair screening left
+    unsigned long long screen_exact;                   // rows that needed the exact scan
 };
 
 struct Ctx {
@@ -53,6 +54,7 @@ struct Ctx {
     int lloyd_iters = 0;
     // capacities
     int cap_round = 0, cap_total = 0;
+    size_t alloc_bytes = 0;       // device memory this context holds
     // device buffers
     DevState *st = nullptr;
     float *D2 = nullptr;
@@ -62,7 +64,8 @@ struct Ctx {
     float *C = nullptr;           // cap_total x d candidate rows
     long long *w = nullptr;       // cap_total
     float *rD2 = nullptr;         // recluster D^2 (cap_total)
-    double *rc_cmass = nullptr;   // recluster chunk masses, 2 x ceil(cap_total / 32)
+    double *rc_cmass = nullptr;   // recluster chunk masses, 2 x ceil(cap_total / 32), then 2 x 1024 CTA totals
+    float *rCT = nullptr;         // recluster grid form: candidates transposed (d x cap_total padded to 32)
     void *rc_sync = nullptr;      // recluster grid barrier / pick flag
     int *rc_err = nullptr;        // recluster timeout flag
     int32_t *chosen = nullptr;    // k
@@ -81,8 +84,10 @@ struct Ctx {
     void *lloyd_rec = nullptr;    // per Lloyd iteration: (cost, labels changed), 16 bytes
     int lloyd_rec_cap = 0;
     double *cost_dev = nullptr;   // one FP64
-    // tensor-core screening (BF16 modes)
-    uint8_t *tc_img = nullptr;    // swizzled BF16 center tiles
+    // tensor-core screening (BF16 and FP8 modes)
+    int tc_fmt = -1;              // tc::Fmt of the screening operands
+    bool tc_list = false;         // undecided rows get the list pass before the exact scan
+    uint8_t *tc_img = nullptr;    // swizzled center tiles
     uint8_t *tc_ximg = nullptr;   // swizzled BF16 image of X (built once per context)
     float *tc_xnorm = nullptr;    // ||x'||^2 per point (x' = x - anchor)
     float *tc_anchor = nullptr;   // d column means of X
@@ -94,6 +99,17 @@ struct Ctx {
     int32_t *fix_rows = nullptr;  // rows left to the exact CUDA-core pass
     int *fix_cnt = nullptr;
     float *dmin = nullptr;        // Lloyd: exact d^2 of each point's chosen center
+    float *tc_ncol = nullptr;     // norms in the epilogue: ||c'||^2 per pass-local center
+    float *tc_tscale = nullptr;   // per center tile scale
+    float *tc_xscale = nullptr;   // FP8: per-row scale of the points image
+    float *tc_ub = nullptr;       // per row: exact upper bound of the deciding distance (undecided rows)
+    uint8_t *tc_cimg = nullptr;   // list pass: image rows of the undecided rows, compacted
+    float *tc_cscale = nullptr;   // list pass: their scales
+    float *tc_thr = nullptr;      // list pass: their thresholds
+    int32_t *tc_lst = nullptr;    // list pass: 4 x kListSlots centers per row
+    int32_t *tc_lcnt = nullptr;   // list pass: entries per row and column group
+    int32_t *fix_rows2 = nullptr; // rows left to the exact scan after the list pass
+    int *fix_cnt2 = nullptr;
     // exactly-l rounds (Sec. 5.3): 0 = independent draws, 1 = floor(l) per round
     int sampling = 0;
     uint32_t *ex_keys = nullptr;  // per point: FP32 clock bits
@@ -215,6 +231,7 @@ cudaError_t launch_phi_finalize(Ctx &c, int nparts, double *out, double *hist_sl
 cudaError_t launch_weights(Ctx &c);
 cudaError_t launch_recluster(Ctx &c, float *centers);
 size_t recluster_sync_bytes();
+size_t recluster_grid_floats(const Ctx &c);   // floats of the transposed copy the grid form needs (0: none)
 cudaError_t launch_assign(const float *X, int64_t n, int d, const float *C, int k, int32_t *labels,
                           const int32_t *prev, int *changed, double *partials, int nparts,
                           unsigned long long *fp64_cnt, cudaStream_t s);
@@ -223,7 +240,7 @@ cudaError_t launch_centroids(Ctx &c, const int32_t *labels, float *centers);
 int sort_block_size(int64_t n, int k);
 int64_t max_pieces(int64_t n, int k);
 int64_t scan_chunks(int nsb);
-cudaError_t count_fixups(Ctx &c);   // adds the current fix-up count to the screening stats
+cudaError_t count_fixups(Ctx &c, const int *exact_cnt);   // adds the pass's counts to the screening stats
 cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
                            int *changed, float *dmin, int timing_cls);
 cudaError_t launch_sum_rows(const float *v, int64_t n, double *partials, int max_parts, double *out, double *copy,

@@ -32,28 +32,30 @@ cudaError_t launch_weights(Ctx &c) {
 
 // ------------------------------------------------------------------ step 8
 // Weighted k-means++ (Alg. 1 with multiplicities w): k sequential draws over the m
-// candidates.  One cooperative launch; the candidates are cut into fixed chunks of
-// 32 (one warp each, FP64 shuffle scans), so every sum is independent of the grid
-// size.  Per draw t:
-//   A  each warp: masses e_j = w_j (t = 0) or w_j D^2_j, inclusive warp scan,
-//      chunk total -> cmass[t & 1][chunk]                    ... grid barrier
-//   B  every CTA: the same fixed-order scan of the chunk totals -> total, target
-//      u_t * total, the first chunk whose running prefix exceeds it; the warp that
-//      owns that chunk picks the first candidate crossing the target and publishes
-//      it (release flag); the other CTAs wait for the flag (bounded)
-//   C  every warp: D^2_j <- min(D^2_j, ||c_j - c_pick||^2) (exact FP32 form)
-// All waits are bounded: a timeout raises st->rc_err and every CTA returns.
-constexpr int kRcThreads = 128;   // 4 warps per CTA
+// candidates.  One cooperative launch, one CTA of 1024 threads per SM; the
+// candidates are cut into fixed chunks of 32 (one warp each, FP64 shuffle scans)
+// and CTA b owns the contiguous chunk range [b cpc, (b+1) cpc).  Per draw t:
+//   A  each warp: masses e_j = w_j (t = 0) or w_j D^2_j, inclusive warp scan;
+//      chunk totals -> gchunk, the CTA's total (its chunks in a fixed order) ->
+//      gctot                                               ... grid barrier
+//   B  every CTA (warp 0) finds the same pick from the published totals: a
+//      fixed-order prefix over the CTA totals gives the owning CTA of the target
+//      u_t * total, a prefix over that CTA's chunk totals the chunk, a scan of the
+//      chunk's masses the first candidate whose prefix exceeds the target
+//   C  every warp: D^2_j <- min(D^2_j, ||c_j - c_pick||^2) in the exact FP32 form,
+//      reading the candidates from a transposed copy (coordinate-major), so a
+//      warp's 32 candidates are one coalesced 128-byte load per coordinate.
+// One grid barrier per draw; every wait is bounded (by `wait` clock cycles, about
+// 2 s by default): a timeout raises the error word and every CTA returns.
+constexpr int kRcThreads = 1024;
 constexpr unsigned long long kRcWait = 4000000000ull;
 
 struct RcSync {
     unsigned int count, gen;   // grid barrier
-    unsigned int pick_flag;    // t + 1 once pick[t] is published
-    int pick[2];
     int abort;
 };
 
-__device__ __forceinline__ bool rc_grid_sync(RcSync *s, unsigned int nblocks, int *err) {
+__device__ __forceinline__ bool rc_grid_sync(RcSync *s, unsigned int nblocks, int *err, unsigned long long wait) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -69,7 +71,7 @@ __device__ __forceinline__ bool rc_grid_sync(RcSync *s, unsigned int nblocks, in
             const unsigned long long t0 = clock64();
             while (*gen == g) {
                 if (*(volatile int *)&s->abort) { ok = 0; break; }
-                if (clock64() - t0 > kRcWait) {
+                if (clock64() - t0 > wait) {
                     atomicCAS(err, 0, 1);
                     atomicExch(&s->abort, 1);
                     ok = 0;
@@ -93,155 +95,185 @@ __device__ __forceinline__ double warp_incl_scan_f64(double v, int lane) {
     return v;
 }
 
-__global__ void __launch_bounds__(kRcThreads) recluster_kernel(const float *__restrict__ C,
-                                                             const long long *__restrict__ w, DevState *st, int d,
-                                                             int k, uint64_t seed, float *rD2, int32_t *chosen,
-                                                             float *centers, double *cmass, RcSync *sync, int *err) {
-    extern __shared__ float cnew[];   // d floats
-    __shared__ double sbuf[kRcThreads];
-    __shared__ int s_min[kRcThreads / 32], s_pick, s_chunk, s_go;
-    __shared__ double s_pre;
+// candidates (m x d, row-major) -> CT (d x mp, coordinate-major), 32 x 32 tiles
+__global__ void transpose_cand_kernel(const float *__restrict__ C, int d, const DevState *st, int mp,
+                                      float *__restrict__ CT) {
+    __shared__ float tile[32][33];
+    const int m = st->m;
+    const int j0 = blockIdx.x * 32, q0 = blockIdx.y * 32;
+    if (j0 >= m) return;
+    for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
+        const int j = j0 + ty, q = q0 + threadIdx.x;
+        tile[ty][threadIdx.x] = (j < m && q < d) ? C[(int64_t)j * d + q] : 0.f;
+    }
+    __syncthreads();
+    for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
+        const int q = q0 + ty, j = j0 + threadIdx.x;
+        if (q < d && j < m) CT[(int64_t)q * mp + j] = tile[threadIdx.x][ty];
+    }
+}
+
+// Lane-parallel search of a fixed-order prefix: values v[lo .. hi) (global, read
+// past L1), lane l summing its consecutive share; returns the first index whose
+// running prefix (starting at `start`) exceeds target (-1: none) and the prefix
+// before it.  Every CTA gets the same answer from the same values.
+__device__ __forceinline__ int prefix_find(const double *v, int lo, int hi, double start, double target, int lane,
+                                           double *before, double *total_out) {
+    const int cnt = hi - lo;
+    const int q = (cnt + 31) / 32;
+    const int a = lo + min(cnt, lane * q), b = lo + min(cnt, lane * q + q);
+    double ls = 0.0;
+    for (int i = a; i < b; ++i) ls += __ldcg(v + i);
+    const double incl = warp_incl_scan_f64(ls, lane);
+    double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = 0.0;
+    if (total_out) *total_out = start + __shfl_sync(0xffffffffu, incl, 31);
+    int hit = -1;
+    double bf = 0.0, run = start + excl;
+    for (int i = a; i < b; ++i) {
+        const double pre = run;
+        run = run + __ldcg(v + i);
+        if (run > target) { hit = i; bf = pre; break; }
+    }
+    const unsigned any = __ballot_sync(0xffffffffu, hit >= 0);
+    if (!any) return -1;
+    const int src = __ffs(any) - 1;
+    *before = __shfl_sync(0xffffffffu, bf, src);
+    return __shfl_sync(0xffffffffu, hit, src);
+}
+
+// last index in [lo, hi) with a positive value (-1: none)
+__device__ __forceinline__ int last_positive(const double *v, int lo, int hi, int lane) {
+    int best = -1;
+    for (int i = lo + lane; i < hi; i += 32)
+        if (__ldcg(v + i) > 0.0) best = i;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    return best;
+}
+
+__global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
+    const float *__restrict__ C, const float *__restrict__ CT, int mp, const long long *__restrict__ w, DevState *st,
+    int d, int k, uint64_t seed, float *rD2, int32_t *chosen, float *centers, double *gchunk, int nchunk_cap,
+    double *gctot, int cpc_cap, RcSync *sync, int *err, unsigned long long wait) {
+    extern __shared__ double rsm[];   // cpc_cap chunk totals, then d floats of the pick's row
+    double *ctl = rsm;
+    float *cnew = reinterpret_cast<float *>(rsm + cpc_cap);
+    __shared__ int s_pick, s_near, s_done;
     const int m = st->m;
     const int nchunk = (m + 31) / 32;
     const int G = gridDim.x;
-    const int cpc = (nchunk + G - 1) / G;                 // chunks per CTA (contiguous)
-    const int c0 = min(nchunk, (int)blockIdx.x * cpc), c1 = min(nchunk, c0 + cpc);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int t_id = threadIdx.x;
+    const int cpc = (nchunk + G - 1) / G;
+    const int b = blockIdx.x;
+    const int c0 = min(nchunk, b * cpc), c1 = min(nchunk, c0 + cpc);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = kRcThreads / 32;
 
     for (int step = 0; step < k; ++step) {
-        double *cm = cmass + (size_t)(step & 1) * nchunk;
-        // ---- A: chunk masses
-        for (int ch = c0 + wid; ch < c1; ch += kRcThreads / 32) {
+        double *gch = gchunk + (size_t)(step & 1) * nchunk_cap;
+        double *gct = gctot + (size_t)(step & 1) * G;
+        // ---- A: chunk masses and the CTA total
+        for (int ch = c0 + wid; ch < c1; ch += nwarps) {
             const int j = ch * 32 + lane;
             double e = 0.0;
             if (j < m) e = step == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)rD2[j]);
             const double incl = warp_incl_scan_f64(e, lane);
-            if (lane == 31) cm[ch] = incl;
+            if (lane == 31) {
+                ctl[ch - c0] = incl;
+                gch[ch] = incl;
+            }
         }
-        if (!rc_grid_sync(sync, G, err)) return;
-        // ---- B: fixed-order scan of the chunk totals (identical in every CTA)
-        const int q = (nchunk + kRcThreads - 1) / kRcThreads;
-        const int lo = min(nchunk, t_id * q), hi = min(nchunk, lo + q);
-        double local = 0.0;
-        for (int i = lo; i < hi; ++i) local += __ldcg(cm + i);
-        sbuf[t_id] = local;
         __syncthreads();
-        for (int off = 1; off < kRcThreads; off <<= 1) {
-            const double a = t_id >= off ? sbuf[t_id - off] : 0.0;
-            __syncthreads();
-            if (t_id >= off) sbuf[t_id] += a;
-            __syncthreads();
+        if (wid == 0) {
+            double s = 0.0;
+            for (int i = lane; i < c1 - c0; i += 32) s += ctl[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) gct[b] = s;
         }
-        const double excl = t_id > 0 ? sbuf[t_id - 1] : 0.0;
-        const double total = sbuf[kRcThreads - 1];
+        __threadfence();
+        if (!rc_grid_sync(sync, G, err, wait)) return;
+        // ---- B: the pick, found identically by every CTA
+        if (wid == 0) {
+            double total = 0.0, before = 0.0;
+            const double u = uniform53((uint64_t)step, 0, TAG_RECLUSTER, seed);
+            // total first (the target depends on it), then the owning CTA
+            double dummy;
+            prefix_find(gct, 0, G, 0.0, __uint_as_float(0x7F800000u), lane, &dummy, &total);
+            int pick = -1, near = 0;
+            if (total > 0.0) {
+                const double target = __dmul_rn(u, total);
+                int ob = prefix_find(gct, 0, G, 0.0, target, lane, &before, nullptr);
+                double pre_b = before;
+                if (ob < 0) { ob = last_positive(gct, 0, G, lane); pre_b = 0.0; near = 1; }
+                const int oc0 = min(nchunk, ob * cpc), oc1 = min(nchunk, oc0 + cpc);
+                int ch = near ? -1 : prefix_find(gch, oc0, oc1, pre_b, target, lane, &before, nullptr);
+                double pre_c = before;
+                if (ch < 0) { ch = last_positive(gch, oc0, oc1, lane); near = 1; }
+                const int j = ch * 32 + lane;
+                double e = 0.0;
+                if (j < m) e = step == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)__ldcg(rD2 + j));
+                const double incl = warp_incl_scan_f64(e, lane);
+                const unsigned pos = __ballot_sync(0xffffffffu, j < m && e > 0.0);
+                if (!near) {
+                    const double cum = pre_c + incl, cum0 = pre_c + (incl - e);
+                    const unsigned hit = __ballot_sync(0xffffffffu, j < m && cum > target);
+                    if (hit) {
+                        const int hl = __ffs(hit) - 1;
+                        pick = ch * 32 + hl;
+                        const int nr = fabs(target - cum0) <= 1e-6 * total || fabs(cum - target) <= 1e-6 * total;
+                        near = __shfl_sync(0xffffffffu, nr, hl);
+                    } else {
+                        near = 1;
+                    }
+                }
+                if (pick < 0) pick = ch * 32 + 31 - __clz(pos);   // last positive mass of the chunk
+            }
+            if (lane == 0) {
+                s_pick = pick;
+                s_near = near;
+                s_done = !(total > 0.0);
+            }
+        }
         __syncthreads();
-        if (!(total > 0.0)) {
+        if (s_done) {
             // positive mass exhausted: the remaining draws repeat the first center
-            if (blockIdx.x == 0) {
-                for (int s = step + t_id; s < k; s += kRcThreads) chosen[s] = step > 0 ? chosen[0] : 0;
-                if (t_id == 0) st->warn = 1;
+            if (b == 0) {
+                for (int s2 = step + threadIdx.x; s2 < k; s2 += kRcThreads) chosen[s2] = step > 0 ? chosen[0] : 0;
+                if (threadIdx.x == 0) st->warn = 1;
                 __syncthreads();
                 const int src = step > 0 ? chosen[0] : 0;
-                for (int s = step; s < k; ++s)
-                    for (int qq = t_id; qq < d; qq += kRcThreads) centers[(int64_t)s * d + qq] = C[(int64_t)src * d + qq];
+                for (int s2 = step; s2 < k; ++s2)
+                    for (int qq = threadIdx.x; qq < d; qq += kRcThreads)
+                        centers[(int64_t)s2 * d + qq] = C[(int64_t)src * d + qq];
             }
             return;
         }
-        const double u = uniform53((uint64_t)step, 0, TAG_RECLUSTER, seed);
-        const double target = __dmul_rn(u, total);
-        int mine = INT_MAX;
-        double run = excl, before = excl;
-        for (int i = lo; i < hi; ++i) {
-            const double b = run;
-            run = run + __ldcg(cm + i);
-            if (run > target) { mine = i; before = b; break; }
-        }
-        int a = mine;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a = min(a, __shfl_down_sync(0xffffffffu, a, o));
-        if (lane == 0) s_min[wid] = a;
-        __syncthreads();
-        if (t_id == 0) {
-            int cmin = INT_MAX;
-            for (int i = 0; i < kRcThreads / 32; ++i) cmin = min(cmin, s_min[i]);
-            s_chunk = cmin;
-        }
-        __syncthreads();
-        int chunk = s_chunk;
-        if (mine == chunk && chunk != INT_MAX) s_pre = before;   // exactly one thread owns it
-        __syncthreads();
-        const bool rounding_miss = chunk == INT_MAX;             // the target rounded past every prefix
-        if (rounding_miss) chunk = nchunk - 1;
-        const double pre = rounding_miss ? 0.0 : s_pre;
-        // ---- the owner warp picks inside the chunk and publishes
-        if (chunk >= c0 && chunk < c1 && (chunk - c0) % (kRcThreads / 32) == wid) {
-            const int j = chunk * 32 + lane;
-            double e = 0.0;
-            if (j < m) e = step == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)rD2[j]);
-            const double incl = warp_incl_scan_f64(e, lane);
-            const double cum = pre + incl, cum0 = pre + (incl - e);
-            int pick;
-            if (!rounding_miss) {
-                const unsigned hit = __ballot_sync(0xffffffffu, j < m && cum > target);
-                // fall back to the chunk's last positive mass if rounding hides the crossing
-                const unsigned pos = __ballot_sync(0xffffffffu, j < m && e > 0.0);
-                pick = hit ? chunk * 32 + __ffs(hit) - 1 : chunk * 32 + 31 - __clz(pos);
-                const bool near = fabs(target - cum0) <= 1e-6 * total || fabs(cum - target) <= 1e-6 * total;
-                if (hit && lane == __ffs(hit) - 1 && near) atomicAdd(&st->recluster_near, 1ull);
-            } else {
-                // last candidate with positive mass anywhere (scan chunks backwards)
-                pick = -1;
-                for (int ch2 = nchunk - 1; ch2 >= 0 && pick < 0; --ch2) {
-                    const int jj = ch2 * 32 + lane;
-                    const double ee = (jj < m) ? (step == 0 ? (double)w[jj] : (double)w[jj] * (double)__ldcg(rD2 + jj)) : 0.0;
-                    const unsigned pos = __ballot_sync(0xffffffffu, ee > 0.0);
-                    if (pos) pick = ch2 * 32 + 31 - __clz(pos);
-                }
-                if (lane == 0) atomicAdd(&st->recluster_near, 1ull);
-            }
-            if (lane == 0) {
-                sync->pick[step & 1] = pick;
-                chosen[step] = pick;
-                __threadfence();
-                atomicExch(&sync->pick_flag, (unsigned)(step + 1));
-            }
-        }
-        // ---- wait for the pick (bounded) and load its row
-        if (t_id == 0) {
-            s_go = 1;
-            volatile unsigned int *flag = &sync->pick_flag;
-            const unsigned long long t0 = clock64();
-            while (*flag < (unsigned)(step + 1)) {
-                if (*(volatile int *)&sync->abort || clock64() - t0 > kRcWait) {
-                    atomicCAS(err, 0, 2);
-                    atomicExch(&sync->abort, 1);
-                    s_go = 0;
-                    break;
-                }
-                __nanosleep(32);
-            }
-            __threadfence();
-            s_pick = s_go ? ((volatile int *)sync->pick)[step & 1] : 0;
-        }
-        __syncthreads();
-        if (!s_go) return;
         const int pick = s_pick;
-        for (int qq = t_id; qq < d; qq += kRcThreads) {
+        if (b == 0 && threadIdx.x == 0) {
+            chosen[step] = pick;
+            if (s_near) atomicAdd(&st->recluster_near, 1ull);
+        }
+        for (int qq = threadIdx.x; qq < d; qq += kRcThreads) {
             const float v = __ldcg(C + (int64_t)pick * d + qq);
             cnew[qq] = v;
-            if (blockIdx.x == 0) centers[(int64_t)step * d + qq] = v;
+            if (b == 0) centers[(int64_t)step * d + qq] = v;
         }
         __syncthreads();
-        // ---- C: D^2 update of own candidates
-        for (int ch = c0 + wid; ch < c1; ch += kRcThreads / 32) {
+        // ---- C: D^2 update of own candidates (t = x_q - c_q, fma, q ascending)
+        for (int ch = c0 + wid; ch < c1; ch += nwarps) {
             const int j = ch * 32 + lane;
             if (j < m) {
-                const float v = dist2_fp32(C + (int64_t)j * d, cnew, d);
+                float v = 0.f;
+                const float *col = CT + j;
+#pragma unroll 8
+                for (int q = 0; q < d; ++q) {
+                    const float t = __fsub_rn(__ldg(col + (int64_t)q * mp), cnew[q]);
+                    v = __fmaf_rn(t, t, v);
+                }
                 rD2[j] = step == 0 ? v : fminf(rD2[j], v);
             }
         }
-        // the next step's barrier orders these writes before anyone reads them
+        // the next draw's barrier orders these writes before any CTA reads them
     }
 }
 
@@ -518,6 +550,14 @@ cudaError_t launch_recluster_cluster(Ctx &c, float *centers, int cpc, int rows) 
     return e;
 }
 
+size_t recluster_grid_floats(const Ctx &c) {
+    int cpc = 0, rows = 0;
+    const char *force_grid = std::getenv("KMPAR_RECLUSTER_GRID");
+    const bool grid_only = force_grid && force_grid[0] == '1';
+    if (!grid_only && cluster_plan(c, &cpc, &rows)) return 0;
+    return (size_t)((c.cap_total + 31) / 32) * 32 * c.d;
+}
+
 cudaError_t launch_recluster(Ctx &c, float *centers) {
     cudaError_t e;
     int cpc = 0, rows = 0;
@@ -526,27 +566,48 @@ cudaError_t launch_recluster(Ctx &c, float *centers) {
     const char *force_grid = std::getenv("KMPAR_RECLUSTER_GRID");
     const bool grid_only = force_grid && force_grid[0] == '1';
     if (!grid_only && cluster_plan(c, &cpc, &rows)) return launch_recluster_cluster(c, centers, cpc, rows);
+    if (!c.rCT) return cudaErrorInvalidValue;   // kmpar_recluster allocates the transposed copy first
     if ((e = cudaMemsetAsync(c.rc_sync, 0, sizeof(RcSync), c.stream)) != cudaSuccess) return e;
-    const size_t smem = sizeof(float) * (size_t)c.d;
-    // co-resident CTAs: one per SM at most, no more than there are chunks
+    const int mp = (c.cap_total + 31) / 32 * 32;
+    transpose_cand_kernel<<<dim3(mp / 32, (c.d + 31) / 32), dim3(32, 8), 0, c.stream>>>(c.C, c.d, c.st, mp, c.rCT);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // one co-resident CTA per SM
+    const int nchunk_cap = (c.cap_total + 31) / 32;
+    int G = std::max(1, std::min(c.num_sms, nchunk_cap));
+    const int cpc_cap = (nchunk_cap + G - 1) / G;
+    const size_t smem = sizeof(double) * (size_t)cpc_cap + sizeof(float) * (size_t)c.d;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(recluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+        return e;
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, recluster_kernel, kRcThreads, smem)) !=
         cudaSuccess)
         return e;
-    const int max_chunks = (c.cap_total + 31) / 32;
-    int G = std::min(c.num_sms * std::max(per_sm, 1), std::max(1, (max_chunks + 3) / 4));
-    G = std::max(1, std::min(G, c.num_sms));
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     const float *Cp = c.C;
+    const float *CTp = c.rCT;
     const long long *wp = c.w;
     DevState *stp = c.st;
-    int d = c.d, k = c.k;
+    int d = c.d, k = c.k, mpv = mp, ncap = nchunk_cap, cpcv = cpc_cap;
     uint64_t seed = c.seed;
     float *rD2 = c.rD2;
     int32_t *chosen = c.chosen;
-    double *cm = c.rc_cmass;
+    double *gch = c.rc_cmass;
+    double *gct = c.rc_cmass + 2 * (size_t)nchunk_cap;
     RcSync *sy = reinterpret_cast<RcSync *>(c.rc_sync);
     int *err = c.rc_err;
-    void *args[] = {&Cp, &wp, &stp, &d, &k, &seed, &rD2, &chosen, &centers, &cm, &sy, &err};
+    // KMPAR_WAIT_CYCLES bounds the grid barrier's wait (fault injection: a budget too
+    // short for the CTAs to meet makes the call return KMPAR_ERR_TIMEOUT)
+    unsigned long long wait = kRcWait;
+    if (const char *wv = std::getenv("KMPAR_WAIT_CYCLES")) {
+        char *end = nullptr;
+        const unsigned long long x = std::strtoull(wv, &end, 10);
+        if (end && *end == 0 && *wv) wait = x;
+    }
+    void *args[] = {&Cp, &CTp, &mpv, &wp, &stp, &d, &k, &seed, &rD2, &chosen, &centers, &gch, &ncap, &gct, &cpcv,
+                    &sy, &err, &wait};
     e = cudaLaunchCooperativeKernel((const void *)recluster_kernel, dim3(G), dim3(kRcThreads), args, smem, c.stream);
     count_launches(1);
     return e;

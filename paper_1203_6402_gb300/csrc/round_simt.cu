@@ -559,13 +559,16 @@ __device__ __forceinline__ int decide_top2(const float *__restrict__ X, int d, c
     }
 }
 
-__global__ void count_fixups_kernel(const int *fix_cnt, int64_t n, DevState *st) {
+// screening statistics of a pass: rows screened, rows the pair screening left
+// undecided, and (after the list pass) rows that needed the exact scan
+__global__ void count_fixups_kernel(const int *fix_cnt, const int *exact_cnt, int64_t n, DevState *st) {
     st->screen_fallback += (unsigned long long)*fix_cnt;
     st->screen_rows += (unsigned long long)n;
+    st->screen_exact += (unsigned long long)(exact_cnt ? *exact_cnt : *fix_cnt);
 }
 
-cudaError_t count_fixups(Ctx &c) {
-    count_fixups_kernel<<<1, 1, 0, c.stream>>>(c.fix_cnt, c.n, c.st);
+cudaError_t count_fixups(Ctx &c, const int *exact_cnt) {
+    count_fixups_kernel<<<1, 1, 0, c.stream>>>(c.fix_cnt, exact_cnt, c.n, c.st);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -605,9 +608,10 @@ struct ScreenBound {
     const float *xnorm;            // ||x'||^2 per point (x' = x - anchor)
     const unsigned int *cmax_bits; // max ||c'|| of the batch
     const DevState *st;            // ROUND: batch range
-    float ep, en;                  // E(x, c) = ep ||x'|| ||c'|| + en (||x'||^2 + ||c'||^2)
+    float ep, en, ec;              // E(x, c) = ep ||x'|| ||c'|| + en (||x'||^2 + ||c'||^2) + ec ||x'|| max ||c'||
     int32_t *fix_rows;
     int *fix_cnt;
+    float *ub;                     // per listed row: exact FP32 upper bound of its deciding distance
 };
 
 // rows whose screening is not certain go to the fix-up list: one atomic per warp
@@ -625,24 +629,39 @@ __device__ __forceinline__ void append_fixups(const ScreenBound &sb, bool fix, i
 // below 2^-17); twice that is allowed for
 constexpr float kKeyTrunc = 1.6e-5f;
 
-// The certainty test.  b1 = the pair's best exact FP32 d^2, v2 = the smallest
-// screened value (s = ||c'||^2 - 2 x'.c') outside the pair.  Any other center c
-// has d^2 = s + ||x'||^2 >= v2 - E(x, c) + ||x'||^2.  A center with ||c'|| >
-// ||x'|| + sqrt(b1 (1 + 2W)) is farther than b1 (1 + 2W) by the triangle
-// inequality; every nearer one has ||c'|| <= ceff, so E(x, c) <= Eo.  If the bound
-// exceeds b1 (1 + 2W), no FP32 value outside the pair can win or fall in the
-// tie window of the best (W = fp32_tie_window covers both FP32 errors).
-__device__ __forceinline__ bool pair_certain(const ScreenBound &sb, float xnorm, float b1, float v2, int d) {
+// The certainty test.  m = the exact FP32 d^2 that decides the row: the pair's
+// best in Lloyd, the nearer of the current center and the pair's best in a round
+// (a center farther than the current one changes nothing unless it falls in the
+// tie window).  v2 = a lower bound of the screened value (s = ||c'||^2 - 2 x'.c')
+// of every center not examined exactly.  Such a center c has d^2 = s + ||x'||^2
+// >= v2 - E(x, c) + ||x'||^2.  A center with ||c'|| > ||x'|| + sqrt(m (1 + 2W)) is
+// farther than m (1 + 2W) by the triangle inequality; every nearer one has
+// ||c'|| <= ceff, so E(x, c) <= Eo.  If the bound exceeds m (1 + 2W), no FP32 value
+// outside the examined centers can win or fall in the tie window of the best
+// (W = fp32_tie_window covers both FP32 errors).
+__device__ __forceinline__ bool bound_certain(const ScreenBound &sb, float xnorm, float m, float v2lo, int d) {
     const float xn = fmaxf(xnorm, 0.f);
     const float X = sqrtf(xn);
     const float cmax = __uint_as_float(*sb.cmax_bits);
     const float W = fp32_tie_window(d);
-    const float lim = fmaxf(b1, 0.f) * (1.f + 2.f * W);
+    const float lim = fmaxf(m, 0.f) * (1.f + 2.f * W);
     const float ceff = fminf(cmax, X + sqrtf(lim));
-    const float Eo = sb.ep * X * ceff + sb.en * (xn + ceff * ceff);
-    // v2 lowered by its key truncation; stays +inf when there is no other center
-    const float v2lo = v2 >= 0.f ? v2 * (1.f - kKeyTrunc) : v2 * (1.f + kKeyTrunc);
+    const float Eo = sb.ep * X * ceff + sb.en * (xn + ceff * ceff) + sb.ec * X * cmax;
     return (v2lo - Eo + xn) > lim + 1e-30f;
+}
+
+// the pair screening's v2 arrives key-truncated: lowered by that truncation (stays
+// +inf when there is no other center)
+__device__ __forceinline__ bool pair_certain(const ScreenBound &sb, float xnorm, float m, float v2, int d) {
+    const float v2lo = v2 >= 0.f ? v2 * (1.f - kKeyTrunc) : v2 * (1.f + kKeyTrunc);
+    return bound_certain(sb, xnorm, m, v2lo, d);
+}
+
+// the distance that decides a row whose nearest screened center has exact FP32
+// value b1 (FLT_MAX: none): see bound_certain
+template <int MODE>
+__device__ __forceinline__ float deciding(const float *D2, int64_t R, float b1) {
+    return MODE == MODE_ROUND ? fminf(D2[R], b1) : b1;
 }
 
 // exact FP32 difference form of one row against one center, both in shared memory
@@ -767,10 +786,15 @@ __global__ void __launch_bounds__(256) refine_kernel(const float *__restrict__ X
         float b1, b2;
         int i1, i2;
         pair_top2(va, j, vb, j + 1, has_b, b1, i1, b2, i2);
-        if (pair_certain(sb, sb.xnorm[R], b1, v2s[R], d))
+        const float m = deciding<MODE>(D2, R, b1);
+        if (pair_certain(sb, sb.xnorm[R], m, v2s[R], d))
             chg = decide_top2<MODE>(X, d, C, R, b1, i1, b2, i2, D2, idx, labels, prev, dmin, fp64_cnt, wide_cnt);
-        else
+        else {
             fix = true;
+            sb.ub[R] = m;
+        }
+    } else if (fix) {
+        sb.ub[R] = deciding<MODE>(D2, R, FLT_MAX);
     }
     append_fixups(sb, fix, R);
     if (MODE == MODE_ASSIGN && changed) {
@@ -886,10 +910,15 @@ __global__ void __launch_bounds__(512) refine_resident_kernel(
             float b1, b2;
             int i1, i2;
             pair_top2(va, j, vb, j + 1, has_b, b1, i1, b2, i2);
-            if (pair_certain(sb, xn, b1, v2, d))
+            const float m = deciding<MODE>(D2, R, b1);
+            if (pair_certain(sb, xn, m, v2, d))
                 chg += decide_top2<MODE>(X, d, C, R, b1, i1, b2, i2, D2, idx, labels, prev, dmin, fp64_cnt, wide_cnt);
-            else
+            else {
                 fix = true;
+                sb.ub[R] = m;
+            }
+        } else if (fix) {
+            sb.ub[R] = deciding<MODE>(D2, R, FLT_MAX);
         }
         append_fixups(sb, fix, R);
         __syncwarp();   // the buffer is refilled two blocks later
@@ -1152,7 +1181,7 @@ int fixup_resident_warps(int cap_rows, int d) {
 size_t fixup_smem_bytes(int d) { return sizeof(float) * (size_t)(kFxRows + 2 * kFxCent) * refine_stride(d); }
 
 cudaError_t launch_fixup(const Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
-                         int *changed, float *dmin) {
+                         int *changed, float *dmin, const int32_t *rows, const int *rows_cnt) {
     // 8-byte center copies need d even and 8-byte aligned rows
     const int c_pairs = (c.d % 2 == 0) && (reinterpret_cast<uintptr_t>(C) % 8 == 0);
     const int cap_rows = mode_round ? c.cap_round : k;
@@ -1161,11 +1190,11 @@ cudaError_t launch_fixup(const Ctx &c, int mode_round, const float *C, int k, in
         const size_t sm = sizeof(float) * ((size_t)cap_rows + rw) * refine_stride(c.d);
         if (mode_round)
             fixup_resident_kernel<MODE_ROUND><<<c.num_sms, 32 * rw, sm, c.stream>>>(
-                c.X, c.d, C, 0, cap_rows, c_pairs, c.st, c.fix_rows, c.fix_cnt, c.D2, c.idx, nullptr, nullptr,
+                c.X, c.d, C, 0, cap_rows, c_pairs, c.st, rows, rows_cnt, c.D2, c.idx, nullptr, nullptr,
                 nullptr, nullptr, &c.st->argmin_fp64, &c.st->argmin_wide);
         else
             fixup_resident_kernel<MODE_ASSIGN><<<c.num_sms, 32 * rw, sm, c.stream>>>(
-                c.X, c.d, C, k, cap_rows, c_pairs, c.st, c.fix_rows, c.fix_cnt, nullptr, nullptr, labels, prev,
+                c.X, c.d, C, k, cap_rows, c_pairs, c.st, rows, rows_cnt, nullptr, nullptr, labels, prev,
                 changed, dmin, &c.st->argmin_fp64, &c.st->argmin_wide);
         count_launches(1);
         return cudaGetLastError();
@@ -1174,11 +1203,11 @@ cudaError_t launch_fixup(const Ctx &c, int mode_round, const float *C, int k, in
     const size_t sm = fixup_smem_bytes(c.d);
     const int pairs = c_pairs;
     if (mode_round)
-        fixup_kernel<MODE_ROUND><<<grid, 256, sm, c.stream>>>(c.X, c.d, C, 0, pairs, c.st, c.fix_rows, c.fix_cnt, c.D2,
+        fixup_kernel<MODE_ROUND><<<grid, 256, sm, c.stream>>>(c.X, c.d, C, 0, pairs, c.st, rows, rows_cnt, c.D2,
                                                               c.idx, nullptr, nullptr, nullptr, nullptr,
                                                               &c.st->argmin_fp64, &c.st->argmin_wide);
     else
-        fixup_kernel<MODE_ASSIGN><<<grid, 256, sm, c.stream>>>(c.X, c.d, C, k, pairs, c.st, c.fix_rows, c.fix_cnt,
+        fixup_kernel<MODE_ASSIGN><<<grid, 256, sm, c.stream>>>(c.X, c.d, C, k, pairs, c.st, rows, rows_cnt,
                                                                nullptr, nullptr, labels, prev, changed, dmin,
                                                                &c.st->argmin_fp64, &c.st->argmin_wide);
     count_launches(1);
@@ -1211,30 +1240,125 @@ cudaError_t configure_refine_kernels() {
                                 200 * 1024);
 }
 
+// exact FP32 difference form of one row against one center, both in global memory:
+// the same chain as dist2_fp32 (ascending coordinates, one rounded subtraction and
+// one FMA each), with 16-byte loads when both rows are 16-byte aligned
+__device__ __forceinline__ float dist2_fp32_v4(const float *__restrict__ x, const float *__restrict__ c, int d) {
+    if ((d & 3) == 0 && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(c)) & 15u) == 0) {
+        const float4 *x4 = reinterpret_cast<const float4 *>(x);
+        const float4 *c4 = reinterpret_cast<const float4 *>(c);
+        float s = 0.f;
+        for (int p = 0; p < (d >> 2); ++p) {
+            const float4 a = __ldg(x4 + p), b = __ldg(c4 + p);
+            float t = __fsub_rn(a.x, b.x);
+            s = __fmaf_rn(t, t, s);
+            t = __fsub_rn(a.y, b.y);
+            s = __fmaf_rn(t, t, s);
+            t = __fsub_rn(a.z, b.z);
+            s = __fmaf_rn(t, t, s);
+            t = __fsub_rn(a.w, b.w);
+            s = __fmaf_rn(t, t, s);
+        }
+        return s;
+    }
+    return dist2_fp32(x, c, d);
+}
+
+// Rows the list pass screened (rows[i], i < *rows_cnt): one warp per row.  The
+// row's four column groups listed their centers whose screened value is at most
+// thr[i]; lane l computes listed center l in the exact FP32 difference form
+// (bit-identical to dist2_fp32), a lexicographic top-2 is merged across the warp,
+// and the row is certain when no group overflowed its slots and every center
+// left off the list (screened value above thr[i]) is, by the screening bound,
+// beyond the tie window of the deciding distance (bound_certain).  Certain rows
+// take decide_top2, the others go to the exact scan's list (rows2).
+template <int MODE>
+__global__ void __launch_bounds__(256) refine_list_kernel(
+    const float *__restrict__ X, int d, const float *__restrict__ C, int c_cnt, const int32_t *__restrict__ rows,
+    const int *rows_cnt, const int32_t *__restrict__ lst, const int32_t *__restrict__ lcnt,
+    const float *__restrict__ thr, ScreenBound sb, int32_t *rows2, int *cnt2, float *D2, int32_t *idx,
+    int32_t *labels, const int32_t *prev, int *changed, float *dmin, unsigned long long *fp64_cnt,
+    unsigned long long *wide_cnt) {
+    constexpr int S = tc::kListSlots;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nrows = *rows_cnt;
+    const int begin = MODE == MODE_ROUND ? sb.st->batch_begin : 0;
+    const int cnt = MODE == MODE_ROUND ? sb.st->batch_cnt : c_cnt;
+    const float FMAX = FLT_MAX;
+    for (int64_t i = gw; i < nrows; i += W) {   // uniform per warp
+        const int64_t R = rows[i];
+        const int cg = lane < 4 ? lcnt[i * 4 + lane] : 0;
+        const bool over = __any_sync(0xffffffffu, cg > S);
+        const int c0 = __shfl_sync(0xffffffffu, cg, 0), c1 = __shfl_sync(0xffffffffu, cg, 1);
+        const int c2 = __shfl_sync(0xffffffffu, cg, 2), c3 = __shfl_sync(0xffffffffu, cg, 3);
+        float b1 = FMAX, b2 = FMAX;
+        int i1 = INT_MAX, i2 = INT_MAX;
+        if (!over) {
+            int g = -1, sidx = lane;
+            if (sidx < c0) g = 0;
+            else if ((sidx -= c0) < c1) g = 1;
+            else if ((sidx -= c1) < c2) g = 2;
+            else if ((sidx -= c2) < c3) g = 3;
+            if (g >= 0) {
+                const int col = lst[(i * 4 + g) * S + sidx];
+                if (col >= 0 && col < cnt) {
+                    const int j = begin + col;
+                    b1 = dist2_fp32_v4(X + R * d, C + (int64_t)j * d, d);
+                    i1 = j;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float u1 = __shfl_xor_sync(0xffffffffu, b1, o), u2 = __shfl_xor_sync(0xffffffffu, b2, o);
+                const int j1 = __shfl_xor_sync(0xffffffffu, i1, o), j2 = __shfl_xor_sync(0xffffffffu, i2, o);
+                top2_merge(b1, i1, b2, i2, u1, j1, u2, j2);
+            }
+        }
+        if (lane == 0) {
+            bool certain = false;
+            if (!over) {
+                const float m = deciding<MODE>(D2, R, i1 != INT_MAX ? b1 : FMAX);
+                certain = m < FMAX && bound_certain(sb, sb.xnorm[R], m, thr[i], d);
+            }
+            if (certain) {
+                if (i2 == INT_MAX) { i2 = -1; b2 = FMAX; }
+                if (decide_top2<MODE>(X, d, C, R, b1, i1, b2, i2, D2, idx, labels, prev, dmin, fp64_cnt, wide_cnt) &&
+                    changed)
+                    atomicAdd(changed, 1);
+            } else {
+                rows2[atomicAdd(cnt2, 1)] = (int32_t)R;
+            }
+        }
+    }
+}
+
 cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
                            int *changed, float *dmin, int timing_cls) {
     cudaError_t e;
-    const int split = c.precision == KMPAR_BF16X3 ? 1 : 0;
-    if ((e = tc::launch_prep_centers(C, c.d, split, c.st, k, mode_round, mode_round ? c.cap_round : k, c.tc_anchor,
-                                     c.tc_img, c.tc_cmax, c.stream)) != cudaSuccess)
+    const int fmt = c.tc_fmt;
+    if ((e = tc::launch_prep_centers(C, c.d, fmt, c.st, k, mode_round, mode_round ? c.cap_round : k, c.tc_anchor,
+                                     c.tc_img, c.tc_ncol, c.tc_tscale, c.tc_cmax, c.stream)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(c.fix_cnt, 0, sizeof(int), c.stream)) != cudaSuccess) return e;
     // rows the screening does not reach (e.g. an empty batch) must not see a stale winner
     if ((e = cudaMemsetAsync(c.cand1, 0xFF, sizeof(int32_t) * (size_t)c.n, c.stream)) != cudaSuccess) return e;
     tc::TcParams p{};
-    p.X = c.X; p.n = c.n; p.d = c.d; p.split = split;
-    p.ximg = c.tc_ximg; p.xnorm = c.tc_xnorm;
-    p.Cf = C; p.cnt = k; p.st = c.st; p.bimg = c.tc_img; p.cmax_bits = c.tc_cmax;
+    p.X = c.X; p.n = c.n; p.d = c.d; p.fmt = fmt;
+    p.ximg = c.tc_ximg; p.xnorm = c.tc_xnorm; p.xscale = c.tc_xscale;
+    p.Cf = C; p.cnt = k; p.st = c.st; p.bimg = c.tc_img; p.ncol = c.tc_ncol; p.tscale = c.tc_tscale;
+    p.cmax_bits = c.tc_cmax;
     p.cand1 = c.cand1; p.v2 = c.tc_v2; p.fix_rows = c.fix_rows; p.fix_cnt = c.fix_cnt;
     p.fp64_cnt = &c.st->argmin_fp64; p.err = c.tc_err;
     cudaEvent_t ev = nullptr;
     if ((e = timing_begin(c, &ev)) != cudaSuccess) return e;
-    if ((e = tc::launch_nearest_tc(p, mode_round, c.num_sms, c.stream)) != cudaSuccess) return e;
+    if ((e = tc::launch_nearest_tc(p, mode_round, tc::EPI_PAIR, c.num_sms, c.stream)) != cudaSuccess) return e;
     if ((e = timing_end(c, ev, timing_cls)) != cudaSuccess) return e;
     ScreenBound sb{};
     sb.xnorm = c.tc_xnorm; sb.cmax_bits = c.tc_cmax; sb.st = c.st;
-    sb.fix_rows = c.fix_rows; sb.fix_cnt = c.fix_cnt;
-    tc::tc_bound(c.d, split, &sb.ep, &sb.en);
+    sb.fix_rows = c.fix_rows; sb.fix_cnt = c.fix_cnt; sb.ub = c.tc_ub;
+    tc::tc_bound(c.d, fmt, &sb.ep, &sb.en, &sb.ec);
     const int cap_rows = mode_round ? c.cap_round : k;
     const ResidentPlan rp = resident_plan(cap_rows, c.d);
     if (rp.parts > 0) {
@@ -1255,24 +1379,53 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
             count_launches(1);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        if ((e = count_fixups(c)) != cudaSuccess) return e;
-        return launch_fixup(c, mode_round, C, k, labels, prev, changed, dmin);
+    } else {
+        const int rthreads = 32 * refine_warps(c.d);
+        const int grid = (int)((c.n + rthreads - 1) / rthreads);
+        const size_t rsm = refine_smem_bytes(c.d);
+        if (mode_round)
+            refine_kernel<MODE_ROUND><<<grid, rthreads, rsm, c.stream>>>(c.X, c.n, c.d, C, 0, c.cand1, c.tc_v2, sb,
+                                                                         c.D2, c.idx, nullptr, nullptr, nullptr,
+                                                                         nullptr, &c.st->argmin_fp64,
+                                                                         &c.st->argmin_wide);
+        else
+            refine_kernel<MODE_ASSIGN><<<grid, rthreads, rsm, c.stream>>>(c.X, c.n, c.d, C, k, c.cand1, c.tc_v2, sb,
+                                                                          nullptr, nullptr, labels, prev, changed,
+                                                                          dmin, &c.st->argmin_fp64,
+                                                                          &c.st->argmin_wide);
+        count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const int rthreads = 32 * refine_warps(c.d);
-    const int grid = (int)((c.n + rthreads - 1) / rthreads);
-    const size_t rsm = refine_smem_bytes(c.d);
+    if (!c.tc_list) {
+        if ((e = count_fixups(c, nullptr)) != cudaSuccess) return e;
+        return launch_fixup(c, mode_round, C, k, labels, prev, changed, dmin, c.fix_rows, c.fix_cnt);
+    }
+    // rows the pair screening left undecided: a second screening of just those rows
+    // that lists every center within twice the screening bound of the row's deciding
+    // distance, the exact FP32 form of the listed centers, and the exact scan only
+    // for rows whose lists overflowed or stayed uncertain
+    if ((e = cudaMemsetAsync(c.fix_cnt2, 0, sizeof(int), c.stream)) != cudaSuccess) return e;
+    if ((e = tc::launch_gather_rows(c.tc_ximg, c.tc_xscale, c.d, fmt, c.fix_rows, c.fix_cnt, c.tc_ub, c.tc_xnorm,
+                                    c.tc_cmax, sb.ep, sb.en, sb.ec, c.tc_cimg, c.tc_cscale, c.tc_thr,
+                                    c.num_sms * 8, c.stream)) != cudaSuccess)
+        return e;
+    tc::TcParams pl = p;
+    pl.ximg = c.tc_cimg; pl.xscale = c.tc_cscale;
+    pl.nrows_dev = c.fix_cnt; pl.thr = c.tc_thr; pl.lst = c.tc_lst; pl.lcnt = c.tc_lcnt;
+    if ((e = tc::launch_nearest_tc(pl, mode_round, tc::EPI_LIST, c.num_sms, c.stream)) != cudaSuccess) return e;
+    const int lgrid = c.num_sms * 8;
     if (mode_round)
-        refine_kernel<MODE_ROUND><<<grid, rthreads, rsm, c.stream>>>(c.X, c.n, c.d, C, 0, c.cand1, c.tc_v2, sb, c.D2,
-                                                                     c.idx, nullptr, nullptr, nullptr, nullptr,
-                                                                     &c.st->argmin_fp64, &c.st->argmin_wide);
+        refine_list_kernel<MODE_ROUND><<<lgrid, 256, 0, c.stream>>>(
+            c.X, c.d, C, 0, c.fix_rows, c.fix_cnt, c.tc_lst, c.tc_lcnt, c.tc_thr, sb, c.fix_rows2, c.fix_cnt2, c.D2,
+            c.idx, nullptr, nullptr, nullptr, nullptr, &c.st->argmin_fp64, &c.st->argmin_wide);
     else
-        refine_kernel<MODE_ASSIGN><<<grid, rthreads, rsm, c.stream>>>(c.X, c.n, c.d, C, k, c.cand1, c.tc_v2, sb,
-                                                                      nullptr, nullptr, labels, prev, changed, dmin,
-                                                                      &c.st->argmin_fp64, &c.st->argmin_wide);
+        refine_list_kernel<MODE_ASSIGN><<<lgrid, 256, 0, c.stream>>>(
+            c.X, c.d, C, k, c.fix_rows, c.fix_cnt, c.tc_lst, c.tc_lcnt, c.tc_thr, sb, c.fix_rows2, c.fix_cnt2,
+            nullptr, nullptr, labels, prev, changed, dmin, &c.st->argmin_fp64, &c.st->argmin_wide);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = count_fixups(c)) != cudaSuccess) return e;
-    return launch_fixup(c, mode_round, C, k, labels, prev, changed, dmin);
+    if ((e = count_fixups(c, c.fix_cnt2)) != cudaSuccess) return e;
+    return launch_fixup(c, mode_round, C, k, labels, prev, changed, dmin, c.fix_rows2, c.fix_cnt2);
 }
 
 }  // namespace kmp

@@ -16,11 +16,11 @@ LIB_PATH = os.path.join(_HERE, "_build", "libkmpar.so")
 
 KMPAR_OK, KMPAR_ERR_ARG, KMPAR_ERR_CUDA, KMPAR_ERR_OOM, KMPAR_ERR_CAPACITY = 0, 1, 2, 3, 4
 KMPAR_ERR_TIMEOUT, KMPAR_ERR_STATE, KMPAR_WARN_FEW_CANDIDATES, KMPAR_ERR_UNSUPPORTED = 5, 6, 7, 8
-KMPAR_FP32, KMPAR_BF16, KMPAR_BF16X3 = 0, 1, 2
+KMPAR_FP32, KMPAR_BF16, KMPAR_BF16X3, KMPAR_FP8E4M3 = 0, 1, 2, 3
 KMPAR_HOST_BUFFERS, KMPAR_EXACT_SAMPLING = 1, 2
 KMPAR_SAMPLE_BERNOULLI, KMPAR_SAMPLE_EXACT = 0, 1
 SAMPLINGS = {"bernoulli": KMPAR_SAMPLE_BERNOULLI, "exact": KMPAR_SAMPLE_EXACT}
-PRECISIONS = {"fp32": KMPAR_FP32, "bf16": KMPAR_BF16, "bf16x3": KMPAR_BF16X3}
+PRECISIONS = {"fp32": KMPAR_FP32, "bf16": KMPAR_BF16, "bf16x3": KMPAR_BF16X3, "fp8": KMPAR_FP8E4M3}
 
 EXPORTED = ["kmpar_init", "kmpar_round", "kmpar_weight", "kmpar_recluster", "kmpar_lloyd", "kmpar_cost",
             "kmpar_fit", "kmpar_state", "kmpar_get_stats", "kmpar_uniforms", "kmpar_set_timing",
@@ -39,7 +39,8 @@ class kmpar_stats(ctypes.Structure):
                 ("recluster_near", ctypes.c_int64),
                 ("capacity_overflow", ctypes.c_int32), ("recluster_warn", ctypes.c_int32),
                 ("kernel_ms", ctypes.c_double * 2), ("kernel_launches", ctypes.c_int64 * 2),
-                ("screen_rows", ctypes.c_int64), ("screen_fallback", ctypes.c_int64)]
+                ("screen_rows", ctypes.c_int64), ("screen_fallback", ctypes.c_int64),
+                ("screen_exact", ctypes.c_int64)]
 
     def to_dict(self) -> dict:
         r = self.rounds_done
@@ -50,7 +51,7 @@ class kmpar_stats(ctypes.Structure):
                     recluster_near=self.recluster_near, capacity_overflow=self.capacity_overflow,
                     recluster_warn=self.recluster_warn, kernel_ms=list(self.kernel_ms),
                     kernel_launches=list(self.kernel_launches), screen_rows=self.screen_rows,
-                    screen_fallback=self.screen_fallback)
+                    screen_fallback=self.screen_fallback, screen_exact=self.screen_exact)
 
 
 class KmparError(RuntimeError):

@@ -94,6 +94,6 @@ def test_binding_constants_match_the_header():
     for name, value in consts.items():
         assert getattr(kmpar, name) == value, name
     assert kmpar.PRECISIONS == {"fp32": consts["KMPAR_FP32"], "bf16": consts["KMPAR_BF16"],
-                                "bf16x3": consts["KMPAR_BF16X3"]}
+                                "bf16x3": consts["KMPAR_BF16X3"], "fp8": consts["KMPAR_FP8E4M3"]}
     assert kmpar.SAMPLINGS == {"bernoulli": consts["KMPAR_SAMPLE_BERNOULLI"],
                                "exact": consts["KMPAR_SAMPLE_EXACT"]}

@@ -44,3 +44,38 @@ def test_dist_evals_of_a_step():
     total, parts = bench.count_dist_evals(10, 7, stats, 3)
     assert parts == {"init": 10, "rounds": 10 * 5000, "recluster": 7 * 5001, "lloyd": 4 * 10 * 7}
     assert total == sum(parts.values())
+
+
+def test_traffic_record_is_used_only_for_the_captured_source(tmp_path, monkeypatch):
+    """roofline.traffic comes from a committed ncu summary row
+    (kernel | workload | precision | bytes per launch | source sha16) and is
+    dropped once the kernel source no longer has the captured hash."""
+    import hashlib
+    src = tmp_path / "paper_1203_6402_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "nearest_tc.cu").write_bytes(b"kernel v1")
+    sha = hashlib.sha256(b"kernel v1").hexdigest()[:16]
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.md").write_text(
+        "| kernel | workload | precision | bytes | sha |\n|---|---|---|---|---|\n"
+        f"| tc::nearest_tc_kernel (assign) | w1 | bf16 | 1.5e9 | {sha} |\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_record("tc::nearest_tc_kernel (assign)", "w1", "bf16") == (1.5e9, sha)
+    assert bench.traffic_record("tc::nearest_tc_kernel (round)", "w1", "bf16") == (None, None)
+    (src / "nearest_tc.cu").write_bytes(b"kernel v2")
+    assert bench.traffic_record("tc::nearest_tc_kernel (assign)", "w1", "bf16") == (None, sha)
+
+
+def test_oracle_sample_keeps_points_per_cluster():
+    import argparse
+    a = argparse.Namespace(workload="gmm_n10M_d128_k10000", n=0, ell_factor=0, cpu_sample_n=50000,
+                           cpu_lloyd_iters=10)
+    assert bench.oracle_sample(a) == dict(n=50000, k=50, ell=100.0, rounds=5, lloyd=10)
+    a = argparse.Namespace(workload="gmm_n10k_d15_k50", n=0, ell_factor=0, cpu_sample_n=50000,
+                           cpu_lloyd_iters=10)
+    assert bench.oracle_sample(a) == dict(n=10000, k=50, ell=100.0, rounds=5, lloyd=10)
+
+
+def test_default_precision_by_dimension():
+    assert bench.default_precision("kdd_n1M_d42_k500") == "bf16x3"
+    assert bench.default_precision("gmm_n10M_d128_k10000") == "bf16"

@@ -140,6 +140,9 @@ CASES = [
     ("d130_generic", lambda: datagen.gauss_mixture(777, 130, 6, 4.0, seed=4), 6, 12.0, 3, 6),
     ("d128", lambda: datagen.gauss_mixture(1500, 128, 12, 100.0, seed=5), 12, 24.0, 5, 7),
     ("d42_many_centers", lambda: datagen.kdd_like(2000, seed=6), 64, 300.0, 3, 8),
+    # the GAUSSMIXTURE configuration exactly: n = 10^4, d = 15, 50 centers ~ N(0, 10 I),
+    # k = 50, l = 2k, r = 5, Lloyd to convergence within 100 updates
+    ("gmm_config_n10k_d15_k50", lambda: datagen.make("gmm_n10k_d15_k50", seed=1000), 50, 100.0, 5, 7),
 ]
 
 
@@ -155,10 +158,18 @@ TC_CASES = [c for c in CASES if c[0] != "d130_generic"] + [
     ("kdd_ragged_3001", lambda: datagen.kdd_like(3001, seed=14), 40, 80.0, 4, 10),
     # round batches of ~1,500 candidates: the resident refine runs in three slices
     ("kdd_sliced_batches", lambda: datagen.kdd_like(6000, seed=16), 100, 1500.0, 2, 11),
+    # 321 row tiles: every persistent CTA of the screening pass takes two or three A
+    # tiles, so the TMEM buffers, the A ring and the L2 prefetch wrap around
+    ("kdd_n41k_multi_tile_per_cta", lambda: datagen.kdd_like(41000, seed=17), 50, 100.0, 3, 12),
+    # the 1e7 x 128 configuration's shape at 1/500 of its size (1,000 points per
+    # cluster, centers ~ N(0, 100 I), l = 2k): a round batch holds several candidates
+    # of one cluster, closer together than the BF16/FP8 screening bound, so many rows
+    # go through the list pass
+    ("gmm_d128_dense_clusters", lambda: datagen.gauss_mixture(20000, 128, 20, 100.0, seed=18), 20, 40.0, 5, 13),
 ]
 
 
-@pytest.mark.parametrize("precision", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("precision", ["bf16x3", "bf16", "fp8"])
 @pytest.mark.parametrize("name,mk,k,ell,rounds,seed", TC_CASES, ids=[c[0] for c in TC_CASES])
 def test_parity_tensor_screening(km, orc, name, mk, k, ell, rounds, seed, precision):
     """tcgen05 screening + exact refine: same decisions as the oracle (and the FP32 path)."""
@@ -176,6 +187,11 @@ def test_parity_tensor_screening(km, orc, name, mk, k, ell, rounds, seed, precis
     if precision == "bf16x3" and name.startswith("gmm"):
         # well-separated data: nearly every row is decided by the screening alone
         assert st["screen_fallback"] <= 0.05 * st["screen_rows"], st
+    assert st["screen_exact"] <= st["screen_fallback"]
+    if name == "gmm_d128_dense_clusters":
+        # rows left undecided by the pair screening were there, and the list pass
+        # settled most of them without the exact scan
+        assert st["screen_fallback"] > 0 and st["screen_exact"] < 0.5 * st["screen_fallback"], st
 
 
 EXACT_CASES = [
@@ -221,7 +237,7 @@ def test_tensor_paths_match_fp32_path(km):
     X = datagen.kdd_like(20000, seed=15)
     Xd = _dev(X)
     res = {}
-    for prec in ("fp32", "bf16x3", "bf16"):
+    for prec in ("fp32", "bf16x3", "bf16", "fp8"):
         g = km.KMeansPar(Xd, 64, 128.0, 5, 3, precision=prec)
         for r in range(1, 6):
             g.round(r)
@@ -231,16 +247,41 @@ def test_tensor_paths_match_fp32_path(km):
         res[prec] = (cand.cpu().numpy(), w.cpu().numpy(), C.cpu().numpy(), out["labels"].cpu().numpy(),
                      out["final_cost"], g.stats())
         g.close()
-    for prec in ("bf16x3", "bf16"):
+    for prec in ("bf16x3", "bf16", "fp8"):
         for a, b in zip(res["fp32"][:4], res[prec][:4]):
             assert np.array_equal(a, b), prec
         assert res["fp32"][4] == res[prec][4]
 
 
+def test_tensor_paths_match_fp32_path_wide_rows(km):
+    """d = 128 (BF16 with the norms added in the epilogue, FP8 e4m3): dense
+    clusters send rows through the list pass; every decision equals the FP32 path's."""
+    X = datagen.gauss_mixture(60000, 128, 60, 100.0, seed=19)
+    Xd = _dev(X)
+    res = {}
+    for prec in ("fp32", "bf16", "fp8"):
+        g = km.KMeansPar(Xd, 60, 120.0, 5, 4, precision=prec)
+        for r in range(1, 6):
+            g.round(r)
+        D2, idx = g.state()
+        cand, w = g.candidates()
+        C, _ = g.recluster()
+        out = g.lloyd(C, 10)
+        res[prec] = (cand.cpu().numpy(), w.cpu().numpy(), D2.cpu().numpy(), idx.cpu().numpy(), C.cpu().numpy(),
+                     out["labels"].cpu().numpy(), out["final_cost"], g.stats())
+        g.close()
+    for prec in ("bf16", "fp8"):
+        for a, b in zip(res["fp32"][:6], res[prec][:6]):
+            assert np.array_equal(a, b), prec
+        assert res["fp32"][6] == res[prec][6]
+        st = res[prec][7]
+        assert st["screen_fallback"] > 0 and st["screen_exact"] < st["screen_fallback"], (prec, st)
+
+
 def test_tensor_precision_rejects_large_d(km):
     # BF16 carries d + 2 K columns, split BF16 3d + 2; three 64-column atoms are built
     X = _dev(datagen.uniform_box(200, 200, seed=1))
-    for prec in ("bf16", "bf16x3"):
+    for prec in ("bf16", "bf16x3", "fp8"):
         with pytest.raises(km.KmparError) as e:
             km.KMeansPar(X, 4, 8.0, 2, 0, precision=prec)
         assert e.value.status == km.KMPAR_ERR_UNSUPPORTED

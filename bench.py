@@ -170,7 +170,7 @@ def traffic_record(kernel: str, workload: str, precision: str):
     while the kernel's source is the one that was captured (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.md")
-    src = os.path.join(ROOT, "paper_1203_6402_gb300", "csrc", "nearest_tc.cu")
+    src = os.path.join(ROOT, "paper_1203_6402_gb300", "csrc", "nearest_tc_kernel.cuh")
     if not (os.path.exists(path) and os.path.exists(src)):
         return None, None
     with open(src, "rb") as f:
@@ -185,6 +185,126 @@ def traffic_record(kernel: str, workload: str, precision: str):
                     continue
                 return (val, parts[4]) if parts[4] == sha else (None, parts[4])
     return None, None
+
+
+def run_batched(args, rank, world):
+    """The batched configuration: 4,096 independent GAUSSMIXTURE problems (n and k
+    log-uniform in [1e3, 2e5] and [16, 256], d in {32, 64, 128}, l = 2k, r = 5,
+    10 Lloyd updates) in one kmpar_batch_run call per step.  The points of each
+    problem are drawn on the device from the problem's own seed (same recipe as
+    datagen.gauss_mixture; the full batch is ~46 GB)."""
+    import torch
+    from paper_1203_6402_gb300 import datagen
+    from paper_1203_6402_gb300 import kmpar as km
+
+    km.load()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    count = args.batch_count
+    probs = datagen.batched_problems(count, seed=1000 + rank)
+    total = sum(p["n"] * p["d"] for p in probs)
+    X = torch.empty(total, dtype=torch.float32, device=dev)
+    gen = torch.Generator(device=dev)
+    for p in probs:
+        gen.manual_seed(p["data_seed"])
+        n, d, k = p["n"], p["d"], p["k"]
+        cen = torch.randn(k, d, generator=gen, device=dev) * (10.0 ** 0.5)
+        comp = torch.randint(0, k, (n,), generator=gen, device=dev)
+        X[p["x_offset"]: p["x_offset"] + n * d].view(n, d).copy_(cen[comp] + torch.randn(n, d, generator=gen,
+                                                                                           device=dev))
+    C = torch.empty(sum(p["k"] * p["d"] for p in probs), dtype=torch.float32, device=dev)
+    L = torch.empty(sum(p["n"] for p in probs), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        st, res = km.kmpar_batch_run(X.data_ptr(), probs, C.data_ptr(), L.data_ptr(), stream=stream.cuda_stream)
+        assert st in (km.KMPAR_OK, km.KMPAR_WARN_FEW_CANDIDATES), st
+        return res
+
+    def evals_of(res):
+        tot = 0
+        for p, r in zip(probs, res):
+            n, k = p["n"], p["k"]
+            tot += n + n * (r["m"] - 1) + k * r["m"] + (r["iters"] + 1) * n * k
+        return tot
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+    evals = evals_of(res)
+    barrier(world)
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = km.kmpar_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    tot = 0
+    for _ in range(args.steps):
+        tot += evals_of(step())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = km.kmpar_launch_count() - l0
+    clocks = sampler.stop()
+    ms = allreduce_max(ev0.elapsed_time(ev1), world)
+    value = allreduce_sum(float(tot), world) / (ms / 1e3)
+    # end to end: points from pinned host memory, centers and labels back, every step
+    e2e = None
+    try:
+        Xh = X.cpu().pin_memory()
+        Ch = torch.empty(C.numel(), dtype=torch.float32).pin_memory()
+        Lh = torch.empty(L.numel(), dtype=torch.int32).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 3))
+        for _ in range(e2e_steps):
+            X.copy_(Xh, non_blocking=True)
+            step()
+            Ch.copy_(C, non_blocking=True)
+            Lh.copy_(L, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_s = allreduce_max(time.perf_counter() - t0, world)
+        e2e = {"value": allreduce_sum(float(evals * e2e_steps), world) / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": total * 4, "d2h_bytes_per_step": C.numel() * 4 + L.numel() * 4,
+               "steps": e2e_steps, "path": "torch copies around kmpar_batch_run (device pointers)"}
+        del Xh, Ch, Lh
+    except RuntimeError as exc:   # pinned host memory for the whole batch may not be available
+        e2e = {"value": None, "unit": UNIT, "note": f"no end-to-end figure: {exc}"[:200]}
+    # FP32 CUDA-core issue roofline: 2 instructions (sub, fma) per padded coordinate
+    peaks = load_peaks()
+    clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    instr = 0.0
+    for p, r in zip(probs, res):
+        dp = 32 if p["d"] <= 32 else (64 if p["d"] <= 64 else 128)
+        n, k = p["n"], p["k"]
+        instr += 2.0 * dp * (n + n * (r["m"] - 1) + k * r["m"] + (r["iters"] + 1) * n * k)
+    achieved = instr / (ms / args.steps / 1e3) / 1e12
+    peak = FP32_LANES_PER_SM * SMS * clk / 1e12
+    xbytes = total * 4
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (exact difference form on CUDA cores), f64 sums", "data": "synthetic",
+        "config": {"workload": (f"batched: {count} GAUSSMIXTURE problems, n log-uniform [1e3, 2e5], "
+                                f"d in {{32, 64, 128}}, k log-uniform [16, 256], l = 2k, r = 5, 10 Lloyd updates; "
+                                f"one kmpar_batch_run per step (one block per problem, largest first)"),
+                   "sum_n": int(sum(p["n"] for p in probs)), "x_gb": xbytes / 1e9,
+                   "parallelism": f"replicas x{world}", "l2": f"inputs larger than L2 (X {xbytes / 1e9:.1f} GB)"},
+        "dist_evals_per_step": evals, "gpu_launches": int(launches), "e2e": e2e,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s (FP32 issue)",
+                     "frac": achieved / peak, "traffic": None, "kernel": "batch_kernel (all problems)",
+                     "peak_source": f"derived: 128 FP32 lanes x 152 SMs x {peaks.get('sm_max_mhz', 2070.0)} MHz",
+                     "hbm": {"gbs_min": xbytes * 16 / (ms / args.steps / 1e3) / 1e9,
+                             "note": "X read once per pass, 16 passes (init, 5 rounds, 10+1 Lloyd)",
+                             "peak_gbs": peaks.get("hbm_gbs")}},
+        "clocks": clocks,
+        "problems": {"status_counts": {str(s): sum(1 for r in res if r["status"] == s) for s in
+                                       sorted(set(r["status"] for r in res))},
+                     "lloyd_iters_mean": statistics.mean(r["iters"] for r in res)},
+        **({"cpu_baseline": cpu_baseline_batched(args)} if rank == 0 and world == 1 and not args.no_cpu_baseline
+           else {}),
+    }
 
 
 def run_ours(args, rank, world):
@@ -428,6 +548,49 @@ def _sample_text(args, smp, threads):
             f"r={smp['rounds']}, Lloyd capped at {smp['lloyd']} updates")
 
 
+def _oracle_batched_job(argv):
+    """Child process: the oracle on a seeded subset of batched problems; (seconds, dist-evals)."""
+    root, seed, count, n_hi = argv
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    from oracle import oracle
+    from paper_1203_6402_gb300 import datagen
+    probs = datagen.batched_problems(count, seed=seed, n_hi=n_hi)
+    X = datagen.batched_points(probs)
+    t0 = time.perf_counter()
+    ev = 0
+    for p in probs:
+        n, d, k = p["n"], p["d"], p["k"]
+        Xi = X[p["x_offset"]: p["x_offset"] + n * d].reshape(n, d)
+        par = oracle.kmeans_par(Xi, k, p["ell"], p["rounds"], seed=p["seed"])
+        _, _, it, _, _, _ = oracle.lloyd(Xi, par.seed_centers, p["max_iter"])
+        ev += n + n * (len(par.cand) - 1) + k * len(par.cand) + (it + 1) * n * k
+    return time.perf_counter() - t0, ev
+
+
+def cpu_baseline_batched(args, count=12, n_hi=20000):
+    import multiprocessing as mp
+    from oracle import oracle
+    oracle.build()
+    dt, ev = _oracle_batched_job((ROOT, 1000, count, n_hi))
+    text = (f"FP64 C oracle, {{}}: {count} problems of the batched recipe with n capped at {n_hi} "
+            f"(n log-uniform [1e3, {n_hi}], d in {{{{32, 64, 128}}}}, k log-uniform [16, 256], l = 2k, r = 5, "
+            f"10 Lloyd updates)")
+    res = {"value": ev / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": dt,
+           "sample": text.format("1 thread")}
+    cores = os.cpu_count() or 1
+    if cores > 1 and not args.no_cpu_all_cores:
+        ctx = mp.get_context("spawn")
+        t0 = time.perf_counter()
+        with ctx.Pool(cores) as pool:
+            outs = pool.map(_oracle_batched_job, [(ROOT, 2000 + j, count, n_hi) for j in range(cores)])
+        wall = time.perf_counter() - t0
+        res["all_cores"] = {"value": sum(o[1] for o in outs) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "seconds": wall, "sample": text.format(f"{cores} processes x 1 thread") +
+                            ", one seeded subset per process; wall time includes process start-up"}
+    return res
+
+
 def cpu_baseline(args):
     """The oracle as it stands: one process (1 thread), then one process per host
     core each on its own seeded sample (all cores busy; it is single-threaded)."""
@@ -458,6 +621,22 @@ def cpu_baseline(args):
 def run_reference(args, rank, world):
     from oracle import oracle
     oracle.build()
+    if args.workload == "batched":
+        for _ in range(args.warmup):
+            _oracle_batched_job((ROOT, 1000, 4, 20000))
+        tot_t, tot_e = 0.0, 0
+        for _ in range(args.steps):
+            dt, e = _oracle_batched_job((ROOT, 1000, 4, 20000))
+            tot_t += dt
+            tot_e += e
+        value = tot_e / tot_t
+        sample = ("FP64 C oracle, 1 thread, per step: 4 problems of the batched recipe with n capped at 20000")
+        return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": "batched (bounded sample)", "precision": "fp64"},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     smp = oracle_sample(argparse.Namespace(**{**vars(args), "cpu_sample_n": args.ref_sample_n}))
     for _ in range(args.warmup):
         _oracle_job((ROOT, args.workload, smp, 1000, 7, args.sampling))
@@ -531,9 +710,10 @@ def main():
     ap.add_argument("--no-cpu-all-cores", action="store_true")
     ap.add_argument("--fp32-steps", type=int, default=1, help="timed steps of the FP32 comparison arm (0: off)")
     ap.add_argument("--fp32-warmup", type=int, default=1)
+    ap.add_argument("--batch-count", type=int, default=4096, help="problems of the batched workload")
     args = ap.parse_args()
     if args.precision is None:
-        args.precision = default_precision(args.workload)
+        args.precision = "fp32" if args.workload == "batched" else default_precision(args.workload)
     if args.warmup < 3:
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -547,7 +727,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    res = run_ours(args, rank, world)
+    res = run_batched(args, rank, world) if args.workload == "batched" else run_ours(args, rank, world)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:

@@ -28,7 +28,8 @@
  *
  * Fault injection (environment variables, read when the limit applies; for
  * tests of the error paths, none of them is needed in normal use):
- *   KMPAR_ROUND_CAPACITY   lowers the per-round draw capacity (read by kmpar_init)
+ *   KMPAR_ROUND_CAPACITY   lowers the per-round draw capacity (read by kmpar_init
+ *                          and kmpar_batch_run)
  *   KMPAR_CTX_LIMIT_BYTES  most device memory one context may hold; a larger
  *                          allocation fails with KMPAR_ERR_OOM (read at every one)
  *   KMPAR_WAIT_CYCLES      clock-cycle budget of the grid barrier of the
@@ -231,6 +232,56 @@ KMPAR_API kmpar_status kmpar_fit(const float *X, int64_t n, int32_t d, int32_t k
                        uint64_t seed, int32_t precision, int32_t max_iter, float *centers_out,
                        int32_t *labels_out, double *seed_cost, double *final_cost, int32_t *iters,
                        int32_t flags, void *stream);
+
+/*
+ * Many independent problems in one call (Alg. 2 steps 1-8 and Lloyd's iteration
+ * per problem, Sec. 3.3 applied to each problem separately: the data-parallel
+ * pattern of Sec. 3.5 over problems instead of machines).  Problem p owns n rows
+ * of d coordinates starting at float x_offset of X (device, row-major); its k
+ * seed-then-Lloyd centers go to centers_out + c_offset (device, k x d FP32), its
+ * final labels to labels_out + l_offset (device, n int32; labels_out nullable),
+ * its candidate row numbers (within the problem) and weights to
+ * cand_out + cand_offset and w_out + cand_offset (device; nullable; room for
+ * kmpar_batch_cand_capacity(ell, rounds) entries).  Every problem draws from
+ * its own seed exactly as kmpar_fit does (same counters, same tie rules); the
+ * distances are the exact FP32 difference form on CUDA cores.  Limits: 1 <= d
+ * <= 128, 1 <= k <= 512, n < 2^31, 0 <= rounds <= 16, per-round capacity
+ * l + 10 sqrt(l) + 64 <= 4096.  results (host, count entries) receive each
+ * problem's outcome; a problem whose round overflows its capacity stops there
+ * with status KMPAR_ERR_CAPACITY, the others are unaffected.  Work space comes
+ * from the library's pool; the problems run one thread block each, largest
+ * first, in one kernel launch per dimension class.  Synchronises.
+ */
+typedef struct {
+    int64_t x_offset;     /* first float of the problem's rows in X               */
+    int64_t n;            /* points                                               */
+    int32_t d, k;         /* dimension, centers                                   */
+    double  ell;          /* oversampling factor l                                */
+    int32_t rounds;       /* rounds r                                             */
+    int32_t max_iter;     /* Lloyd updates at most                                */
+    uint64_t seed;
+    int64_t c_offset;     /* first float of the problem's centers in centers_out  */
+    int64_t l_offset;     /* first label in labels_out                            */
+    int64_t cand_offset;  /* first entry in cand_out / w_out                      */
+} kmpar_problem;
+
+typedef struct {
+    int64_t m;            /* candidates                                           */
+    double  seed_cost;    /* cost of the seed centers (Lloyd's first assignment)  */
+    double  final_cost;   /* cost of the final centers                            */
+    int32_t iters;        /* Lloyd updates made                                   */
+    int32_t status;       /* KMPAR_OK, KMPAR_ERR_CAPACITY or KMPAR_WARN_FEW_CANDIDATES */
+    int64_t sample_near;  /* draws with |u - p| <= 1e-6                           */
+    int64_t argmin_fp64;  /* argmin decisions re-decided in FP64                  */
+    int64_t recluster_near; /* reclustering targets within 1e-6 of a boundary     */
+} kmpar_problem_result;
+
+/* Candidate slots a problem of oversampling l and r rounds needs in cand_out/w_out. */
+KMPAR_API int64_t kmpar_batch_cand_capacity(double ell, int32_t rounds);
+
+KMPAR_API kmpar_status kmpar_batch_run(const float *X, const kmpar_problem *problems, int32_t count,
+                                       float *centers_out, int32_t *labels_out, int32_t *cand_out,
+                                       int64_t *w_out, kmpar_problem_result *results, void *stream);
 
 /*
  * How Alg. 2 step 4 draws.  KMPAR_SAMPLE_BERNOULLI (the default): every x is

@@ -1,0 +1,723 @@
+// batch.cu -- many independent k-means|| problems in one call (kmpar_batch_run):
+// Algorithm 2 (Sec. 3.3) and Lloyd's iteration (Sec. 1, Sec. 3.1) per problem,
+// one thread block per problem, every step on the device.  The data-parallel
+// pattern of Sec. 3.5 is applied across problems: a block owns its problem from
+// the first center to the last centroid update, so no grid-wide synchronisation
+// is needed and the blocks run in any order (largest problems first).
+//
+// Per problem (kBT threads, the point loop in chunks of kBT rows, thread = row,
+// the row's coordinates in registers, centers in kBTile-row shared-memory tiles):
+//   init     i0 = floor(u n), D^2 = ||x - x_i0||^2, idx = 0, phi = sum D^2 (FP64)
+//   round i  every x drawn with p = min(1, l D^2 / phi) (Philox, FP64 re-decision
+//            of near draws), appended in ascending point order by an ordered
+//            block compaction (no sort); D^2/idx against the batch
+//   step 7   w_c = #{x : idx(x) = c} (shared-memory integer atomics)
+//   step 8   weighted k-means++: per draw a blocked FP64 prefix over the masses,
+//            the first candidate whose prefix exceeds u * total
+//   Lloyd    assignment with the FP32 path's decision rule; centroids from a
+//            stable counting sort by label (warp-private label counters,
+//            __match_any_sync ranks) and compensated FP32 sums in ascending
+//            point order, divided in FP64, rounded to FP32 once
+// Distances are the exact FP32 difference form (ascending coordinates, one
+// rounded subtraction and one FMA each), so every decision equals kmpar_fit's
+// FP32 path on the same problem.
+#include <float.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <vector>
+
+#include "kmpar_internal.cuh"
+
+namespace kmp {
+void set_thread_error(const std::string &m);
+
+namespace {
+
+constexpr int kBT = 256;          // threads per problem block
+constexpr int kBW = kBT / 32;     // warps per block
+constexpr int kBTile = 32;        // centers per shared-memory tile
+constexpr int kBMaxK = 512;
+constexpr int kBMaxRounds = 16;
+constexpr int kBMaxCap = 4096;    // per-round draw capacity
+
+// device copy of one problem with its work-space offsets
+struct BProb {
+    int64_t x_off, n;
+    int d, k;
+    double ell;
+    int rounds, max_iter;
+    uint64_t seed;
+    int64_t c_off, l_off, cand_off;   // outputs
+    int64_t p_off, m_off;             // work space: per-point arrays, per-candidate arrays
+    int cap_round, cap_total;
+};
+
+struct BRes {
+    long long m;
+    double seed_cost, final_cost;
+    int iters, status;
+    unsigned long long sample_near, argmin_fp64, recluster_near;
+};
+
+struct BArgs {
+    const float *X;
+    const BProb *probs;
+    const int32_t *order;    // problems of this launch, largest first
+    float *centers;
+    int32_t *labels_out;     // nullable
+    int32_t *cand_out;       // nullable
+    long long *w_out;        // nullable
+    BRes *res;
+    // work space
+    float *D2;
+    int32_t *idx, *lab, *perm;
+    int32_t *cand;
+    int32_t *w;
+    float *rD2;
+};
+
+enum { BM_FIRST = 0, BM_ROUND = 1, BM_ASSIGN = 2 };
+
+// Deterministic block sum of one FP64 per thread: fixed shuffle tree, warps in
+// order; the result is returned to every thread.
+__device__ __forceinline__ double bsum_f64(double v, double *sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    for (int i = 0; i < kBW; ++i) r += sh[i];
+    return r;
+}
+
+__device__ __forceinline__ int bsum_i32(int v, int *sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    int r = 0;
+    for (int i = 0; i < kBW; ++i) r += sh[i];
+    return r;
+}
+
+// one term of the exact FP32 difference form: t = x - c rounded, a = fma(t, t, a)
+__device__ __forceinline__ void sq_acc(float x, float c, float &a) {
+    const float t = __fsub_rn(x, c);
+    a = __fmaf_rn(t, t, a);
+}
+
+__device__ __forceinline__ void take_better(double v, int j, double &best, int &bj) {
+    if (v < best || (v == best && j < bj)) { best = v; bj = j; }
+}
+
+// Shared state of one block.
+template <int DP>
+struct BShared {
+    float tile[kBTile * DP];
+    double red[kBW];
+    int redi[kBW];
+    int hist[kBW][kBMaxK];     // Lloyd: per-warp label counts, then the warps' running bases
+    int base[kBMaxK + 1];      // step 8: the chosen candidates; Lloyd: cluster offsets
+    int wpos[kBW];
+    int s_int[4];
+    unsigned long long s_near, s_fp64, s_rnear;
+};
+
+// One pass over the problem's rows against `cnt` centers: the rows of C_rows (a
+// center matrix, stride d) or, when cand is given, X rows cand[begin + r].  Each
+// thread holds one row's coordinates in registers (padded to DP with zeros: they
+// add exact zeros to the sums) and keeps the lexicographic (value, center number)
+// top-2 over centers in ascending order; the decision is the FP32 path's:
+//   FIRST   D^2 = the single distance, idx = 0
+//   ROUND   the current center is replaced by the best new one when nearer; two
+//           or more of (current, best, runner-up) within the FP32 tie window are
+//           re-decided in FP64 (difference form, no FMA), equal values keeping
+//           the lower center number
+//   ASSIGN  the best, re-decided in FP64 against the runner-up inside the window
+// Returns the block's FP64 sum of the stored distances (D^2 or the chosen
+// center's distance) and adds the number of changed labels to *changed.
+template <int DP, int MODE>
+__device__ double dist_pass(BShared<DP> &sh, const float *__restrict__ Xp, int64_t n, int d,
+                            const float *__restrict__ C_rows, const int32_t *__restrict__ cand, int begin, int cnt,
+                            float *D2, int32_t *idx, int32_t *lab, int *changed, unsigned long long *fp64_cnt) {
+    const int tid = threadIdx.x;
+    const float W = fp32_tie_window(d);
+    double acc_sum = 0.0;
+    int chg = 0;
+    unsigned long long nfp64 = 0;
+    for (int64_t base = 0; base < n; base += kBT) {
+        const int64_t pt = base + tid;
+        const bool valid = pt < n;
+        const float *xrow = Xp + (valid ? pt : 0) * (int64_t)d;
+        float xr[DP];
+#pragma unroll
+        for (int q = 0; q < DP; ++q) xr[q] = (valid && q < d) ? __ldg(xrow + q) : 0.f;
+        float b1 = FLT_MAX, b2 = FLT_MAX;
+        int i1 = -1, i2 = -1;
+        for (int t0 = 0; t0 < cnt; t0 += kBTile) {
+            const int nt = min(kBTile, cnt - t0);
+            __syncthreads();
+            for (int e = tid; e < kBTile * DP; e += kBT) {
+                const int r = e / DP, q = e - r * DP;
+                float v = 0.f;
+                if (r < nt && q < d) {
+                    const int j = begin + t0 + r;
+                    const float *row = cand ? Xp + (int64_t)cand[j] * d : C_rows + (int64_t)j * d;
+                    v = __ldg(row + q);
+                }
+                sh.tile[e] = v;
+            }
+            __syncthreads();
+            if (valid) {
+                int r = 0;
+                for (; r + 4 <= nt; r += 4) {
+                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                    const float4 *c0 = reinterpret_cast<const float4 *>(sh.tile + (r + 0) * DP);
+                    const float4 *c1 = reinterpret_cast<const float4 *>(sh.tile + (r + 1) * DP);
+                    const float4 *c2 = reinterpret_cast<const float4 *>(sh.tile + (r + 2) * DP);
+                    const float4 *c3 = reinterpret_cast<const float4 *>(sh.tile + (r + 3) * DP);
+#pragma unroll
+                    for (int q4 = 0; q4 < DP / 4; ++q4) {
+                        const float4 u0 = c0[q4], u1 = c1[q4], u2 = c2[q4], u3 = c3[q4];
+                        sq_acc(xr[4 * q4 + 0], u0.x, a0); sq_acc(xr[4 * q4 + 0], u1.x, a1);
+                        sq_acc(xr[4 * q4 + 0], u2.x, a2); sq_acc(xr[4 * q4 + 0], u3.x, a3);
+                        sq_acc(xr[4 * q4 + 1], u0.y, a0); sq_acc(xr[4 * q4 + 1], u1.y, a1);
+                        sq_acc(xr[4 * q4 + 1], u2.y, a2); sq_acc(xr[4 * q4 + 1], u3.y, a3);
+                        sq_acc(xr[4 * q4 + 2], u0.z, a0); sq_acc(xr[4 * q4 + 2], u1.z, a1);
+                        sq_acc(xr[4 * q4 + 2], u2.z, a2); sq_acc(xr[4 * q4 + 2], u3.z, a3);
+                        sq_acc(xr[4 * q4 + 3], u0.w, a0); sq_acc(xr[4 * q4 + 3], u1.w, a1);
+                        sq_acc(xr[4 * q4 + 3], u2.w, a2); sq_acc(xr[4 * q4 + 3], u3.w, a3);
+                    }
+                    const float av[4] = {a0, a1, a2, a3};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = begin + t0 + r + u;
+                        const float a = av[u];
+                        if (a < b2) {
+                            if (a < b1) { b2 = b1; i2 = i1; b1 = a; i1 = j; }
+                            else { b2 = a; i2 = j; }
+                        }
+                    }
+                }
+                for (; r < nt; ++r) {
+                    float a = 0.f;
+                    const float4 *c4 = reinterpret_cast<const float4 *>(sh.tile + r * DP);
+#pragma unroll
+                    for (int q4 = 0; q4 < DP / 4; ++q4) {
+                        const float4 u = c4[q4];
+                        sq_acc(xr[4 * q4 + 0], u.x, a);
+                        sq_acc(xr[4 * q4 + 1], u.y, a);
+                        sq_acc(xr[4 * q4 + 2], u.z, a);
+                        sq_acc(xr[4 * q4 + 3], u.w, a);
+                    }
+                    const int j = begin + t0 + r;
+                    if (a < b2) {
+                        if (a < b1) { b2 = b1; i2 = i1; b1 = a; i1 = j; }
+                        else { b2 = a; i2 = j; }
+                    }
+                }
+            }
+        }
+        if (!valid) continue;
+        auto crow = [&](int j) -> const float * {
+            return cand ? Xp + (int64_t)cand[j] * d : C_rows + (int64_t)j * d;
+        };
+        float stored = 0.f;
+        if (MODE == BM_FIRST) {
+            stored = (i1 >= 0) ? b1 : __int_as_float(0x7f800000);
+            D2[pt] = stored;
+            idx[pt] = 0;
+        } else if (MODE == BM_ASSIGN) {
+            int l = i1 >= 0 ? i1 : 0;
+            stored = b1;
+            if (i2 >= 0 && b2 <= b1 + W * b1) {
+                double best = dist2_fp64(xrow, crow(i1), d);
+                int bj = i1;
+                take_better(dist2_fp64(xrow, crow(i2), d), i2, best, bj);
+                if (bj == i2) { l = i2; stored = b2; }
+                ++nfp64;
+            }
+            if (changed) chg += (lab[pt] != l);
+            lab[pt] = l;
+        } else {
+            const float old = D2[pt];
+            const int oi = idx[pt];
+            const float m32 = fminf(old, b1);
+            const float lim = m32 + W * m32;
+            const bool in_old = (oi >= 0) && old <= lim;
+            const bool in1 = i1 >= 0 && b1 <= lim;
+            const bool in2 = i2 >= 0 && b2 <= lim;
+            int win = -1;
+            float wv = old;
+            if ((int)in_old + (int)in1 + (int)in2 >= 2) {
+                double best = DBL_MAX;
+                int bj = INT_MAX;
+                if (in_old) take_better(dist2_fp64(xrow, Xp + (int64_t)cand[oi] * d, d), oi, best, bj);
+                if (in1) take_better(dist2_fp64(xrow, crow(i1), d), i1, best, bj);
+                if (in2) take_better(dist2_fp64(xrow, crow(i2), d), i2, best, bj);
+                ++nfp64;
+                if (bj == i1) { win = i1; wv = b1; }
+                else if (bj == i2) { win = i2; wv = b2; }
+            } else if (i1 >= 0 && b1 < old) {
+                win = i1; wv = b1;
+            }
+            if (win >= 0) { D2[pt] = wv; idx[pt] = win; stored = wv; }
+            else stored = old;
+        }
+        acc_sum += (double)stored;
+    }
+    if (nfp64) atomicAdd(fp64_cnt, nfp64);
+    if (MODE == BM_ASSIGN && changed) *changed = bsum_i32(chg, sh.redi);   // every thread
+    return bsum_f64(acc_sum, sh.red);
+}
+
+// Block-wide exclusive prefix of one FP64 per thread in thread order (warp scans,
+// then the warp totals in order); returns the thread's exclusive prefix and the
+// total (to every thread).
+__device__ __forceinline__ double bscan_f64(double v, double *sh, double *total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    __syncthreads();
+    if (lane == 31) sh[wid] = incl;
+    __syncthreads();
+    double before = 0.0, tot = 0.0;
+    for (int i = 0; i < kBW; ++i) {
+        if (i < wid) before += sh[i];
+        tot += sh[i];
+    }
+    *total = tot;
+    double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = 0.0;
+    return before + excl;
+}
+
+__device__ __forceinline__ int bmin_i32(int v, int *sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    int r = INT_MAX;
+    for (int i = 0; i < kBW; ++i) r = min(r, sh[i]);
+    return r;
+}
+
+__device__ __forceinline__ int bmax_i32(int v, int *sh) { return -bmin_i32(-v, sh); }
+
+// Knuth's TwoSum: (s, c) += x with s the rounded sum and c the accumulated
+// rounding errors (all FP32, each operation rounded to nearest)
+__device__ __forceinline__ void two_sum_add(float &s, float &c, float x) {
+    const float t = __fadd_rn(s, x);
+    const float bp = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    c = __fadd_rn(c, e);
+    s = t;
+}
+
+template <int DP>
+__global__ void __launch_bounds__(kBT, DP == 128 ? 1 : (DP == 64 ? 2 : 3)) batch_kernel(BArgs a, int first) {
+    __shared__ BShared<DP> sh;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int pi = a.order[first + blockIdx.x];
+    const BProb P = a.probs[pi];
+    const float *X = a.X + P.x_off;
+    const int64_t n = P.n;
+    const int d = P.d, k = P.k;
+    float *D2 = a.D2 + P.p_off;
+    int32_t *idx = a.idx + P.p_off, *lab = a.lab + P.p_off, *perm = a.perm + P.p_off;
+    int32_t *cand = a.cand + P.m_off, *w = a.w + P.m_off;
+    float *rD2 = a.rD2 + P.m_off;
+    float *C = a.centers + P.c_off;
+    if (tid == 0) {
+        sh.s_near = 0; sh.s_fp64 = 0; sh.s_rnear = 0;
+        // Alg. 2 step 1: the first center, uniform over the problem's points
+        const double u = uniform53(0, 0, TAG_INIT, P.seed);
+        int64_t i0 = (int64_t)floor(__dmul_rn(u, (double)n));
+        if (i0 >= n) i0 = n - 1;
+        cand[0] = (int32_t)i0;
+    }
+    __syncthreads();
+    // step 2: D^2 to the first center and psi
+    double phi = dist_pass<DP, BM_FIRST>(sh, X, n, d, nullptr, cand, 0, 1, D2, idx, nullptr, nullptr, &sh.s_fp64);
+    int m = 1, status = KMPAR_OK;
+    for (int r = 1; r <= P.rounds; ++r) {
+        // step 4: independent draws, appended in ascending point order
+        int appended = 0;
+        unsigned long long near = 0;
+        for (int64_t base = 0; base < n; base += kBT) {
+            const int64_t pt = base + tid;
+            bool take = false;
+            if (pt < n) {
+                const float dd = D2[pt];
+                double pr = 0.0;
+                if (phi > 0.0) pr = fmin(1.0, __ddiv_rn(__dmul_rn(P.ell, (double)dd), phi));
+                const double u = uniform53((uint64_t)pt, (uint32_t)r, TAG_SAMPLE, P.seed);
+                if (dd > 0.f && fabs(u - pr) <= 1e-5) {
+                    // the FP32 D^2 could decide this draw: use the FP64 distance of the definition
+                    const double d64 = dist2_fp64(X + pt * d, X + (int64_t)cand[idx[pt]] * d, d);
+                    pr = fmin(1.0, __ddiv_rn(__dmul_rn(P.ell, d64), phi));
+                }
+                if (fabs(u - pr) <= 1e-6) ++near;
+                take = u < pr;
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, take);
+            if (lane == 0) sh.wpos[wid] = __popc(mask);
+            __syncthreads();
+            int before = 0, tot = 0;
+            for (int i = 0; i < kBW; ++i) {
+                if (i < wid) before += sh.wpos[i];
+                tot += sh.wpos[i];
+            }
+            if (take) {
+                const int pos = appended + before + __popc(mask & ((1u << lane) - 1u));
+                if (pos < P.cap_round) cand[m + pos] = (int32_t)pt;
+            }
+            appended += tot;
+            __syncthreads();   // wpos is rewritten by the next chunk
+        }
+        if (near) atomicAdd(&sh.s_near, near);
+        if (appended > P.cap_round) { status = KMPAR_ERR_CAPACITY; break; }
+        __syncthreads();       // the batch's row numbers are visible to the whole block
+        // step 5: D^2 and idx against the batch, then phi
+        phi = dist_pass<DP, BM_ROUND>(sh, X, n, d, nullptr, cand, m, appended, D2, idx, nullptr, nullptr,
+                                      &sh.s_fp64);
+        m += appended;
+    }
+    BRes res{};
+    res.m = m;
+    if (status == KMPAR_OK) {
+        // step 7: weights
+        for (int j = tid; j < m; j += kBT) w[j] = 0;
+        __syncthreads();
+        for (int64_t pt = tid; pt < n; pt += kBT) atomicAdd(&w[idx[pt]], 1);
+        __syncthreads();
+        // step 8: weighted k-means++ over the m candidates
+        const int q = (m + kBT - 1) / kBT;
+        const int lo = min(m, tid * q), hi = min(m, lo + q);
+        int *chosen = sh.base;
+        bool warn = false;
+        for (int t = 0; t < k; ++t) {
+            double local = 0.0;
+            for (int j = lo; j < hi; ++j)
+                local += t == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)rD2[j]);
+            double total;
+            const double excl = bscan_f64(local, sh.red, &total);
+            if (!(total > 0.0)) {
+                // positive mass exhausted: the remaining centers repeat the first chosen one
+                const int src = t > 0 ? chosen[0] : 0;
+                for (int s2 = t; s2 < k; ++s2) {
+                    for (int qq = tid; qq < d; qq += kBT) C[(int64_t)s2 * d + qq] = X[(int64_t)cand[src] * d + qq];
+                    if (tid == 0) chosen[s2] = src;
+                }
+                warn = true;
+                break;
+            }
+            const double target = __dmul_rn(uniform53((uint64_t)t, 0, TAG_RECLUSTER, P.seed), total);
+            int mine = INT_MAX;
+            double cum0 = 0.0, cum = 0.0, run = excl;
+            for (int j = lo; j < hi; ++j) {
+                const double e = t == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)rD2[j]);
+                const double pre = run;
+                run = run + e;
+                if (run > target) { mine = j; cum0 = pre; cum = run; break; }
+            }
+            int pick = bmin_i32(mine, sh.redi);
+            if (pick == INT_MAX) {
+                // the target rounded past every prefix: the last candidate with positive mass
+                int lastp = -1;
+                for (int j = lo; j < hi; ++j)
+                    if ((t == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)rD2[j])) > 0.0) lastp = j;
+                pick = bmax_i32(lastp, sh.redi);
+                if (tid == 0) atomicAdd(&sh.s_rnear, 1ull);
+            } else if (mine == pick &&
+                       (fabs(target - cum0) <= 1e-6 * total || fabs(cum - target) <= 1e-6 * total)) {
+                atomicAdd(&sh.s_rnear, 1ull);
+            }
+            if (tid == 0) chosen[t] = pick;
+            const float *prow = X + (int64_t)cand[pick] * d;
+            for (int qq = tid; qq < d; qq += kBT) C[(int64_t)t * d + qq] = prow[qq];
+            __syncthreads();
+            // D^2 of every candidate to the centers drawn so far
+            const float *crow = C + (int64_t)t * d;
+            for (int j = tid; j < m; j += kBT) {
+                const float v = dist2_fp32(X + (int64_t)cand[j] * d, crow, d);
+                rD2[j] = t == 0 ? v : fminf(rD2[j], v);
+            }
+            __syncthreads();
+        }
+        if (warn) status = KMPAR_WARN_FEW_CANDIDATES;
+        __syncthreads();
+        // Lloyd's iteration from the seed centers
+        int it = 0;
+        double cost = 0.0;
+        for (;; ++it) {
+            int chg = 0;
+            cost = dist_pass<DP, BM_ASSIGN>(sh, X, n, d, C, nullptr, 0, k, nullptr, nullptr, lab,
+                                            it > 0 ? &chg : nullptr, &sh.s_fp64);
+            if (it == 0) res.seed_cost = cost;
+            if (it > 0 && chg == 0) break;
+            if (it == P.max_iter) break;
+            // stable counting sort by label: warp wr owns the contiguous rows [wr npw, (wr+1) npw)
+            const int64_t npw = (n + kBW - 1) / kBW;
+            const int64_t r0 = min(n, (int64_t)wid * npw), r1 = min(n, r0 + npw);
+            for (int l = tid; l < kBW * kBMaxK; l += kBT) (&sh.hist[0][0])[l] = 0;
+            __syncthreads();
+            for (int64_t c0 = r0; c0 < r1; c0 += 32) {
+                const int64_t pt = c0 + lane;
+                const int l = pt < r1 ? lab[pt] : -1;
+                const unsigned peers = __match_any_sync(0xffffffffu, l);
+                if (l >= 0 && lane == __ffs(peers) - 1) sh.hist[wid][l] += __popc(peers);
+                __syncwarp();
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int acc = 0;
+                for (int l = 0; l < k; ++l) {
+                    sh.base[l] = acc;
+                    for (int i = 0; i < kBW; ++i) acc += sh.hist[i][l];
+                }
+                sh.base[k] = acc;
+            }
+            __syncthreads();
+            for (int l = tid; l < k; l += kBT) {
+                int run2 = sh.base[l];
+                for (int i = 0; i < kBW; ++i) {
+                    const int c = sh.hist[i][l];
+                    sh.hist[i][l] = run2;
+                    run2 += c;
+                }
+            }
+            __syncthreads();
+            for (int64_t c0 = r0; c0 < r1; c0 += 32) {
+                const int64_t pt = c0 + lane;
+                const int l = pt < r1 ? lab[pt] : -1;
+                const unsigned peers = __match_any_sync(0xffffffffu, l);
+                if (l >= 0) perm[sh.hist[wid][l] + __popc(peers & ((1u << lane) - 1u))] = (int32_t)pt;
+                __syncwarp();
+                if (l >= 0 && lane == __ffs(peers) - 1) sh.hist[wid][l] += __popc(peers);
+                __syncwarp();
+            }
+            __syncthreads();
+            // centroids: member coordinates in ascending point order, compensated FP32
+            for (int64_t pq = tid; pq < (int64_t)k * d; pq += kBT) {
+                const int j = (int)(pq / d), qq = (int)(pq % d);
+                const int b0 = sh.base[j], b1 = sh.base[j + 1];
+                if (b1 == b0) continue;   // an empty cluster keeps its center
+                float s = 0.f, c = 0.f;
+                for (int i = b0; i < b1; ++i) two_sum_add(s, c, X[(int64_t)perm[i] * d + qq]);
+                C[pq] = (float)(((double)s + (double)c) / (double)(b1 - b0));
+            }
+            __syncthreads();
+        }
+        res.iters = it;
+        res.final_cost = cost;
+        if (a.labels_out)
+            for (int64_t pt = tid; pt < n; pt += kBT) a.labels_out[P.l_off + pt] = lab[pt];
+    }
+    if (a.cand_out)
+        for (int j = tid; j < m && j < P.cap_total; j += kBT) a.cand_out[P.cand_off + j] = cand[j];
+    if (a.w_out && status != KMPAR_ERR_CAPACITY)
+        for (int j = tid; j < m; j += kBT) a.w_out[P.cand_off + j] = w[j];
+    __syncthreads();
+    if (tid == 0) {
+        res.status = status;
+        res.sample_near = sh.s_near;
+        res.argmin_fp64 = sh.s_fp64;
+        res.recluster_near = sh.s_rnear;
+        a.res[pi] = res;
+    }
+}
+
+}  // namespace
+}  // namespace kmp
+
+// ------------------------------------------------------------------ host side
+namespace kmp {
+namespace {
+
+// l + 10 sqrt(l) + 64 (the round count is a sum of independent draws with mean at
+// most l and variance at most l), lowered by KMPAR_ROUND_CAPACITY when set
+int batch_round_capacity(double ell) {
+    double c = ell + 10.0 * std::sqrt(ell) + 64.0;
+    if (c > 2.0e9) c = 2.0e9;
+    int cap = (int)std::ceil(c);
+    if (const char *v = std::getenv("KMPAR_ROUND_CAPACITY")) {
+        char *end = nullptr;
+        const unsigned long long x = std::strtoull(v, &end, 10);
+        if (*v && end && *end == 0 && x > 0 && x < (unsigned long long)cap) cap = (int)x;
+    }
+    return cap;
+}
+
+kmpar_status batch_fail(kmpar_status s, const std::string &m) {
+    kmp::set_thread_error(m);
+    return s;
+}
+
+template <int DP>
+cudaError_t launch_class(const kmp::BArgs &a, int first, int count, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    kmp::batch_kernel<DP><<<count, kmp::kBT, 0, s>>>(a, first);
+    kmp::count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace kmp
+
+extern "C" {
+
+int64_t kmpar_batch_cand_capacity(double ell, int32_t rounds) {
+    if (!(ell > 0.0) || rounds < 0) return 0;
+    return 1 + (int64_t)rounds * kmp::batch_round_capacity(ell);
+}
+
+kmpar_status kmpar_batch_run(const float *X, const kmpar_problem *problems, int32_t count, float *centers_out,
+                             int32_t *labels_out, int32_t *cand_out, int64_t *w_out, kmpar_problem_result *results,
+                             void *stream) {
+    using namespace kmp;
+    if (count < 0 || (count > 0 && (!X || !problems || !centers_out || !results)))
+        return batch_fail(KMPAR_ERR_ARG, "NULL pointer or negative count");
+    if (count == 0) return KMPAR_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<BProb> hp((size_t)count);
+    std::vector<double> work((size_t)count);
+    int64_t p_tot = 0, m_tot = 0;
+    for (int i = 0; i < count; ++i) {
+        const kmpar_problem &q = problems[i];
+        if (q.n < 1 || q.n >= (int64_t)INT32_MAX || q.d < 1 || q.d > 128 || q.k < 1 || q.k > kBMaxK ||
+            !(q.ell > 0.0) || !std::isfinite(q.ell) || q.rounds < 0 || q.rounds > kBMaxRounds || q.max_iter < 0 ||
+            q.x_offset < 0 || q.c_offset < 0 || q.l_offset < 0 || q.cand_offset < 0)
+            return batch_fail(KMPAR_ERR_ARG, "problem " + std::to_string(i) + ": argument out of range");
+        const int cap = batch_round_capacity(q.ell);
+        if (cap > kBMaxCap)
+            return batch_fail(KMPAR_ERR_UNSUPPORTED,
+                              "problem " + std::to_string(i) + ": l + 10 sqrt(l) + 64 exceeds 4096 per round");
+        BProb &b = hp[(size_t)i];
+        b.x_off = q.x_offset; b.n = q.n; b.d = q.d; b.k = q.k; b.ell = q.ell; b.rounds = q.rounds;
+        b.max_iter = q.max_iter; b.seed = q.seed; b.c_off = q.c_offset; b.l_off = q.l_offset;
+        b.cand_off = q.cand_offset;
+        b.cap_round = cap;
+        b.cap_total = 1 + q.rounds * cap;
+        b.p_off = p_tot;
+        b.m_off = m_tot;
+        p_tot += q.n;
+        m_tot += b.cap_total;
+        // distance evaluations of the rounds and of Lloyd, times the padded dimension
+        const int dp = q.d <= 32 ? 32 : (q.d <= 64 ? 64 : 128);
+        work[(size_t)i] = (double)q.n * dp * (1.0 + q.rounds * q.ell + (double)(q.max_iter + 1) * q.k);
+    }
+    // each dimension class in one launch, largest problems first
+    std::vector<int32_t> order;
+    order.reserve((size_t)count);
+    int first[3] = {0, 0, 0}, cnt[3] = {0, 0, 0};
+    for (int c = 0; c < 3; ++c) {
+        first[c] = (int)order.size();
+        const int lo = c == 0 ? 1 : (c == 1 ? 33 : 65), hi = c == 0 ? 32 : (c == 1 ? 64 : 128);
+        std::vector<int32_t> ids;
+        for (int i = 0; i < count; ++i)
+            if (problems[i].d >= lo && problems[i].d <= hi) ids.push_back(i);
+        std::stable_sort(ids.begin(), ids.end(), [&](int32_t x, int32_t y) { return work[x] > work[y]; });
+        order.insert(order.end(), ids.begin(), ids.end());
+        cnt[c] = (int)ids.size();
+    }
+    // one device block holds the table, the order, the results and the work space
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t o_probs = 0;
+    const size_t o_order = o_probs + up(sizeof(BProb) * (size_t)count);
+    const size_t o_res = o_order + up(sizeof(int32_t) * (size_t)count);
+    const size_t o_d2 = o_res + up(sizeof(BRes) * (size_t)count);
+    const size_t o_idx = o_d2 + up(sizeof(float) * (size_t)p_tot);
+    const size_t o_lab = o_idx + up(sizeof(int32_t) * (size_t)p_tot);
+    const size_t o_perm = o_lab + up(sizeof(int32_t) * (size_t)p_tot);
+    const size_t o_cand = o_perm + up(sizeof(int32_t) * (size_t)p_tot);
+    const size_t o_w = o_cand + up(sizeof(int32_t) * (size_t)m_tot);
+    const size_t o_rd2 = o_w + up(sizeof(int32_t) * (size_t)m_tot);
+    const size_t total = o_rd2 + up(sizeof(float) * (size_t)m_tot);
+    unsigned char *ws = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&ws), total, s);
+    if (e != cudaSuccess)
+        return batch_fail(e == cudaErrorMemoryAllocation ? KMPAR_ERR_OOM : KMPAR_ERR_CUDA,
+                          std::string("batch work space: ") + cudaGetErrorString(e));
+    std::vector<BRes> hres((size_t)count);
+    cudaStream_t side[2] = {nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+    BArgs a{};
+    a.X = X;
+    a.probs = reinterpret_cast<const BProb *>(ws + o_probs);
+    a.order = reinterpret_cast<const int32_t *>(ws + o_order);
+    a.centers = centers_out;
+    a.labels_out = labels_out;
+    a.cand_out = cand_out;
+    a.w_out = reinterpret_cast<long long *>(w_out);
+    a.res = reinterpret_cast<BRes *>(ws + o_res);
+    a.D2 = reinterpret_cast<float *>(ws + o_d2);
+    a.idx = reinterpret_cast<int32_t *>(ws + o_idx);
+    a.lab = reinterpret_cast<int32_t *>(ws + o_lab);
+    a.perm = reinterpret_cast<int32_t *>(ws + o_perm);
+    a.cand = reinterpret_cast<int32_t *>(ws + o_cand);
+    a.w = reinterpret_cast<int32_t *>(ws + o_w);
+    a.rD2 = reinterpret_cast<float *>(ws + o_rd2);
+    e = cudaMemcpyAsync(ws + o_probs, hp.data(), sizeof(BProb) * (size_t)count, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws + o_order, order.data(), sizeof(int32_t) * (size_t)count, cudaMemcpyHostToDevice, s);
+    // the three classes run concurrently: the caller's stream and two side streams
+    // forked from it and joined back (also valid inside a stream capture)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_join[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev_fork, s);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(side[i], ev_fork, 0);
+    if (e == cudaSuccess) e = launch_class<128>(a, first[2], cnt[2], s);
+    if (e == cudaSuccess) e = launch_class<64>(a, first[1], cnt[1], side[0]);
+    if (e == cudaSuccess) e = launch_class<32>(a, first[0], cnt[0], side[1]);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(ev_join[i], side[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_join[i], 0);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hres.data(), ws + o_res, sizeof(BRes) * (size_t)count, cudaMemcpyDeviceToHost, s);
+    const cudaError_t ef = cudaFreeAsync(ws, s);
+    if (e == cudaSuccess) e = ef;
+    const cudaError_t es = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = es;
+    for (int i = 0; i < 2; ++i) {
+        if (side[i]) cudaStreamDestroy(side[i]);
+        if (ev_join[i]) cudaEventDestroy(ev_join[i]);
+    }
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (e != cudaSuccess) return batch_fail(KMPAR_ERR_CUDA, std::string("batch kernels: ") + cudaGetErrorString(e));
+    kmpar_status worst = KMPAR_OK;
+    for (int i = 0; i < count; ++i) {
+        const BRes &r = hres[(size_t)i];
+        kmpar_problem_result &o = results[i];
+        o.m = r.m;
+        o.seed_cost = r.seed_cost;
+        o.final_cost = r.final_cost;
+        o.iters = r.iters;
+        o.status = r.status;
+        o.sample_near = (int64_t)r.sample_near;
+        o.argmin_fp64 = (int64_t)r.argmin_fp64;
+        o.recluster_near = (int64_t)r.recluster_near;
+        if (r.status == KMPAR_ERR_CAPACITY) worst = KMPAR_ERR_CAPACITY;
+        else if (r.status == KMPAR_WARN_FEW_CANDIDATES && worst == KMPAR_OK) worst = KMPAR_WARN_FEW_CANDIDATES;
+    }
+    if (worst == KMPAR_ERR_CAPACITY) kmp::set_thread_error("a problem's round drew more points than its capacity");
+    return worst;
+}
+
+}  // extern "C"

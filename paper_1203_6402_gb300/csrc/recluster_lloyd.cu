@@ -142,6 +142,42 @@ __device__ __forceinline__ int prefix_find(const double *v, int lo, int hi, doub
     return __shfl_sync(0xffffffffu, hit, src);
 }
 
+// prefix_find with the values cached in registers (at most 16 per lane): one pass
+// over global memory for the sum, the scan and the search
+__device__ __forceinline__ int prefix_find_reg(const double *v, int lo, int hi, double start, double target, int lane,
+                                               double *before, double *total_out) {
+    const int cnt = hi - lo;
+    const int q = (cnt + 31) / 32;
+    if (q > 16) return prefix_find(v, lo, hi, start, target, lane, before, total_out);
+    const int a = lo + min(cnt, lane * q), b = lo + min(cnt, lane * q + q);
+    double vals[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) vals[t] = (t < q && a + t < b) ? __ldcg(v + a + t) : 0.0;
+    double ls = 0.0;
+#pragma unroll
+    for (int t = 0; t < 16; ++t)
+        if (t < q && a + t < b) ls += vals[t];
+    const double incl = warp_incl_scan_f64(ls, lane);
+    double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = 0.0;
+    if (total_out) *total_out = start + __shfl_sync(0xffffffffu, incl, 31);
+    int hit = -1;
+    double bf = 0.0, run = start + excl;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        if (hit < 0 && t < q && a + t < b) {
+            const double pre = run;
+            run = run + vals[t];
+            if (run > target) { hit = a + t; bf = pre; }
+        }
+    }
+    const unsigned any = __ballot_sync(0xffffffffu, hit >= 0);
+    if (!any) return -1;
+    const int src = __ffs(any) - 1;
+    *before = __shfl_sync(0xffffffffu, bf, src);
+    return __shfl_sync(0xffffffffu, hit, src);
+}
+
 // last index in [lo, hi) with a positive value (-1: none)
 __device__ __forceinline__ int last_positive(const double *v, int lo, int hi, int lane) {
     int best = -1;
@@ -156,9 +192,13 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
     const float *__restrict__ C, const float *__restrict__ CT, int mp, const long long *__restrict__ w, DevState *st,
     int d, int k, uint64_t seed, float *rD2, int32_t *chosen, float *centers, double *gchunk, int nchunk_cap,
     double *gctot, int cpc_cap, RcSync *sync, int *err, unsigned long long wait) {
-    extern __shared__ double rsm[];   // cpc_cap chunk totals, then d floats of the pick's row
+    // shared: cpc_cap chunk totals, the CTA's candidates' weights (FP64) and D^2,
+    // then d floats of the pick's row
+    extern __shared__ double rsm[];
     double *ctl = rsm;
-    float *cnew = reinterpret_cast<float *>(rsm + cpc_cap);
+    double *wl = rsm + cpc_cap;
+    float *dl = reinterpret_cast<float *>(wl + (size_t)cpc_cap * 32);
+    float *cnew = dl + (size_t)cpc_cap * 32;
     __shared__ int s_pick, s_near, s_done;
     const int m = st->m;
     const int nchunk = (m + 31) / 32;
@@ -167,6 +207,11 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
     const int b = blockIdx.x;
     const int c0 = min(nchunk, b * cpc), c1 = min(nchunk, c0 + cpc);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = kRcThreads / 32;
+    for (int ch = c0 + wid; ch < c1; ch += nwarps) {
+        const int j = ch * 32 + lane;
+        wl[(ch - c0) * 32 + lane] = j < m ? (double)w[j] : 0.0;
+    }
+    __syncthreads();
 
     for (int step = 0; step < k; ++step) {
         double *gch = gchunk + (size_t)(step & 1) * nchunk_cap;
@@ -174,8 +219,9 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
         // ---- A: chunk masses and the CTA total
         for (int ch = c0 + wid; ch < c1; ch += nwarps) {
             const int j = ch * 32 + lane;
+            const int jl = (ch - c0) * 32 + lane;
             double e = 0.0;
-            if (j < m) e = step == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)rD2[j]);
+            if (j < m) e = step == 0 ? wl[jl] : __dmul_rn(wl[jl], (double)dl[jl]);
             const double incl = warp_incl_scan_f64(e, lane);
             if (lane == 31) {
                 ctl[ch - c0] = incl;
@@ -197,16 +243,45 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
             double total = 0.0, before = 0.0;
             const double u = uniform53((uint64_t)step, 0, TAG_RECLUSTER, seed);
             // total first (the target depends on it), then the owning CTA
-            double dummy;
-            prefix_find(gct, 0, G, 0.0, __uint_as_float(0x7F800000u), lane, &dummy, &total);
+            // the total first (the target depends on it): a sum with the same association
+            // as the search below
             int pick = -1, near = 0;
+            const int qg = (G + 31) / 32;
+            const int ga = min(G, lane * qg), gb = min(G, lane * qg + qg);
+            double gv[16];
+#pragma unroll
+            for (int t = 0; t < 16; ++t) gv[t] = (t < qg && ga + t < gb) ? __ldcg(gct + ga + t) : 0.0;
+            double ls = 0.0;
+#pragma unroll
+            for (int t = 0; t < 16; ++t)
+                if (t < qg && ga + t < gb) ls += gv[t];
+            const double gincl = warp_incl_scan_f64(ls, lane);
+            total = __shfl_sync(0xffffffffu, gincl, 31);
             if (total > 0.0) {
                 const double target = __dmul_rn(u, total);
-                int ob = prefix_find(gct, 0, G, 0.0, target, lane, &before, nullptr);
+                double gex = __shfl_up_sync(0xffffffffu, gincl, 1);
+                if (lane == 0) gex = 0.0;
+                int hit = -1;
+                double bf = 0.0, run = gex;
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    if (hit < 0 && t < qg && ga + t < gb) {
+                        const double pre = run;
+                        run = run + gv[t];
+                        if (run > target) { hit = ga + t; bf = pre; }
+                    }
+                }
+                const unsigned anyb = __ballot_sync(0xffffffffu, hit >= 0);
+                int ob = -1;
+                if (anyb) {
+                    const int src = __ffs(anyb) - 1;
+                    before = __shfl_sync(0xffffffffu, bf, src);
+                    ob = __shfl_sync(0xffffffffu, hit, src);
+                }
                 double pre_b = before;
                 if (ob < 0) { ob = last_positive(gct, 0, G, lane); pre_b = 0.0; near = 1; }
                 const int oc0 = min(nchunk, ob * cpc), oc1 = min(nchunk, oc0 + cpc);
-                int ch = near ? -1 : prefix_find(gch, oc0, oc1, pre_b, target, lane, &before, nullptr);
+                int ch = near ? -1 : prefix_find_reg(gch, oc0, oc1, pre_b, target, lane, &before, nullptr);
                 double pre_c = before;
                 if (ch < 0) { ch = last_positive(gch, oc0, oc1, lane); near = 1; }
                 const int j = ch * 32 + lane;
@@ -259,18 +334,32 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
             if (b == 0) centers[(int64_t)step * d + qq] = v;
         }
         __syncthreads();
-        // ---- C: D^2 update of own candidates (t = x_q - c_q, fma, q ascending)
+        // ---- C: D^2 update of own candidates (t = x_q - c_q, fma, q ascending); 16
+        // coordinates are loaded before their FMA chain runs
         for (int ch = c0 + wid; ch < c1; ch += nwarps) {
             const int j = ch * 32 + lane;
+            const int jl = (ch - c0) * 32 + lane;
             if (j < m) {
                 float v = 0.f;
                 const float *col = CT + j;
-#pragma unroll 8
-                for (int q = 0; q < d; ++q) {
+                int q = 0;
+                for (; q + 16 <= d; q += 16) {
+                    float buf[16];
+#pragma unroll
+                    for (int u2 = 0; u2 < 16; ++u2) buf[u2] = __ldg(col + (int64_t)(q + u2) * mp);
+#pragma unroll
+                    for (int u2 = 0; u2 < 16; ++u2) {
+                        const float t = __fsub_rn(buf[u2], cnew[q + u2]);
+                        v = __fmaf_rn(t, t, v);
+                    }
+                }
+                for (; q < d; ++q) {
                     const float t = __fsub_rn(__ldg(col + (int64_t)q * mp), cnew[q]);
                     v = __fmaf_rn(t, t, v);
                 }
-                rD2[j] = step == 0 ? v : fminf(rD2[j], v);
+                const float nv = step == 0 ? v : fminf(dl[jl], v);
+                dl[jl] = nv;
+                rD2[j] = nv;
             }
         }
         // the next draw's barrier orders these writes before any CTA reads them
@@ -576,7 +665,8 @@ cudaError_t launch_recluster(Ctx &c, float *centers) {
     const int nchunk_cap = (c.cap_total + 31) / 32;
     int G = std::max(1, std::min(c.num_sms, nchunk_cap));
     const int cpc_cap = (nchunk_cap + G - 1) / G;
-    const size_t smem = sizeof(double) * (size_t)cpc_cap + sizeof(float) * (size_t)c.d;
+    const size_t smem = sizeof(double) * (size_t)cpc_cap * 33 + sizeof(float) * ((size_t)cpc_cap * 32 + c.d);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;   // beyond ~500,000 candidates per SM
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(recluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
             cudaSuccess)

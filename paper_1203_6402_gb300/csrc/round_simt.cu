@@ -803,6 +803,65 @@ __global__ void __launch_bounds__(256) refine_kernel(const float *__restrict__ X
     }
 }
 
+// Per-row refine for rows of d = 0 mod 4 floats (16-byte aligned): one thread per
+// row sums both centers of its screened pair with two interleaved exact FP32
+// chains (ascending coordinates, bit-identical to dist2_fp32) from 16-byte loads
+// of the point row and the two center rows; no shared-memory staging, so the
+// kernel runs at full occupancy and the rows come through L1.
+template <int MODE>
+__global__ void __launch_bounds__(256) refine_direct_kernel(const float *__restrict__ X, int64_t n, int d,
+                                                           const float *__restrict__ C, int c_cnt,
+                                                           const int32_t *__restrict__ cand1,
+                                                           const float *__restrict__ v2s, ScreenBound sb, float *D2,
+                                                           int32_t *idx, int32_t *labels, const int32_t *prev,
+                                                           int *changed, float *dmin, unsigned long long *fp64_cnt,
+                                                           unsigned long long *wide_cnt) {
+    const int64_t R = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = R < n;
+    const int end = MODE == MODE_ROUND ? sb.st->batch_begin + sb.st->batch_cnt : c_cnt;
+    const int j = valid ? cand1[R] : -1;
+    bool fix = valid && j < 0;
+    int chg = 0;
+    if (valid && j >= 0) {
+        const bool has_b = j + 1 < end;
+        const float4 *x4 = reinterpret_cast<const float4 *>(X + R * d);
+        const float4 *a4 = reinterpret_cast<const float4 *>(C + (int64_t)j * d);
+        const float4 *b4 = reinterpret_cast<const float4 *>(C + (int64_t)(has_b ? j + 1 : j) * d);
+        float va = 0.f, vb = 0.f;
+#pragma unroll 4
+        for (int p = 0; p < (d >> 2); ++p) {
+            const float4 x = __ldg(x4 + p), a = __ldg(a4 + p), b = __ldg(b4 + p);
+            float t;
+            t = __fsub_rn(x.x, a.x); va = __fmaf_rn(t, t, va);
+            t = __fsub_rn(x.x, b.x); vb = __fmaf_rn(t, t, vb);
+            t = __fsub_rn(x.y, a.y); va = __fmaf_rn(t, t, va);
+            t = __fsub_rn(x.y, b.y); vb = __fmaf_rn(t, t, vb);
+            t = __fsub_rn(x.z, a.z); va = __fmaf_rn(t, t, va);
+            t = __fsub_rn(x.z, b.z); vb = __fmaf_rn(t, t, vb);
+            t = __fsub_rn(x.w, a.w); va = __fmaf_rn(t, t, va);
+            t = __fsub_rn(x.w, b.w); vb = __fmaf_rn(t, t, vb);
+        }
+        float b1, b2;
+        int i1, i2;
+        pair_top2(va, j, vb, j + 1, has_b, b1, i1, b2, i2);
+        const float m = deciding<MODE>(D2, R, b1);
+        if (pair_certain(sb, sb.xnorm[R], m, v2s[R], d))
+            chg = decide_top2<MODE>(X, d, C, R, b1, i1, b2, i2, D2, idx, labels, prev, dmin, fp64_cnt, wide_cnt);
+        else {
+            fix = true;
+            sb.ub[R] = m;
+        }
+    } else if (fix) {
+        sb.ub[R] = deciding<MODE>(D2, R, FLT_MAX);
+    }
+    append_fixups(sb, fix, R);
+    if (MODE == MODE_ASSIGN && changed) {
+        const int c = warp_sum_i32(chg);
+        if (lane == 0 && c) atomicAdd(changed, c);
+    }
+}
+
 // Centers resident in shared memory (used when lane-per-row reads are conflict-free:
 // d odd or d = 2 mod 4).  Persistent CTAs copy the pass's centers once; each warp
 // then walks 32-row blocks of X.  A block is contiguous in X, so flat 16-byte
@@ -1379,6 +1438,20 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
             count_launches(1);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
+    } else if ((c.d & 3) == 0 && ((reinterpret_cast<uintptr_t>(c.X) | reinterpret_cast<uintptr_t>(C)) & 15u) == 0) {
+        const int grid = (int)((c.n + 255) / 256);
+        if (mode_round)
+            refine_direct_kernel<MODE_ROUND><<<grid, 256, 0, c.stream>>>(c.X, c.n, c.d, C, 0, c.cand1, c.tc_v2, sb,
+                                                                         c.D2, c.idx, nullptr, nullptr, nullptr,
+                                                                         nullptr, &c.st->argmin_fp64,
+                                                                         &c.st->argmin_wide);
+        else
+            refine_direct_kernel<MODE_ASSIGN><<<grid, 256, 0, c.stream>>>(c.X, c.n, c.d, C, k, c.cand1, c.tc_v2, sb,
+                                                                          nullptr, nullptr, labels, prev, changed,
+                                                                          dmin, &c.st->argmin_fp64,
+                                                                          &c.st->argmin_wide);
+        count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     } else {
         const int rthreads = 32 * refine_warps(c.d);
         const int grid = (int)((c.n + rthreads - 1) / rthreads);

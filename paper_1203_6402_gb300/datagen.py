@@ -80,3 +80,38 @@ def make(name: str, seed: int, n: int | None = None) -> np.ndarray:
     if w["kind"] == "gmm":
         return gauss_mixture(nn, w["d"], w["k_true"], w["R"], seed)
     return kdd_like(nn, seed)
+
+
+def batched_problems(count: int, seed: int, n_lo: int = 1_000, n_hi: int = 200_000, k_lo: int = 16,
+                     k_hi: int = 256, dims=(32, 64, 128), R: float = 10.0, rounds: int = 5, max_iter: int = 10):
+    """Descriptions of `count` independent GAUSSMIXTURE problems: n and k
+    log-uniform in [n_lo, n_hi] and [k_lo, k_hi] (k at most n), d uniform over
+    `dims`, l = 2k, each with its own data seed and run seed, and the offsets of
+    its rows in one concatenated X (row-major, float32), of its k x d centers and
+    of its labels."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), size=count)).astype(np.int64)
+    k = np.exp(rng.uniform(np.log(k_lo), np.log(k_hi), size=count)).astype(np.int64)
+    k = np.minimum(k, n)
+    d = rng.choice(np.asarray(dims), size=count)
+    probs = []
+    xo = co = lo = 0
+    for i in range(count):
+        probs.append(dict(x_offset=xo, n=int(n[i]), d=int(d[i]), k=int(k[i]), ell=2.0 * int(k[i]), rounds=rounds,
+                          max_iter=max_iter, seed=int(seed) * 100003 + i, data_seed=int(seed) * 7919 + i,
+                          c_offset=co, l_offset=lo, cand_offset=0))
+        xo += int(n[i]) * int(d[i])
+        co += int(k[i]) * int(d[i])
+        lo += int(n[i])
+    return probs
+
+
+def batched_points(problems, out=None) -> np.ndarray:
+    """The concatenated X of batched_problems (each problem its own mixture of k
+    components, centers ~ N(0, R I), unit-variance points), float32."""
+    total = sum(p["n"] * p["d"] for p in problems)
+    X = np.empty(total, dtype=np.float32) if out is None else out
+    for p in problems:
+        Xi = gauss_mixture(p["n"], p["d"], p["k"], 10.0, p["data_seed"])
+        X[p["x_offset"]: p["x_offset"] + p["n"] * p["d"]] = Xi.ravel()
+    return X

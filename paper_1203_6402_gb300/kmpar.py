@@ -25,7 +25,7 @@ PRECISIONS = {"fp32": KMPAR_FP32, "bf16": KMPAR_BF16, "bf16x3": KMPAR_BF16X3, "f
 EXPORTED = ["kmpar_init", "kmpar_round", "kmpar_weight", "kmpar_recluster", "kmpar_lloyd", "kmpar_cost",
             "kmpar_fit", "kmpar_state", "kmpar_get_stats", "kmpar_uniforms", "kmpar_set_timing",
             "kmpar_launch_count", "kmpar_cost_noalloc", "kmpar_destroy", "kmpar_release_cached_memory",
-            "kmpar_set_sampling",
+            "kmpar_set_sampling", "kmpar_batch_run", "kmpar_batch_cand_capacity",
             "kmpar_status_string", "kmpar_last_error"]
 
 
@@ -52,6 +52,22 @@ class kmpar_stats(ctypes.Structure):
                     recluster_warn=self.recluster_warn, kernel_ms=list(self.kernel_ms),
                     kernel_launches=list(self.kernel_launches), screen_rows=self.screen_rows,
                     screen_fallback=self.screen_fallback, screen_exact=self.screen_exact)
+
+
+class kmpar_problem(ctypes.Structure):
+    _fields_ = [("x_offset", ctypes.c_int64), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("ell", ctypes.c_double), ("rounds", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("c_offset", ctypes.c_int64), ("l_offset", ctypes.c_int64),
+                ("cand_offset", ctypes.c_int64)]
+
+
+class kmpar_problem_result(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("seed_cost", ctypes.c_double), ("final_cost", ctypes.c_double),
+                ("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("sample_near", ctypes.c_int64),
+                ("argmin_fp64", ctypes.c_int64), ("recluster_near", ctypes.c_int64)]
+
+    def to_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class KmparError(RuntimeError):
@@ -90,6 +106,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kmpar_set_sampling": (i32, [P, i32]),
         "kmpar_launch_count": (i64, []),
         "kmpar_cost_noalloc": (i32, [P, i64, i32, P, i32, ctypes.POINTER(f64), P]),
+        "kmpar_batch_cand_capacity": (i64, [f64, i32]),
+        "kmpar_batch_run": (i32, [P, ctypes.POINTER(kmpar_problem), i32, P, P, P, P,
+                                  ctypes.POINTER(kmpar_problem_result), P]),
         "kmpar_destroy": (None, [P]),
         "kmpar_release_cached_memory": (i32, []),
         "kmpar_status_string": (ctypes.c_char_p, [i32]),
@@ -164,6 +183,25 @@ def kmpar_fit(X_ptr: int, n: int, d: int, k: int, ell: float, rounds: int, seed:
     st = _check(load().kmpar_fit(X_ptr, n, d, k, ell, rounds, seed, precision, max_iter, centers_ptr,
                                  labels_ptr, ctypes.byref(sc), ctypes.byref(fc), ctypes.byref(it), flags, stream))
     return dict(seed_cost=sc.value, final_cost=fc.value, iters=it.value, status=st)
+
+
+def kmpar_batch_cand_capacity(ell: float, rounds: int) -> int:
+    return load().kmpar_batch_cand_capacity(ell, rounds)
+
+
+def kmpar_batch_run(X_ptr: int, problems: list, centers_ptr: int, labels_ptr: int | None = None,
+                    cand_ptr: int | None = None, w_ptr: int | None = None, stream: int = 0):
+    """problems: dicts with the kmpar_problem fields; returns (status, per-problem result dicts).
+    A per-problem capacity overflow is reported in its result (status 4), not raised."""
+    arr = (kmpar_problem * len(problems))()
+    for i, p in enumerate(problems):
+        for name, _ in kmpar_problem._fields_:
+            setattr(arr[i], name, p[name])
+    res = (kmpar_problem_result * len(problems))()
+    st = load().kmpar_batch_run(X_ptr, arr, len(problems), centers_ptr, labels_ptr, cand_ptr, w_ptr, res, stream)
+    if st not in (KMPAR_OK, KMPAR_WARN_FEW_CANDIDATES, KMPAR_ERR_CAPACITY):
+        _check(st)
+    return st, [r.to_dict() for r in res]
 
 
 def kmpar_state(ctx: int):

@@ -53,7 +53,7 @@ def test_traffic_record_is_used_only_for_the_captured_source(tmp_path, monkeypat
     import hashlib
     src = tmp_path / "paper_1203_6402_gb300" / "csrc"
     src.mkdir(parents=True)
-    (src / "nearest_tc.cu").write_bytes(b"kernel v1")
+    (src / "nearest_tc_kernel.cuh").write_bytes(b"kernel v1")
     sha = hashlib.sha256(b"kernel v1").hexdigest()[:16]
     (tmp_path / "profiles").mkdir()
     (tmp_path / "profiles" / "traffic.md").write_text(
@@ -62,7 +62,7 @@ def test_traffic_record_is_used_only_for_the_captured_source(tmp_path, monkeypat
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.traffic_record("tc::nearest_tc_kernel (assign)", "w1", "bf16") == (1.5e9, sha)
     assert bench.traffic_record("tc::nearest_tc_kernel (round)", "w1", "bf16") == (None, None)
-    (src / "nearest_tc.cu").write_bytes(b"kernel v2")
+    (src / "nearest_tc_kernel.cuh").write_bytes(b"kernel v2")
     assert bench.traffic_record("tc::nearest_tc_kernel (assign)", "w1", "bf16") == (None, sha)
 
 

@@ -16,6 +16,9 @@
  *   - Algorithm 1 (k-means++), in its weighted form, for step 8 Sec. 3.1
  *   - the exactly-l-per-round variant of step 4                  Sec. 5.3
  *   - Lloyd's iteration                                         Sec. 1, Sec. 3.1
+ *   - Lloyd's iteration on the weighted candidates (the alternative
+ *     reading of step 8: weighted k-means++, then local search on the
+ *     weighted set, as Sec. 3.3 leaves the reclustering open)   Sec. 3.3
  *
  * Arithmetic: coordinates are read as FP32 and widened to FP64; every distance,
  * probability, prefix sum and centroid is FP64.  The file must be compiled with
@@ -401,5 +404,52 @@ int64_t orc_lloyd(const float *X, int64_t n, int d, double *C, int64_t k, int64_
     }
     if (final_cost) *final_cost = cost;
     free(prev); free(sum); free(count);
+    return t;
+}
+
+/* ---------------------------------------------------------------------------
+ * Step 8 alternative: Lloyd's iteration on the weighted candidate set (Sec. 3.3
+ * step 8 reclusters the weighted candidates; Lloyd's local search of Sec. 1 /
+ * Sec. 3.1 with every candidate counted w times).  Each iteration assigns every
+ * candidate to its nearest center (FP64 difference form, lowest index on ties)
+ * and stops if no label changed or max_iter updates were made; otherwise center
+ * j becomes sum_c w_c c / sum_c w_c over its candidates (ascending candidate
+ * order, FP64; a center with no candidate keeps its place).  Returns the number
+ * of updates; *wcost = sum_c w_c d^2(c, nearest center) of the final centers.
+ * ------------------------------------------------------------------------- */
+int64_t orc_weighted_lloyd(const float *Cand, const int64_t *w, int64_t m, int d, double *C, int64_t k,
+                           int64_t max_iter, int64_t *labels, double *wcost) {
+    int64_t *prev = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+    double *d2 = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    double *sum = (double *)malloc(sizeof(double) * (size_t)(k * d > 0 ? k * d : 1));
+    int64_t *wsum = (int64_t *)malloc(sizeof(int64_t) * (size_t)(k > 0 ? k : 1));
+    int64_t t = 0;
+    for (;;) {
+        orc_assign(Cand, m, d, C, k, labels, d2, NULL);
+        if (t > 0) {
+            int64_t changed = 0;
+            for (int64_t c = 0; c < m; ++c) changed += (labels[c] != prev[c]);
+            if (changed == 0) break;
+        }
+        if (t == max_iter) break;
+        for (int64_t q = 0; q < k * d; ++q) sum[q] = 0.0;
+        for (int64_t j = 0; j < k; ++j) wsum[j] = 0;
+        for (int64_t c = 0; c < m; ++c) {
+            const int64_t j = labels[c];
+            wsum[j] += w[c];
+            for (int q = 0; q < d; ++q)
+                sum[j * d + q] = sum[j * d + q] + (double)w[c] * (double)Cand[c * (int64_t)d + q];
+        }
+        for (int64_t j = 0; j < k; ++j) {
+            if (wsum[j] == 0) continue;
+            for (int q = 0; q < d; ++q) C[j * d + q] = sum[j * d + q] / (double)wsum[j];
+        }
+        memcpy(prev, labels, sizeof(int64_t) * (size_t)m);
+        t++;
+    }
+    double cost = 0.0;
+    for (int64_t c = 0; c < m; ++c) cost = cost + (double)w[c] * d2[c];
+    if (wcost) *wcost = cost;
+    free(prev); free(d2); free(sum); free(wsum);
     return t;
 }

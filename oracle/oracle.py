@@ -64,6 +64,7 @@ def _load():
         "orc_weights": (None, [P, i64, i64, P]),
         "orc_recluster": (i32, [P, P, i64, i32, i64, u64, P, P]),
         "orc_lloyd": (i64, [P, i64, i32, P, i64, i64, P, P, P, P]),
+        "orc_weighted_lloyd": (i64, [P, P, i64, i32, P, i64, i64, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -229,6 +230,20 @@ class KMeansParResult:
     recluster_warn: bool = False
     seed_centers: np.ndarray = None
     seed_cost: float = 0.0
+
+
+def weighted_lloyd(cand_rows, w, C, max_iter: int):
+    """Lloyd's iteration on the weighted candidates (step 8 alternative, Sec. 3.3):
+    returns (centers FP64, labels, updates, weighted cost)."""
+    cand_rows = _f32(cand_rows)
+    w = np.ascontiguousarray(w, dtype=np.int64)
+    C = np.array(C, dtype=np.float64, copy=True, order="C")
+    m, d = cand_rows.shape
+    labels = np.empty(m, np.int64)
+    wc = ctypes.c_double(0.0)
+    it = _load().orc_weighted_lloyd(_p(cand_rows), _p(w), m, d, _p(C), C.shape[0], max_iter, _p(labels),
+                                    ctypes.byref(wc))
+    return C, labels, int(it), wc.value
 
 
 def kmeans_par(X, k: int, ell: float, rounds: int, seed: int, sampling: str = "bernoulli",

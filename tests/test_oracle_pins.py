@@ -444,3 +444,50 @@ def test_table1_gaussmixture_final_costs(orc):
         for name, vals in fin.items():
             printed = t1[name][2 * col + 1]
             assert abs(np.median(vals) / printed - 1) < 0.3, (name, R, np.median(vals), printed)
+
+
+# ----------------------------------------------------------------- step 8 alternative: weighted Lloyd
+def test_weighted_lloyd_hand_example(orc):
+    """Candidates 0, 1, 10 with weights 3, 1, 2 from centers (0, 10): the first
+    center moves to the weighted mean (3*0 + 1*1) / 4 = 0.25, then nothing changes."""
+    cand = np.array([[0.0], [1.0], [10.0]], np.float32)
+    C, lab, it, wc = orc.weighted_lloyd(cand, [3, 1, 2], [[0.0], [10.0]], 10)
+    assert it == 1 and list(lab) == [0, 0, 1]
+    assert C[0, 0] == 0.25 and C[1, 0] == 10.0
+    assert wc == 3 * 0.25 ** 2 + 0.75 ** 2
+
+
+def test_weighted_lloyd_unit_weights_is_lloyd(orc):
+    """w = 1 everywhere: exactly Lloyd's iteration on the candidate rows (the weighted
+    sum adds 1 * x, the same value as x)."""
+    X = datagen.gauss_mixture(600, 5, 8, 10.0, seed=71)
+    C0 = X[:8].astype(np.float64)
+    C1, l1, it1, _ = orc.weighted_lloyd(X, np.ones(600, np.int64), C0, 50)
+    C2, l2, it2, _, _, _ = orc.lloyd(X, C0, 50)
+    assert it1 == it2 and np.array_equal(l1, l2) and np.array_equal(C1, C2)
+
+
+def test_weighted_lloyd_is_lloyd_on_the_multiset(orc):
+    """Integer weights: the same as Lloyd's iteration on the multiset with every
+    candidate repeated w times (brute force of the definition)."""
+    rng = np.random.default_rng(5)
+    cand = datagen.gauss_mixture(300, 4, 6, 10.0, seed=72)
+    w = rng.integers(1, 6, size=300)
+    C0 = cand[:6].astype(np.float64)
+    C1, l1, it1, wc = orc.weighted_lloyd(cand, w, C0, 50)
+    big = np.repeat(cand, w, axis=0)
+    C2, l2, it2, fc2, _, near = orc.lloyd(big, C0, 50)
+    assert not near.any()
+    assert it1 == it2
+    assert np.array_equal(np.repeat(l1, w), l2)
+    np.testing.assert_allclose(C1, C2, rtol=1e-12, atol=1e-12)
+    assert math.isclose(wc, fc2, rel_tol=1e-12)
+
+
+def test_weighted_lloyd_never_raises_the_weighted_cost(orc):
+    cand = datagen.kdd_like(400, seed=73)
+    w = np.random.default_rng(6).integers(1, 50, size=400)
+    C0 = cand[::40][:10].astype(np.float64)
+    _, lab0, _, wc0 = orc.weighted_lloyd(cand, w, C0, 0)
+    _, _, it, wc = orc.weighted_lloyd(cand, w, C0, 30)
+    assert it >= 1 and wc <= wc0 * (1 + 1e-12)

@@ -168,6 +168,20 @@ KMPAR_API kmpar_status kmpar_weight(kmpar_ctx *ctx, int64_t *m_out, const int32_
 KMPAR_API kmpar_status kmpar_recluster(kmpar_ctx *ctx, float *centers_dev);
 
 /*
+ * Alg. 2 step 8, second half (optional): Lloyd's iteration on the weighted
+ * candidate set from the k centers in centers_dev (device, k x d FP32, updated in
+ * place), the reading of step 8 in which weighted k-means++ is followed by local
+ * search on the weighted candidates (Sec. 3.3 leaves the reclustering method
+ * open).  Each iteration assigns every candidate to its nearest center (the same
+ * rule as kmpar_lloyd) and stops if no label changed; otherwise center j becomes
+ * sum w_c c / sum w_c over its candidates (FP64 products and sums in ascending
+ * candidate order, rounded to FP32 once; a center without candidates keeps its
+ * place).  At most max_iter updates; *iters (host, nullable) receives their
+ * number.  Requires kmpar_weight.  Synchronises once per iteration.
+ */
+KMPAR_API kmpar_status kmpar_weighted_lloyd(kmpar_ctx *ctx, float *centers_dev, int32_t max_iter, int32_t *iters);
+
+/*
  * Lloyd's iteration (Sec. 1, Sec. 3.1) on X from the k centers in centers_dev
  * (device, k x d FP32, updated in place).  Each iteration assigns every point to
  * its nearest center (lowest index on ties) and stops if no label changed;
@@ -223,7 +237,8 @@ KMPAR_API kmpar_status kmpar_cost_noalloc(const float *X, int64_t n, int32_t d, 
  * flags & KMPAR_HOST_BUFFERS: X, centers_out and labels_out are HOST pointers
  * (copied in and out inside the call); otherwise device pointers.
  * flags & KMPAR_EXACT_SAMPLING: exactly floor(l) draws per round (see
- * kmpar_set_sampling).  seed_cost, final_cost and iters are host pointers
+ * kmpar_set_sampling).  (flags >> 8) & 255: updates of kmpar_weighted_lloyd on
+ * the candidates after the reclustering (0: none, the default).  seed_cost, final_cost and iters are host pointers
  * (nullable).  labels_out is nullable.
  */
 #define KMPAR_HOST_BUFFERS 1

@@ -127,7 +127,7 @@ void free_ctx(kmp::Ctx &c) {
                     c.piece, c.psum, c.rc_cmass, c.rc_sync, c.rc_err, c.chunk, c.tc_v2,
                     c.tc_anchor, c.tc_anchor_part, c.lloyd_rec, c.ex_keys, c.ex_ws, c.ex_ties,
                     c.tc_ncol, c.tc_tscale, c.tc_xscale, c.tc_ub, c.tc_cimg, c.tc_cscale, c.tc_thr,
-                    c.tc_lst, c.tc_lcnt, c.fix_rows2, c.fix_cnt2, c.rCT};
+                    c.tc_lst, c.tc_lcnt, c.fix_rows2, c.fix_cnt2, c.rCT, c.wl_lab[0], c.wl_lab[1]};
     // stream-ordered: the memory returns to the pool once the context's work is done
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, c.stream);
@@ -402,6 +402,39 @@ kmpar_status kmpar_recluster(kmpar_ctx *ctx, float *centers_dev) {
     return warn ? KMPAR_WARN_FEW_CANDIDATES : KMPAR_OK;
 }
 
+kmpar_status kmpar_weighted_lloyd(kmpar_ctx *ctx, float *centers_dev, int32_t max_iter, int32_t *iters) {
+    if (!ctx) return fail(nullptr, KMPAR_ERR_ARG, "ctx is NULL");
+    kmp::Ctx &c = ctx->c;
+    if (!centers_dev) return fail(&c, KMPAR_ERR_ARG, "centers_dev is NULL");
+    if (max_iter < 0) return fail(&c, KMPAR_ERR_ARG, "max_iter < 0");
+    if (!c.weighted) return fail(&c, KMPAR_ERR_STATE, "weighted Lloyd before weight");
+    if (c.d > 4096) return fail(&c, KMPAR_ERR_UNSUPPORTED, "weighted Lloyd supports d <= 4096");
+    for (int b = 0; b < 2; ++b)
+        if (!c.wl_lab[b]) KMP_CUDA(&c, alloc(c, &c.wl_lab[b], (size_t)c.cap_total), "alloc candidate labels");
+    int32_t m = 0;
+    KMP_CUDA(&c, cudaMemcpyAsync(&m, &c.st->m, sizeof(m), cudaMemcpyDeviceToHost, c.stream), "read m");
+    KMP_CUDA(&c, cudaStreamSynchronize(c.stream), "sync");
+    int *changed = reinterpret_cast<int *>(c.partials + c.num_partials - 1);   // the last partial slot
+    const int np = kmp::assign_num_partials(m, c.d);
+    if (np + 1 > c.num_partials) return fail(&c, KMPAR_ERR_UNSUPPORTED, "candidate set larger than the point set");
+    int cur = 0, t = 0;
+    for (;; ++t) {
+        KMP_CUDA(&c, cudaMemsetAsync(changed, 0, sizeof(int), c.stream), "memset changed");
+        KMP_CUDA(&c, kmp::launch_assign(c.C, m, c.d, centers_dev, c.k, c.wl_lab[cur], t > 0 ? c.wl_lab[cur ^ 1] : nullptr,
+                                        changed, c.partials, np, &c.st->argmin_fp64, c.stream),
+                 "candidate assignment");
+        int h = 0;
+        KMP_CUDA(&c, cudaMemcpyAsync(&h, changed, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "read changed");
+        KMP_CUDA(&c, cudaStreamSynchronize(c.stream), "sync");
+        if (t > 0 && h == 0) break;
+        if (t == max_iter) break;
+        KMP_CUDA(&c, kmp::launch_weighted_centroids(c, m, c.wl_lab[cur], centers_dev), "weighted centroids");
+        cur ^= 1;
+    }
+    if (iters) *iters = t;
+    return KMPAR_OK;
+}
+
 // Each buffer is allocated once.  A call that failed part way (out of memory)
 // leaves the buffers it got in place; the next call allocates the missing ones, and
 // Lloyd runs only once all of them exist.
@@ -627,6 +660,8 @@ kmpar_status kmpar_fit(const float *X, int64_t n, int32_t d, int32_t k, double e
         st = kmpar_recluster(ctx, Cd);
         if (st == KMPAR_WARN_FEW_CANDIDATES) { warn = st; st = KMPAR_OK; }
     }
+    const int wl_iters = (flags >> 8) & 0xFF;
+    if (st == KMPAR_OK && wl_iters > 0) st = kmpar_weighted_lloyd(ctx, Cd, wl_iters, nullptr);
     // Lloyd's first assignment is made with the seed centers: its cost is the seed cost
     std::vector<double> hist(max_iter >= 0 ? (size_t)max_iter + 1 : 1);
     if (st == KMPAR_OK) st = kmpar_lloyd(ctx, Cd, max_iter, Ld, iters, final_cost, hist.data());

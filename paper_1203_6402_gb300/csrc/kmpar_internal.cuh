@@ -66,6 +66,7 @@ struct Ctx {
     float *rD2 = nullptr;         // recluster D^2 (cap_total)
     double *rc_cmass = nullptr;   // recluster chunk masses, 2 x ceil(cap_total / 32), then 2 x 1024 CTA totals
     float *rCT = nullptr;         // recluster grid form: candidates transposed (d x cap_total padded to 32)
+    int32_t *wl_lab[2] = {nullptr, nullptr};   // weighted Lloyd: candidate labels (cap_total each)
     void *rc_sync = nullptr;      // recluster grid barrier / pick flag
     int *rc_err = nullptr;        // recluster timeout flag
     int32_t *chosen = nullptr;    // k
@@ -232,6 +233,7 @@ cudaError_t launch_weights(Ctx &c);
 cudaError_t launch_recluster(Ctx &c, float *centers);
 size_t recluster_sync_bytes();
 size_t recluster_grid_floats(const Ctx &c);   // floats of the transposed copy the grid form needs (0: none)
+cudaError_t launch_weighted_centroids(const Ctx &c, int m, const int32_t *lab, float *centers);
 cudaError_t launch_assign(const float *X, int64_t n, int d, const float *C, int k, int32_t *labels,
                           const int32_t *prev, int *changed, double *partials, int nparts,
                           unsigned long long *fp64_cnt, cudaStream_t s);

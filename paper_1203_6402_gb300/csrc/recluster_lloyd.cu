@@ -705,6 +705,71 @@ cudaError_t launch_recluster(Ctx &c, float *centers) {
 
 size_t recluster_sync_bytes() { return sizeof(RcSync); }
 
+// ------------------------------------------------------------------ step 8 alternative
+// Lloyd's iteration on the weighted candidates: the centroid half.  One block per
+// center j: the block walks the candidate labels in chunks of its size, keeps the
+// members of j in ascending order (ordered block compaction) and thread q adds
+// w_c * c_q in FP64 (rounded product, then rounded sum, as the definition is
+// written); the center becomes the FP64 quotient by sum w_c rounded to FP32, or
+// keeps its place when no candidate is its nearest.
+constexpr int kWlThreads = 256;
+constexpr int kWlMaxQ = 16;   // d <= 16 * kWlThreads
+
+__global__ void __launch_bounds__(kWlThreads) weighted_centroid_kernel(const float *__restrict__ cand,
+                                                                       const long long *__restrict__ w,
+                                                                       const int32_t *__restrict__ lab, int m, int d,
+                                                                       float *__restrict__ centers) {
+    __shared__ int mem[kWlThreads];
+    __shared__ int wcnt[kWlThreads / 32];
+    const int j = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    double acc[kWlMaxQ];
+#pragma unroll
+    for (int u = 0; u < kWlMaxQ; ++u) acc[u] = 0.0;
+    long long wsum = 0;
+    for (int base = 0; base < m; base += kWlThreads) {
+        const int i = base + tid;
+        const bool mine = i < m && lab[i] == j;
+        const unsigned mask = __ballot_sync(0xffffffffu, mine);
+        if (lane == 0) wcnt[wid] = __popc(mask);
+        __syncthreads();
+        int before = 0, tot = 0;
+        for (int q = 0; q < kWlThreads / 32; ++q) {
+            if (q < wid) before += wcnt[q];
+            tot += wcnt[q];
+        }
+        if (mine) mem[before + __popc(mask & ((1u << lane) - 1u))] = i;
+        __syncthreads();
+        for (int t = 0; t < tot; ++t) {
+            const int c = mem[t];
+            const double wc = (double)w[c];
+            if (tid == 0) wsum += w[c];
+#pragma unroll
+            for (int u = 0; u < kWlMaxQ; ++u) {
+                const int q = tid + u * kWlThreads;
+                if (q < d) acc[u] = __dadd_rn(acc[u], __dmul_rn(wc, (double)cand[(int64_t)c * d + q]));
+            }
+        }
+        __syncthreads();
+    }
+    __shared__ long long s_w;
+    if (tid == 0) s_w = wsum;
+    __syncthreads();
+    if (s_w == 0) return;
+#pragma unroll
+    for (int u = 0; u < kWlMaxQ; ++u) {
+        const int q = tid + u * kWlThreads;
+        if (q < d) centers[(int64_t)j * d + q] = (float)(acc[u] / (double)s_w);
+    }
+}
+
+cudaError_t launch_weighted_centroids(const Ctx &c, int m, const int32_t *lab, float *centers) {
+    if (c.d > kWlMaxQ * kWlThreads) return cudaErrorInvalidValue;
+    weighted_centroid_kernel<<<c.k, kWlThreads, 0, c.stream>>>(c.C, c.w, lab, m, c.d, centers);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ Lloyd: centroids
 // A stable counting sort of the points by label (per-block histograms, a chunked
 // column scan, one warp per block scattering in point order) puts every cluster's

@@ -25,7 +25,7 @@ PRECISIONS = {"fp32": KMPAR_FP32, "bf16": KMPAR_BF16, "bf16x3": KMPAR_BF16X3, "f
 EXPORTED = ["kmpar_init", "kmpar_round", "kmpar_weight", "kmpar_recluster", "kmpar_lloyd", "kmpar_cost",
             "kmpar_fit", "kmpar_state", "kmpar_get_stats", "kmpar_uniforms", "kmpar_set_timing",
             "kmpar_launch_count", "kmpar_cost_noalloc", "kmpar_destroy", "kmpar_release_cached_memory",
-            "kmpar_set_sampling", "kmpar_batch_run", "kmpar_batch_cand_capacity",
+            "kmpar_set_sampling", "kmpar_batch_run", "kmpar_batch_cand_capacity", "kmpar_weighted_lloyd",
             "kmpar_status_string", "kmpar_last_error"]
 
 
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kmpar_launch_count": (i64, []),
         "kmpar_cost_noalloc": (i32, [P, i64, i32, P, i32, ctypes.POINTER(f64), P]),
         "kmpar_batch_cand_capacity": (i64, [f64, i32]),
+        "kmpar_weighted_lloyd": (i32, [P, P, i32, ctypes.POINTER(i32)]),
         "kmpar_batch_run": (i32, [P, ctypes.POINTER(kmpar_problem), i32, P, P, P, P,
                                   ctypes.POINTER(kmpar_problem_result), P]),
         "kmpar_destroy": (None, [P]),
@@ -153,6 +154,12 @@ def kmpar_weight(ctx: int):
 
 def kmpar_recluster(ctx: int, centers_ptr: int) -> int:
     return _check(load().kmpar_recluster(ctx, centers_ptr), ctx)
+
+
+def kmpar_weighted_lloyd(ctx: int, centers_ptr: int, max_iter: int) -> int:
+    it = ctypes.c_int32()
+    _check(load().kmpar_weighted_lloyd(ctx, centers_ptr, max_iter, ctypes.byref(it)), ctx)
+    return it.value
 
 
 def kmpar_lloyd(ctx: int, centers_ptr: int, max_iter: int, labels_ptr: int | None = None, hist: bool = False):

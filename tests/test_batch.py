@@ -126,7 +126,9 @@ def test_batch_capacity_overflow_is_per_problem(km, monkeypatch):
     st, res = km.kmpar_batch_run(Xd.data_ptr(), probs, C.data_ptr())
     assert st == km.KMPAR_ERR_CAPACITY
     assert res[1]["status"] == km.KMPAR_ERR_CAPACITY
-    assert res[0]["status"] == km.KMPAR_OK and res[2]["status"] == km.KMPAR_OK
+    # about 11 candidates for k >= 20: these two finish with the few-candidates warning
+    assert res[0]["status"] in (km.KMPAR_OK, km.KMPAR_WARN_FEW_CANDIDATES)
+    assert res[2]["status"] in (km.KMPAR_OK, km.KMPAR_WARN_FEW_CANDIDATES)
     assert res[0]["final_cost"] > 0 and res[2]["final_cost"] > 0
 
 

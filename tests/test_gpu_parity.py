@@ -439,3 +439,36 @@ def test_state_machine_and_arguments(km):
         g.round(3)
     assert e.value.status == km.KMPAR_ERR_STATE
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_weighted_lloyd_on_candidates_matches_oracle(km, orc, precision):
+    """Step 8's optional second half: Lloyd's iteration on the weighted candidates
+    from the weighted k-means++ centers, against the oracle's from the same seed."""
+    X = datagen.gauss_mixture(8000, 15, 30, 10.0, seed=61)
+    Xd = _dev(X)
+    g = km.KMeansPar(Xd, 30, 60.0, 5, 8, precision=precision)
+    for r in range(1, 6):
+        g.round(r)
+    cand, w = g.candidates()
+    C, _ = g.recluster()
+    C0 = C.cpu().numpy().astype(np.float64)
+    it = km.kmpar_weighted_lloyd(g.ctx, C.data_ptr(), 25)
+    Cg = C.cpu().numpy()
+    g.close()
+    cand, w = cand.cpu().numpy(), w.cpu().numpy()
+    oC, olab, oit, owc = orc.weighted_lloyd(X[cand], w, C0, 25)
+    assert it == oit and it >= 1
+    np.testing.assert_allclose(Cg, oC, rtol=1e-6, atol=1e-6 * (np.abs(oC).max() + 1))
+
+
+def test_fit_with_weighted_lloyd_flag(km, orc):
+    X = datagen.gauss_mixture(6000, 15, 25, 10.0, seed=62)
+    n, d, k = X.shape[0], X.shape[1], 25
+    Xd = _dev(X)
+    Cd = torch.empty(k, d, dtype=torch.float32, device="cuda")
+    r = km.kmpar_fit(Xd.data_ptr(), n, d, k, 50.0, 5, 3, km.KMPAR_FP32, 50, Cd.data_ptr(), None, flags=10 << 8)
+    par = orc.kmeans_par(X, k, 50.0, 5, 3)
+    oC, _, _, _ = orc.weighted_lloyd(X[par.cand], par.w, par.seed_centers.astype(np.float64), 10)
+    _, _, oit, ofc, _, _ = orc.lloyd(X, oC, 50)
+    assert math.isclose(r["final_cost"], ofc, rel_tol=1e-4)

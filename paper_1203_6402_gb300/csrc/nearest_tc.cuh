@@ -41,8 +41,8 @@ struct TcParams {
     const float *ncol;       // BF16N / FP8: ||c'||^2 per pass-local center (pad rows: 1e30)
     const float *tscale;     // BF16N / FP8: per center tile scale (1 for BF16N)
     const unsigned int *cmax_bits;
-    int32_t *cand1;          // EPI_PAIR: per row, first center of the best screened pair (-1: none)
-    float *v2;               // EPI_PAIR: per row, smallest screened value outside that pair (key-truncated)
+    int32_t *cand1;          // EPI_PAIR: per row, first center of the best screened group (-1: none)
+    float *v2;               // EPI_PAIR: per row, smallest screened value outside that group (key-truncated)
     const int *nrows_dev;    // EPI_LIST: number of listed rows
     const float *thr;        // EPI_LIST: per listed row, the screened-value threshold
     int32_t *lst;            // EPI_LIST: per listed row, 4 x kListSlots pass-local center numbers
@@ -51,6 +51,7 @@ struct TcParams {
     int *fix_cnt;
     unsigned long long *fp64_cnt;
     int *err;                // first timeout code, 0 if none
+    int group;               // EPI_PAIR: centers per screened group, 2 or 4 (BF16N and FP8 only)
     int ksteps;              // MMA instructions per tile (32 bytes of K each)
     uint32_t vmask;          // value bits of a key (set by launch_nearest_tc)
 };

@@ -180,11 +180,13 @@ constexpr size_t smem_bytes() {
            (EPI == EPI_LIST ? sizeof(int32_t) * kListSlots * kEpiThreads : 0);
 }
 
-// bounded wait on an mbarrier phase; false if this or another warp gave up
+// bounded wait on an mbarrier phase; false if this or another warp gave up.  The
+// first probes spin (the hand-offs between the producer, the MMA warp and the
+// epilogue are on the critical path of every tile), later ones back off.
 __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatile int *abort, int *err, int code) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = clock64();
-    for (;;) {
+    for (int it = 0;; ++it) {
         if (mbar_try(bar, parity)) return true;
         if (*abort) return false;
         if (clock64() - t0 > kWaitCycles) {
@@ -192,7 +194,7 @@ __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatil
             atomicCAS(err, 0, code);
             return false;
         }
-        __nanosleep(64);
+        if (it >= 256) __nanosleep(64);
     }
 }
 
@@ -209,7 +211,10 @@ __device__ __forceinline__ float screened(uint32_t raw, float f, float nc) {
     return NE ? __fmaf_rn(__uint_as_float(raw), f, nc) : __uint_as_float(raw);
 }
 
-template <int KA, int BN, int S, int A16B, int FMT, int EPI>
+// GS: centers per screened group (2: pairs; 4: groups of four adjacent centers,
+// whose minimum costs fewer ALU operations per value; the refine then computes all
+// four exactly)
+template <int KA, int BN, int S, int A16B, int FMT, int EPI, int GS>
 __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int mode_round) {
     using C = Cfg<KA, BN>;
     constexpr bool NE = FMT == FMT_BF16N || FMT == FMT_FP8;
@@ -407,6 +412,23 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
                                 float v[8];
 #pragma unroll
                                 for (int u = 0; u < 8; ++u) v[u] = screened<NE>(r[cc][q + u], f, nv[u]);
+                                if (GS == 4) {
+                                    // two groups of four: minimum, key, one top-2 insertion
+                                    const uint32_t gc = (uint32_t)(((c + cc) * 32 + q) >> 2);
+                                    const float m0 = fminf(min3f(v[0], v[1], v[2]), v[3]);
+                                    const float m1 = fminf(min3f(v[4], v[5], v[6]), v[7]);
+                                    const float a = __uint_as_float((__float_as_uint(m0) & vmask) | gc);
+                                    const float b = __uint_as_float((__float_as_uint(m1) & vmask) | (gc + 1));
+                                    const float lo = fminf(a, b), hi = fmaxf(a, b);
+                                    if ((q >> 3) & 1) {
+                                        k2b = min3f(fmaxf(k1b, lo), k2b, hi);
+                                        k1b = fminf(k1b, lo);
+                                    } else {
+                                        k2a = min3f(fmaxf(k1a, lo), k2a, hi);
+                                        k1a = fminf(k1a, lo);
+                                    }
+                                    continue;
+                                }
                                 const uint32_t pc = (uint32_t)(((c + cc) * 32 + q) >> 1);
                                 const float m0 = fminf(v[0], v[1]);
                                 const float m1 = fminf(v[2], v[3]);
@@ -502,12 +524,12 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
                 // of different pairs are near ties that the certainty test sends to
                 // the fix-up anyway.  Group 0's columns start at 0 within the tile,
                 // group q+1's at (q+1) GW; a key carries the pair number in the group.
-                J1 = T1 * BN + 2 * (int)(__float_as_uint(K1) & ~kValMask);
+                J1 = T1 * BN + GS * (int)(__float_as_uint(K1) & ~kValMask);
 #pragma unroll
                 for (int q = 0; q < kGroups - 1; ++q) {
                     const float m1v = __uint_as_float(__float_as_uint(o1[q]) & kValMask);
                     const float k1v = __uint_as_float(__float_as_uint(K1) & kValMask);
-                    const int oj = ot[q] * BN + (q + 1) * C::GW + 2 * (int)(__float_as_uint(o1[q]) & ~kValMask);
+                    const int oj = ot[q] * BN + (q + 1) * C::GW + GS * (int)(__float_as_uint(o1[q]) & ~kValMask);
                     if (m1v < k1v || (m1v == k1v && oj < J1)) { K2 = min3f(K1, o2[q], K2); K1 = o1[q]; J1 = oj; }
                     else K2 = min3f(K2, o1[q], o2[q]);
                 }
@@ -529,12 +551,12 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
     }
 }
 
-template <int KA, int BN, int S, int A16B, int FMT, int EPI>
+template <int KA, int BN, int S, int A16B, int FMT, int EPI, int GS>
 cudaError_t launch_cfg(const TcParams &p, int mode_round, int grid, cudaStream_t s) {
     static_assert(smem_bytes<KA, BN, S, A16B, EPI>() <= 227 * 1024, "shared memory");
     static_assert(S <= 8 && A16B <= 4, "barrier arrays");
     constexpr size_t sm = smem_bytes<KA, BN, S, A16B, EPI>();
-    auto kern = nearest_tc_kernel<KA, BN, S, A16B, FMT, EPI>;
+    auto kern = nearest_tc_kernel<KA, BN, S, A16B, FMT, EPI, GS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     kern<<<grid, kThreads, sm, s>>>(p, mode_round);
@@ -543,11 +565,11 @@ cudaError_t launch_cfg(const TcParams &p, int mode_round, int grid, cudaStream_t
 }
 
 // the configurations of one format; KA = K atoms of 128 bytes
-template <int FMT, int EPI>
+template <int FMT, int EPI, int GS = 2>
 cudaError_t dispatch_fmt(const TcParams &p, int mode_round, int KA, int grid, cudaStream_t s) {
-    if (KA == 1) return launch_cfg<1, 256, 4, 4, FMT, EPI>(p, mode_round, grid, s);
-    if (KA == 2) return launch_cfg<2, 256, 2, 2, FMT, EPI>(p, mode_round, grid, s);
-    if (KA == 3) return launch_cfg<3, 128, 2, 2, FMT, EPI>(p, mode_round, grid, s);
+    if (KA == 1) return launch_cfg<1, 256, 4, 4, FMT, EPI, GS>(p, mode_round, grid, s);
+    if (KA == 2) return launch_cfg<2, 256, 2, 2, FMT, EPI, GS>(p, mode_round, grid, s);
+    if (KA == 3) return launch_cfg<3, 128, 2, 2, FMT, EPI, GS>(p, mode_round, grid, s);
     return cudaErrorInvalidValue;
 }
 

@@ -804,11 +804,13 @@ __global__ void __launch_bounds__(256) refine_kernel(const float *__restrict__ X
 }
 
 // Per-row refine for rows of d = 0 mod 4 floats (16-byte aligned): one thread per
-// row sums both centers of its screened pair with two interleaved exact FP32
-// chains (ascending coordinates, bit-identical to dist2_fp32) from 16-byte loads
-// of the point row and the two center rows; no shared-memory staging, so the
-// kernel runs at full occupancy and the rows come through L1.
-template <int MODE>
+// row sums every center of its screened group (G adjacent centers) with G
+// interleaved exact FP32 chains (ascending coordinates, bit-identical to
+// dist2_fp32) from 16-byte loads of the point row and the center rows; no
+// shared-memory staging, so the kernel runs at full occupancy and the rows come
+// through L1.  The lexicographic top-2 of the group then goes through the same
+// certainty test and decision as a pair.
+template <int MODE, int G>
 __global__ void __launch_bounds__(256) refine_direct_kernel(const float *__restrict__ X, int64_t n, int d,
                                                            const float *__restrict__ C, int c_cnt,
                                                            const int32_t *__restrict__ cand1,
@@ -824,27 +826,37 @@ __global__ void __launch_bounds__(256) refine_direct_kernel(const float *__restr
     bool fix = valid && j < 0;
     int chg = 0;
     if (valid && j >= 0) {
-        const bool has_b = j + 1 < end;
         const float4 *x4 = reinterpret_cast<const float4 *>(X + R * d);
-        const float4 *a4 = reinterpret_cast<const float4 *>(C + (int64_t)j * d);
-        const float4 *b4 = reinterpret_cast<const float4 *>(C + (int64_t)(has_b ? j + 1 : j) * d);
-        float va = 0.f, vb = 0.f;
-#pragma unroll 4
+        const float4 *c4[G];
+#pragma unroll
+        for (int u = 0; u < G; ++u) c4[u] = reinterpret_cast<const float4 *>(C + (int64_t)min(j + u, end - 1) * d);
+        float v[G];
+#pragma unroll
+        for (int u = 0; u < G; ++u) v[u] = 0.f;
+#pragma unroll 2
         for (int p = 0; p < (d >> 2); ++p) {
-            const float4 x = __ldg(x4 + p), a = __ldg(a4 + p), b = __ldg(b4 + p);
-            float t;
-            t = __fsub_rn(x.x, a.x); va = __fmaf_rn(t, t, va);
-            t = __fsub_rn(x.x, b.x); vb = __fmaf_rn(t, t, vb);
-            t = __fsub_rn(x.y, a.y); va = __fmaf_rn(t, t, va);
-            t = __fsub_rn(x.y, b.y); vb = __fmaf_rn(t, t, vb);
-            t = __fsub_rn(x.z, a.z); va = __fmaf_rn(t, t, va);
-            t = __fsub_rn(x.z, b.z); vb = __fmaf_rn(t, t, vb);
-            t = __fsub_rn(x.w, a.w); va = __fmaf_rn(t, t, va);
-            t = __fsub_rn(x.w, b.w); vb = __fmaf_rn(t, t, vb);
+            const float4 x = __ldg(x4 + p);
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                const float4 c = __ldg(c4[u] + p);
+                float t;
+                t = __fsub_rn(x.x, c.x); v[u] = __fmaf_rn(t, t, v[u]);
+                t = __fsub_rn(x.y, c.y); v[u] = __fmaf_rn(t, t, v[u]);
+                t = __fsub_rn(x.z, c.z); v[u] = __fmaf_rn(t, t, v[u]);
+                t = __fsub_rn(x.w, c.w); v[u] = __fmaf_rn(t, t, v[u]);
+            }
         }
-        float b1, b2;
-        int i1, i2;
-        pair_top2(va, j, vb, j + 1, has_b, b1, i1, b2, i2);
+        // lexicographic (value, center number) top-2 over the group's real centers
+        float b1 = FLT_MAX, b2 = FLT_MAX;
+        int i1 = INT_MAX, i2 = -1;
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            if (j + u < end) {
+                if (v[u] < b1) { b2 = b1; i2 = i1 == INT_MAX ? -1 : i1; b1 = v[u]; i1 = j + u; }
+                else if (v[u] < b2) { b2 = v[u]; i2 = j + u; }
+            }
+        }
+        if (i2 < 0) b2 = FLT_MAX;
         const float m = deciding<MODE>(D2, R, b1);
         if (pair_certain(sb, sb.xnorm[R], m, v2s[R], d))
             chg = decide_top2<MODE>(X, d, C, R, b1, i1, b2, i2, D2, idx, labels, prev, dmin, fp64_cnt, wide_cnt);
@@ -1410,6 +1422,13 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
     p.cmax_bits = c.tc_cmax;
     p.cand1 = c.cand1; p.v2 = c.tc_v2; p.fix_rows = c.fix_rows; p.fix_cnt = c.fix_cnt;
     p.fp64_cnt = &c.st->argmin_fp64; p.err = c.tc_err;
+    const int cap_rows = mode_round ? c.cap_round : k;
+    const ResidentPlan rp = resident_plan(cap_rows, c.d);
+    // the direct refine serves rows of d = 0 mod 4; with it, formats that add the norms
+    // in the epilogue screen groups of four centers (fewer ALU operations per value)
+    const bool direct = rp.parts == 0 && (c.d & 3) == 0 &&
+                        ((reinterpret_cast<uintptr_t>(c.X) | reinterpret_cast<uintptr_t>(C)) & 15u) == 0;
+    p.group = (direct && tc::tc_norms_in_epilogue(fmt)) ? 4 : 2;
     cudaEvent_t ev = nullptr;
     if ((e = timing_begin(c, &ev)) != cudaSuccess) return e;
     if ((e = tc::launch_nearest_tc(p, mode_round, tc::EPI_PAIR, c.num_sms, c.stream)) != cudaSuccess) return e;
@@ -1418,8 +1437,6 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
     sb.xnorm = c.tc_xnorm; sb.cmax_bits = c.tc_cmax; sb.st = c.st;
     sb.fix_rows = c.fix_rows; sb.fix_cnt = c.fix_cnt; sb.ub = c.tc_ub;
     tc::tc_bound(c.d, fmt, &sb.ep, &sb.en, &sb.ec);
-    const int cap_rows = mode_round ? c.cap_round : k;
-    const ResidentPlan rp = resident_plan(cap_rows, c.d);
     if (rp.parts > 0) {
         const int rw = rp.warps;
         const size_t rsm = resident_smem_bytes(rp.hold, c.d, rw);
@@ -1438,18 +1455,21 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
             count_launches(1);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-    } else if ((c.d & 3) == 0 && ((reinterpret_cast<uintptr_t>(c.X) | reinterpret_cast<uintptr_t>(C)) & 15u) == 0) {
+    } else if (direct) {
         const int grid = (int)((c.n + 255) / 256);
-        if (mode_round)
-            refine_direct_kernel<MODE_ROUND><<<grid, 256, 0, c.stream>>>(c.X, c.n, c.d, C, 0, c.cand1, c.tc_v2, sb,
-                                                                         c.D2, c.idx, nullptr, nullptr, nullptr,
-                                                                         nullptr, &c.st->argmin_fp64,
+#define KMP_DIRECT(G)                                                                                           \
+    if (mode_round)                                                                                             \
+        refine_direct_kernel<MODE_ROUND, G><<<grid, 256, 0, c.stream>>>(c.X, c.n, c.d, C, 0, c.cand1, c.tc_v2, sb, \
+                                                                        c.D2, c.idx, nullptr, nullptr, nullptr,  \
+                                                                        nullptr, &c.st->argmin_fp64,             \
+                                                                        &c.st->argmin_wide);                     \
+    else                                                                                                        \
+        refine_direct_kernel<MODE_ASSIGN, G><<<grid, 256, 0, c.stream>>>(c.X, c.n, c.d, C, k, c.cand1, c.tc_v2,  \
+                                                                         sb, nullptr, nullptr, labels, prev,     \
+                                                                         changed, dmin, &c.st->argmin_fp64,      \
                                                                          &c.st->argmin_wide);
-        else
-            refine_direct_kernel<MODE_ASSIGN><<<grid, 256, 0, c.stream>>>(c.X, c.n, c.d, C, k, c.cand1, c.tc_v2, sb,
-                                                                          nullptr, nullptr, labels, prev, changed,
-                                                                          dmin, &c.st->argmin_fp64,
-                                                                          &c.st->argmin_wide);
+        if (p.group == 4) { KMP_DIRECT(4) } else { KMP_DIRECT(2) }
+#undef KMP_DIRECT
         count_launches(1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     } else {

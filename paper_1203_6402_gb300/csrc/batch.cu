@@ -28,7 +28,11 @@
 #include <cstdlib>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "kmpar_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace kmp {
 void set_thread_error(const std::string &m);
@@ -126,10 +130,13 @@ struct BShared {
     int base[kBMaxK + 1];      // step 8: the chosen candidates; Lloyd: cluster offsets
     int wpos[kBW];
     int s_int[4];
+    double s_dslot;
+    int s_islot;
+    unsigned long long s_uslot;
     unsigned long long s_near, s_fp64, s_rnear;
 };
 
-// One pass over the problem's rows against `cnt` centers: the rows of C_rows (a
+// One pass over the rows [r0, r1) of a problem against `cnt` centers: the rows of C_rows (a
 // center matrix, stride d) or, when cand is given, X rows cand[begin + r].  Each
 // thread holds one row's coordinates in registers (padded to DP with zeros: they
 // add exact zeros to the sums) and keeps the lexicographic (value, center number)
@@ -141,9 +148,9 @@ struct BShared {
 //           the lower center number
 //   ASSIGN  the best, re-decided in FP64 against the runner-up inside the window
 // Returns the block's FP64 sum of the stored distances (D^2 or the chosen
-// center's distance) and adds the number of changed labels to *changed.
+// center's distance) and sets *changed to the block's number of changed labels.
 template <int DP, int MODE>
-__device__ double dist_pass(BShared<DP> &sh, const float *__restrict__ Xp, int64_t n, int d,
+__device__ double dist_pass(BShared<DP> &sh, const float *__restrict__ Xp, int64_t r0, int64_t r1, int d,
                             const float *__restrict__ C_rows, const int32_t *__restrict__ cand, int begin, int cnt,
                             float *D2, int32_t *idx, int32_t *lab, int *changed, unsigned long long *fp64_cnt) {
     const int tid = threadIdx.x;
@@ -151,9 +158,9 @@ __device__ double dist_pass(BShared<DP> &sh, const float *__restrict__ Xp, int64
     double acc_sum = 0.0;
     int chg = 0;
     unsigned long long nfp64 = 0;
-    for (int64_t base = 0; base < n; base += kBT) {
+    for (int64_t base = r0; base < r1; base += kBT) {
         const int64_t pt = base + tid;
-        const bool valid = pt < n;
+        const bool valid = pt < r1;
         const float *xrow = Xp + (valid ? pt : 0) * (int64_t)d;
         float xr[DP];
 #pragma unroll
@@ -315,6 +322,52 @@ __device__ __forceinline__ int bmin_i32(int v, int *sh) {
 }
 
 __device__ __forceinline__ int bmax_i32(int v, int *sh) { return -bmin_i32(-v, sh); }
+
+// ---- a problem split over a thread-block cluster of CS blocks (CS = 1: one block)
+// Barrier of the cluster (hardware; its arrive/wait pair orders memory at cluster
+// scope, and the fence makes the global writes of this block visible first).
+template <int CS>
+__device__ __forceinline__ void csync() {
+    if (CS > 1) {
+        __threadfence();
+        cg::this_cluster().sync();
+    } else {
+        __syncthreads();
+    }
+}
+
+// Sum over the cluster's blocks, in rank order, of a block-uniform value: every
+// block gets the same result.
+template <int CS, typename T>
+__device__ __forceinline__ T csum(T v, T *slot) {
+    if (CS == 1) return v;
+    __syncthreads();
+    if (threadIdx.x == 0) *slot = v;
+    cg::this_cluster().sync();
+    T r = 0;
+    for (int q = 0; q < CS; ++q) r += *cg::this_cluster().map_shared_rank(slot, q);
+    cg::this_cluster().sync();   // no block overwrites its slot before every block has read it
+    return r;
+}
+
+// Exclusive prefix in rank order and total of a block-uniform count.
+template <int CS>
+__device__ __forceinline__ int cprefix(int v, int *slot, int *total) {
+    if (CS == 1) { *total = v; return 0; }
+    __syncthreads();
+    if (threadIdx.x == 0) *slot = v;
+    cg::this_cluster().sync();
+    const int me = (int)cg::this_cluster().block_rank();
+    int before = 0, tot = 0;
+    for (int q = 0; q < CS; ++q) {
+        const int c = *cg::this_cluster().map_shared_rank(slot, q);
+        if (q < me) before += c;
+        tot += c;
+    }
+    cg::this_cluster().sync();
+    *total = tot;
+    return before;
+}
 
 // Knuth's TwoSum: (s, c) += x with s the rounded sum and c the accumulated
 // rounding errors (all FP32, each operation rounded to nearest)

@@ -216,6 +216,11 @@ def run_batched(args, rank, world):
     C = torch.empty(sum(p["k"] * p["d"] for p in probs), dtype=torch.float32, device=dev)
     L = torch.empty(sum(p["n"] for p in probs), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
+    # the schedule the autotuner measured fastest (paper_1203_6402_gb300/batch_tune.py)
+    from paper_1203_6402_gb300 import batch_tune
+    table = batch_tune.load_table()
+    if table is not None:
+        km.kmpar_batch_set_split(int(table["rows_per_block"]))
 
     def step():
         st, res = km.kmpar_batch_run(X.data_ptr(), probs, C.data_ptr(), L.data_ptr(), stream=stream.cuda_stream)
@@ -290,6 +295,8 @@ def run_batched(args, rank, world):
                                 f"d in {{32, 64, 128}}, k log-uniform [16, 256], l = 2k, r = 5, 10 Lloyd updates; "
                                 f"one kmpar_batch_run per step (one block per problem, largest first)"),
                    "sum_n": int(sum(p["n"] for p in probs)), "x_gb": xbytes / 1e9,
+                   "schedule": ({"rows_per_block": table["rows_per_block"], "source": "batch_tuning.json"}
+                                if table is not None else {"rows_per_block": 25000, "source": "default"}),
                    "parallelism": f"replicas x{world}", "l2": f"inputs larger than L2 (X {xbytes / 1e9:.1f} GB)"},
         "dist_evals_per_step": evals, "gpu_launches": int(launches), "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s (FP32 issue)",

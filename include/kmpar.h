@@ -264,8 +264,11 @@ KMPAR_API kmpar_status kmpar_fit(const float *X, int64_t n, int32_t d, int32_t k
  * l + 10 sqrt(l) + 64 <= 4096.  results (host, count entries) receive each
  * problem's outcome; a problem whose round overflows its capacity stops there
  * with status KMPAR_ERR_CAPACITY, the others are unaffected.  Work space comes
- * from the library's pool; the problems run one thread block each, largest
- * first, in one kernel launch per dimension class.  Synchronises.
+ * from the library's pool; a problem runs in one thread block, or in a
+ * thread-block cluster of 2, 4 or 8 blocks when it has more than 25,000 rows
+ * (each block a contiguous range of rows; the cluster combines its sums and its
+ * ordered draws in rank order; see kmpar_batch_set_split), largest problems
+ * first, one kernel launch per (dimension class, cluster size).  Synchronises.
  */
 typedef struct {
     int64_t x_offset;     /* first float of the problem's rows in X               */
@@ -290,6 +293,12 @@ typedef struct {
     int64_t argmin_fp64;  /* argmin decisions re-decided in FP64                  */
     int64_t recluster_near; /* reclustering targets within 1e-6 of a boundary     */
 } kmpar_problem_result;
+
+/* Schedule of kmpar_batch_run (process-wide): a problem of more than
+ * rows_per_block rows is split over a thread-block cluster of 2, 4 or 8 blocks
+ * (default 25,000; 0: never split).  Results do not depend on it beyond the
+ * association of FP64 sums.  KMPAR_ERR_ARG for a negative value. */
+KMPAR_API kmpar_status kmpar_batch_set_split(int32_t rows_per_block);
 
 /* Candidate slots a problem of oversampling l and r rounds needs in cand_out/w_out. */
 KMPAR_API int64_t kmpar_batch_cand_capacity(double ell, int32_t rounds);

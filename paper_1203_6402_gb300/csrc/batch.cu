@@ -24,6 +24,7 @@
 #include <float.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <vector>
@@ -130,6 +131,7 @@ struct BShared {
     int base[kBMaxK + 1];      // step 8: the chosen candidates; Lloyd: cluster offsets
     int wpos[kBW];
     int s_int[4];
+    int wl_tot[kBMaxK];        // Lloyd (rank 0): label totals over the cluster
     double s_dslot;
     int s_islot;
     unsigned long long s_uslot;
@@ -183,29 +185,30 @@ __device__ double dist_pass(BShared<DP> &sh, const float *__restrict__ Xp, int64
             __syncthreads();
             if (valid) {
                 int r = 0;
-                for (; r + 4 <= nt; r += 4) {
-                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-                    const float4 *c0 = reinterpret_cast<const float4 *>(sh.tile + (r + 0) * DP);
-                    const float4 *c1 = reinterpret_cast<const float4 *>(sh.tile + (r + 1) * DP);
-                    const float4 *c2 = reinterpret_cast<const float4 *>(sh.tile + (r + 2) * DP);
-                    const float4 *c3 = reinterpret_cast<const float4 *>(sh.tile + (r + 3) * DP);
+                // NCH independent chains (one per center) interleaved per coordinate
+                constexpr int NCH = 8;
+                for (; r + NCH <= nt; r += NCH) {
+                    float acc[NCH];
+#pragma unroll
+                    for (int u = 0; u < NCH; ++u) acc[u] = 0.f;
 #pragma unroll
                     for (int q4 = 0; q4 < DP / 4; ++q4) {
-                        const float4 u0 = c0[q4], u1 = c1[q4], u2 = c2[q4], u3 = c3[q4];
-                        sq_acc(xr[4 * q4 + 0], u0.x, a0); sq_acc(xr[4 * q4 + 0], u1.x, a1);
-                        sq_acc(xr[4 * q4 + 0], u2.x, a2); sq_acc(xr[4 * q4 + 0], u3.x, a3);
-                        sq_acc(xr[4 * q4 + 1], u0.y, a0); sq_acc(xr[4 * q4 + 1], u1.y, a1);
-                        sq_acc(xr[4 * q4 + 1], u2.y, a2); sq_acc(xr[4 * q4 + 1], u3.y, a3);
-                        sq_acc(xr[4 * q4 + 2], u0.z, a0); sq_acc(xr[4 * q4 + 2], u1.z, a1);
-                        sq_acc(xr[4 * q4 + 2], u2.z, a2); sq_acc(xr[4 * q4 + 2], u3.z, a3);
-                        sq_acc(xr[4 * q4 + 3], u0.w, a0); sq_acc(xr[4 * q4 + 3], u1.w, a1);
-                        sq_acc(xr[4 * q4 + 3], u2.w, a2); sq_acc(xr[4 * q4 + 3], u3.w, a3);
-                    }
-                    const float av[4] = {a0, a1, a2, a3};
+                        float4 cv[NCH];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
+                        for (int u = 0; u < NCH; ++u) cv[u] = reinterpret_cast<const float4 *>(sh.tile + (r + u) * DP)[q4];
+#pragma unroll
+                        for (int u = 0; u < NCH; ++u) sq_acc(xr[4 * q4 + 0], cv[u].x, acc[u]);
+#pragma unroll
+                        for (int u = 0; u < NCH; ++u) sq_acc(xr[4 * q4 + 1], cv[u].y, acc[u]);
+#pragma unroll
+                        for (int u = 0; u < NCH; ++u) sq_acc(xr[4 * q4 + 2], cv[u].z, acc[u]);
+#pragma unroll
+                        for (int u = 0; u < NCH; ++u) sq_acc(xr[4 * q4 + 3], cv[u].w, acc[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < NCH; ++u) {
                         const int j = begin + t0 + r + u;
-                        const float a = av[u];
+                        const float a = acc[u];
                         if (a < b2) {
                             if (a < b1) { b2 = b1; i2 = i1; b1 = a; i1 = j; }
                             else { b2 = a; i2 = j; }
@@ -379,15 +382,24 @@ __device__ __forceinline__ void two_sum_add(float &s, float &c, float x) {
     s = t;
 }
 
-template <int DP>
-__global__ void __launch_bounds__(kBT, DP == 128 ? 1 : (DP == 64 ? 2 : 3)) batch_kernel(BArgs a, int first) {
+// One problem per cluster of CS blocks (CS = 1: one block).  Block rank r of the
+// cluster owns the contiguous rows [r0, r1); every per-point step runs on the
+// block's own rows, and the cluster combines in rank order: phi and the Lloyd
+// cost and change counts (sums), the round draws (each block appends its draws in
+// ascending point order after those of the lower ranks), and Lloyd's counting sort
+// (label offsets over (rank, warp) in order).  Step 8 runs in rank 0.
+template <int DP, int CS>
+__global__ void __launch_bounds__(kBT, DP == 128 ? 1 : 2) batch_kernel(BArgs a, int first) {
     __shared__ BShared<DP> sh;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int pi = a.order[first + blockIdx.x];
+    const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    const int pi = a.order[first + blockIdx.x / CS];
     const BProb P = a.probs[pi];
     const float *X = a.X + P.x_off;
     const int64_t n = P.n;
     const int d = P.d, k = P.k;
+    const int64_t per = (n + CS - 1) / CS;
+    const int64_t r0 = min(n, (int64_t)rank * per), r1 = min(n, r0 + per);
     float *D2 = a.D2 + P.p_off;
     int32_t *idx = a.idx + P.p_off, *lab = a.lab + P.p_off, *perm = a.perm + P.p_off;
     int32_t *cand = a.cand + P.m_off, *w = a.w + P.m_off;
@@ -395,36 +407,56 @@ __global__ void __launch_bounds__(kBT, DP == 128 ? 1 : (DP == 64 ? 2 : 3)) batch
     float *C = a.centers + P.c_off;
     if (tid == 0) {
         sh.s_near = 0; sh.s_fp64 = 0; sh.s_rnear = 0;
-        // Alg. 2 step 1: the first center, uniform over the problem's points
-        const double u = uniform53(0, 0, TAG_INIT, P.seed);
-        int64_t i0 = (int64_t)floor(__dmul_rn(u, (double)n));
-        if (i0 >= n) i0 = n - 1;
-        cand[0] = (int32_t)i0;
+        if (rank == 0) {
+            // Alg. 2 step 1: the first center, uniform over the problem's points
+            const double u = uniform53(0, 0, TAG_INIT, P.seed);
+            int64_t i0 = (int64_t)floor(__dmul_rn(u, (double)n));
+            if (i0 >= n) i0 = n - 1;
+            cand[0] = (int32_t)i0;
+        }
     }
-    __syncthreads();
+    csync<CS>();
     // step 2: D^2 to the first center and psi
-    double phi = dist_pass<DP, BM_FIRST>(sh, X, n, d, nullptr, cand, 0, 1, D2, idx, nullptr, nullptr, &sh.s_fp64);
+    double phi = csum<CS>(dist_pass<DP, BM_FIRST>(sh, X, r0, r1, d, nullptr, cand, 0, 1, D2, idx, nullptr, nullptr,
+                                                  &sh.s_fp64),
+                          &sh.s_dslot);
     int m = 1, status = KMPAR_OK;
     for (int r = 1; r <= P.rounds; ++r) {
-        // step 4: independent draws, appended in ascending point order
+        // step 4: independent draws of the block's rows; p and the near-draw rule as
+        // in the single-problem path
+        auto draw = [&](int64_t pt, bool &take, unsigned long long &near) {
+            const float dd = D2[pt];
+            double pr = 0.0;
+            if (phi > 0.0) pr = fmin(1.0, __ddiv_rn(__dmul_rn(P.ell, (double)dd), phi));
+            const double u = uniform53((uint64_t)pt, (uint32_t)r, TAG_SAMPLE, P.seed);
+            if (dd > 0.f && fabs(u - pr) <= 1e-5) {
+                // the FP32 D^2 could decide this draw: use the FP64 distance of the definition
+                const double d64 = dist2_fp64(X + pt * d, X + (int64_t)cand[idx[pt]] * d, d);
+                pr = fmin(1.0, __ddiv_rn(__dmul_rn(P.ell, d64), phi));
+            }
+            if (fabs(u - pr) <= 1e-6) ++near;
+            take = u < pr;
+        };
+        // the block's place among the cluster's draws (a counting pass first)
+        int mine = 0;
+        if (CS > 1) {
+            unsigned long long dummy = 0;
+            int cntl = 0;
+            for (int64_t pt = r0 + tid; pt < r1; pt += kBT) {
+                bool take;
+                draw(pt, take, dummy);
+                cntl += take;
+            }
+            mine = bsum_i32(cntl, sh.redi);
+        }
+        int appended_all = 0;
+        const int before_blocks = cprefix<CS>(mine, &sh.s_islot, &appended_all);
         int appended = 0;
         unsigned long long near = 0;
-        for (int64_t base = 0; base < n; base += kBT) {
+        for (int64_t base = r0; base < r1; base += kBT) {
             const int64_t pt = base + tid;
             bool take = false;
-            if (pt < n) {
-                const float dd = D2[pt];
-                double pr = 0.0;
-                if (phi > 0.0) pr = fmin(1.0, __ddiv_rn(__dmul_rn(P.ell, (double)dd), phi));
-                const double u = uniform53((uint64_t)pt, (uint32_t)r, TAG_SAMPLE, P.seed);
-                if (dd > 0.f && fabs(u - pr) <= 1e-5) {
-                    // the FP32 D^2 could decide this draw: use the FP64 distance of the definition
-                    const double d64 = dist2_fp64(X + pt * d, X + (int64_t)cand[idx[pt]] * d, d);
-                    pr = fmin(1.0, __ddiv_rn(__dmul_rn(P.ell, d64), phi));
-                }
-                if (fabs(u - pr) <= 1e-6) ++near;
-                take = u < pr;
-            }
+            if (pt < r1) draw(pt, take, near);
             const unsigned mask = __ballot_sync(0xffffffffu, take);
             if (lane == 0) sh.wpos[wid] = __popc(mask);
             __syncthreads();
@@ -434,137 +466,179 @@ __global__ void __launch_bounds__(kBT, DP == 128 ? 1 : (DP == 64 ? 2 : 3)) batch
                 tot += sh.wpos[i];
             }
             if (take) {
-                const int pos = appended + before + __popc(mask & ((1u << lane) - 1u));
+                const int pos = before_blocks + appended + before + __popc(mask & ((1u << lane) - 1u));
                 if (pos < P.cap_round) cand[m + pos] = (int32_t)pt;
             }
             appended += tot;
             __syncthreads();   // wpos is rewritten by the next chunk
         }
         if (near) atomicAdd(&sh.s_near, near);
-        if (appended > P.cap_round) { status = KMPAR_ERR_CAPACITY; break; }
-        __syncthreads();       // the batch's row numbers are visible to the whole block
+        if (CS == 1) appended_all = appended;
+        if (appended_all > P.cap_round) { status = KMPAR_ERR_CAPACITY; break; }
+        csync<CS>();           // the batch's row numbers are visible to the whole cluster
         // step 5: D^2 and idx against the batch, then phi
-        phi = dist_pass<DP, BM_ROUND>(sh, X, n, d, nullptr, cand, m, appended, D2, idx, nullptr, nullptr,
-                                      &sh.s_fp64);
-        m += appended;
+        phi = csum<CS>(dist_pass<DP, BM_ROUND>(sh, X, r0, r1, d, nullptr, cand, m, appended_all, D2, idx, nullptr,
+                                               nullptr, &sh.s_fp64),
+                       &sh.s_dslot);
+        m += appended_all;
     }
     BRes res{};
     res.m = m;
     if (status == KMPAR_OK) {
         // step 7: weights
-        for (int j = tid; j < m; j += kBT) w[j] = 0;
-        __syncthreads();
-        for (int64_t pt = tid; pt < n; pt += kBT) atomicAdd(&w[idx[pt]], 1);
-        __syncthreads();
-        // step 8: weighted k-means++ over the m candidates
-        const int q = (m + kBT - 1) / kBT;
-        const int lo = min(m, tid * q), hi = min(m, lo + q);
-        int *chosen = sh.base;
+        for (int j = (int)(rank * kBT) + tid; j < m; j += CS * kBT) w[j] = 0;
+        csync<CS>();
+        for (int64_t pt = r0 + tid; pt < r1; pt += kBT) atomicAdd(&w[idx[pt]], 1);
+        csync<CS>();
+        // step 8 (rank 0): weighted k-means++ over the m candidates
         bool warn = false;
-        for (int t = 0; t < k; ++t) {
-            double local = 0.0;
-            for (int j = lo; j < hi; ++j)
-                local += t == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)rD2[j]);
-            double total;
-            const double excl = bscan_f64(local, sh.red, &total);
-            if (!(total > 0.0)) {
-                // positive mass exhausted: the remaining centers repeat the first chosen one
-                const int src = t > 0 ? chosen[0] : 0;
-                for (int s2 = t; s2 < k; ++s2) {
-                    for (int qq = tid; qq < d; qq += kBT) C[(int64_t)s2 * d + qq] = X[(int64_t)cand[src] * d + qq];
-                    if (tid == 0) chosen[s2] = src;
-                }
-                warn = true;
-                break;
-            }
-            const double target = __dmul_rn(uniform53((uint64_t)t, 0, TAG_RECLUSTER, P.seed), total);
-            int mine = INT_MAX;
-            double cum0 = 0.0, cum = 0.0, run = excl;
-            for (int j = lo; j < hi; ++j) {
-                const double e = t == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)rD2[j]);
-                const double pre = run;
-                run = run + e;
-                if (run > target) { mine = j; cum0 = pre; cum = run; break; }
-            }
-            int pick = bmin_i32(mine, sh.redi);
-            if (pick == INT_MAX) {
-                // the target rounded past every prefix: the last candidate with positive mass
-                int lastp = -1;
+        if (rank == 0) {
+            const int q = (m + kBT - 1) / kBT;
+            const int lo = min(m, tid * q), hi = min(m, lo + q);
+            int *chosen = sh.base;
+            for (int t = 0; t < k; ++t) {
+                double local = 0.0;
                 for (int j = lo; j < hi; ++j)
-                    if ((t == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)rD2[j])) > 0.0) lastp = j;
-                pick = bmax_i32(lastp, sh.redi);
-                if (tid == 0) atomicAdd(&sh.s_rnear, 1ull);
-            } else if (mine == pick &&
-                       (fabs(target - cum0) <= 1e-6 * total || fabs(cum - target) <= 1e-6 * total)) {
-                atomicAdd(&sh.s_rnear, 1ull);
+                    local += t == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)rD2[j]);
+                double total;
+                const double excl = bscan_f64(local, sh.red, &total);
+                if (!(total > 0.0)) {
+                    // positive mass exhausted: the remaining centers repeat the first chosen one
+                    const int src = t > 0 ? chosen[0] : 0;
+                    for (int s2 = t; s2 < k; ++s2) {
+                        for (int qq = tid; qq < d; qq += kBT)
+                            C[(int64_t)s2 * d + qq] = X[(int64_t)cand[src] * d + qq];
+                        if (tid == 0) chosen[s2] = src;
+                    }
+                    warn = true;
+                    break;
+                }
+                const double target = __dmul_rn(uniform53((uint64_t)t, 0, TAG_RECLUSTER, P.seed), total);
+                int hit = INT_MAX;
+                double cum0 = 0.0, cum = 0.0, run = excl;
+                for (int j = lo; j < hi; ++j) {
+                    const double e = t == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)rD2[j]);
+                    const double pre = run;
+                    run = run + e;
+                    if (run > target) { hit = j; cum0 = pre; cum = run; break; }
+                }
+                int pick = bmin_i32(hit, sh.redi);
+                if (pick == INT_MAX) {
+                    // the target rounded past every prefix: the last candidate with positive mass
+                    int lastp = -1;
+                    for (int j = lo; j < hi; ++j)
+                        if ((t == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)rD2[j])) > 0.0) lastp = j;
+                    pick = bmax_i32(lastp, sh.redi);
+                    if (tid == 0) atomicAdd(&sh.s_rnear, 1ull);
+                } else if (hit == pick &&
+                           (fabs(target - cum0) <= 1e-6 * total || fabs(cum - target) <= 1e-6 * total)) {
+                    atomicAdd(&sh.s_rnear, 1ull);
+                }
+                if (tid == 0) chosen[t] = pick;
+                const float *prow = X + (int64_t)cand[pick] * d;
+                for (int qq = tid; qq < DP; qq += kBT) {
+                    const float v = qq < d ? prow[qq] : 0.f;
+                    sh.tile[qq] = v;   // the pick's row, zero-padded to DP
+                    if (qq < d) C[(int64_t)t * d + qq] = v;
+                }
+                __syncthreads();
+                // D^2 of every candidate to the centers drawn so far: the candidate's row
+                // is loaded into registers first (all loads in flight at once), then the
+                // exact FP32 chain (t = x_q - c_q, fma, q ascending; padded zeros add 0)
+                for (int j = tid; j < m; j += kBT) {
+                    const float *xj = X + (int64_t)cand[j] * d;
+                    float xr[DP];
+#pragma unroll
+                    for (int q = 0; q < DP; ++q) xr[q] = q < d ? __ldg(xj + q) : 0.f;
+                    float v = 0.f;
+#pragma unroll
+                    for (int q = 0; q < DP; ++q) sq_acc(xr[q], sh.tile[q], v);
+                    rD2[j] = t == 0 ? v : fminf(rD2[j], v);
+                }
+                __syncthreads();
             }
-            if (tid == 0) chosen[t] = pick;
-            const float *prow = X + (int64_t)cand[pick] * d;
-            for (int qq = tid; qq < d; qq += kBT) C[(int64_t)t * d + qq] = prow[qq];
-            __syncthreads();
-            // D^2 of every candidate to the centers drawn so far
-            const float *crow = C + (int64_t)t * d;
-            for (int j = tid; j < m; j += kBT) {
-                const float v = dist2_fp32(X + (int64_t)cand[j] * d, crow, d);
-                rD2[j] = t == 0 ? v : fminf(rD2[j], v);
-            }
-            __syncthreads();
         }
         if (warn) status = KMPAR_WARN_FEW_CANDIDATES;
-        __syncthreads();
+        csync<CS>();           // the seed centers are visible to the whole cluster
         // Lloyd's iteration from the seed centers
         int it = 0;
         double cost = 0.0;
         for (;; ++it) {
             int chg = 0;
-            cost = dist_pass<DP, BM_ASSIGN>(sh, X, n, d, C, nullptr, 0, k, nullptr, nullptr, lab,
-                                            it > 0 ? &chg : nullptr, &sh.s_fp64);
+            const double part = dist_pass<DP, BM_ASSIGN>(sh, X, r0, r1, d, C, nullptr, 0, k, nullptr, nullptr, lab,
+                                                         it > 0 ? &chg : nullptr, &sh.s_fp64);
+            cost = csum<CS>(part, &sh.s_dslot);
+            if (it > 0) chg = csum<CS>(chg, &sh.s_islot);
             if (it == 0) res.seed_cost = cost;
             if (it > 0 && chg == 0) break;
             if (it == P.max_iter) break;
-            // stable counting sort by label: warp wr owns the contiguous rows [wr npw, (wr+1) npw)
-            const int64_t npw = (n + kBW - 1) / kBW;
-            const int64_t r0 = min(n, (int64_t)wid * npw), r1 = min(n, r0 + npw);
+            // stable counting sort by label: warp wr of block r owns the contiguous rows
+            // [r0 + wr npw, r0 + (wr+1) npw); offsets run over (rank, warp) in order
+            const int64_t npw = (r1 - r0 + kBW - 1) / kBW;
+            const int64_t w0 = min(r1, r0 + (int64_t)wid * npw), w1 = min(r1, w0 + npw);
             for (int l = tid; l < kBW * kBMaxK; l += kBT) (&sh.hist[0][0])[l] = 0;
             __syncthreads();
-            for (int64_t c0 = r0; c0 < r1; c0 += 32) {
+            for (int64_t c0 = w0; c0 < w1; c0 += 32) {
                 const int64_t pt = c0 + lane;
-                const int l = pt < r1 ? lab[pt] : -1;
+                const int l = pt < w1 ? lab[pt] : -1;
                 const unsigned peers = __match_any_sync(0xffffffffu, l);
                 if (l >= 0 && lane == __ffs(peers) - 1) sh.hist[wid][l] += __popc(peers);
                 __syncwarp();
             }
-            __syncthreads();
-            if (tid == 0) {
-                int acc = 0;
-                for (int l = 0; l < k; ++l) {
-                    sh.base[l] = acc;
-                    for (int i = 0; i < kBW; ++i) acc += sh.hist[i][l];
+            csync<CS>();
+            if (rank == 0) {
+                // label totals over the cluster, their prefix, then every (rank, warp)
+                // count replaced by its running offset (written into the owning block)
+                for (int l = tid; l < k; l += kBT) {
+                    int tot = 0;
+                    for (int q2 = 0; q2 < CS; ++q2) {
+                        const int(*hq)[kBMaxK] = CS > 1 ? cg::this_cluster().map_shared_rank(sh.hist, q2) : sh.hist;
+                        for (int i = 0; i < kBW; ++i) tot += hq[i][l];
+                    }
+                    sh.wl_tot[l] = tot;
                 }
-                sh.base[k] = acc;
-            }
-            __syncthreads();
-            for (int l = tid; l < k; l += kBT) {
-                int run2 = sh.base[l];
-                for (int i = 0; i < kBW; ++i) {
-                    const int c = sh.hist[i][l];
-                    sh.hist[i][l] = run2;
-                    run2 += c;
+                __syncthreads();
+                if (tid == 0) {
+                    int acc = 0;
+                    for (int l = 0; l < k; ++l) {
+                        sh.base[l] = acc;
+                        acc += sh.wl_tot[l];
+                    }
+                    sh.base[k] = acc;
                 }
+                __syncthreads();
+                for (int l = tid; l < k; l += kBT) {
+                    int run2 = sh.base[l];
+                    for (int q2 = 0; q2 < CS; ++q2) {
+                        int(*hq)[kBMaxK] = CS > 1 ? cg::this_cluster().map_shared_rank(sh.hist, q2) : sh.hist;
+                        for (int i = 0; i < kBW; ++i) {
+                            const int c = hq[i][l];
+                            hq[i][l] = run2;
+                            run2 += c;
+                        }
+                    }
+                }
+                __syncthreads();
+                if (CS > 1)
+                    for (int q2 = 1; q2 < CS; ++q2) {
+                        int *bq = cg::this_cluster().map_shared_rank(sh.base, q2);
+                        for (int l = tid; l <= k; l += kBT) bq[l] = sh.base[l];
+                    }
             }
-            __syncthreads();
-            for (int64_t c0 = r0; c0 < r1; c0 += 32) {
+            csync<CS>();
+            for (int64_t c0 = w0; c0 < w1; c0 += 32) {
                 const int64_t pt = c0 + lane;
-                const int l = pt < r1 ? lab[pt] : -1;
+                const int l = pt < w1 ? lab[pt] : -1;
                 const unsigned peers = __match_any_sync(0xffffffffu, l);
                 if (l >= 0) perm[sh.hist[wid][l] + __popc(peers & ((1u << lane) - 1u))] = (int32_t)pt;
                 __syncwarp();
                 if (l >= 0 && lane == __ffs(peers) - 1) sh.hist[wid][l] += __popc(peers);
                 __syncwarp();
             }
-            __syncthreads();
-            // centroids: member coordinates in ascending point order, compensated FP32
-            for (int64_t pq = tid; pq < (int64_t)k * d; pq += kBT) {
+            csync<CS>();
+            // centroids: member coordinates in ascending point order, compensated FP32;
+            // the (center, coordinate) pairs are shared out over the cluster
+            for (int64_t pq = (int64_t)rank * kBT + tid; pq < (int64_t)k * d; pq += (int64_t)CS * kBT) {
                 const int j = (int)(pq / d), qq = (int)(pq % d);
                 const int b0 = sh.base[j], b1 = sh.base[j + 1];
                 if (b1 == b0) continue;   // an empty cluster keeps its center
@@ -572,23 +646,25 @@ __global__ void __launch_bounds__(kBT, DP == 128 ? 1 : (DP == 64 ? 2 : 3)) batch
                 for (int i = b0; i < b1; ++i) two_sum_add(s, c, X[(int64_t)perm[i] * d + qq]);
                 C[pq] = (float)(((double)s + (double)c) / (double)(b1 - b0));
             }
-            __syncthreads();
+            csync<CS>();
         }
         res.iters = it;
         res.final_cost = cost;
         if (a.labels_out)
-            for (int64_t pt = tid; pt < n; pt += kBT) a.labels_out[P.l_off + pt] = lab[pt];
+            for (int64_t pt = r0 + tid; pt < r1; pt += kBT) a.labels_out[P.l_off + pt] = lab[pt];
     }
     if (a.cand_out)
-        for (int j = tid; j < m && j < P.cap_total; j += kBT) a.cand_out[P.cand_off + j] = cand[j];
+        for (int j = rank * kBT + tid; j < m && j < P.cap_total; j += CS * kBT) a.cand_out[P.cand_off + j] = cand[j];
     if (a.w_out && status != KMPAR_ERR_CAPACITY)
-        for (int j = tid; j < m; j += kBT) a.w_out[P.cand_off + j] = w[j];
-    __syncthreads();
-    if (tid == 0) {
+        for (int j = rank * kBT + tid; j < m; j += CS * kBT) a.w_out[P.cand_off + j] = w[j];
+    const unsigned long long nr = csum<CS>(sh.s_near, &sh.s_uslot);
+    const unsigned long long nf = csum<CS>(sh.s_fp64, &sh.s_uslot);
+    const unsigned long long nrc = csum<CS>(sh.s_rnear, &sh.s_uslot);
+    if (rank == 0 && tid == 0) {
         res.status = status;
-        res.sample_near = sh.s_near;
-        res.argmin_fp64 = sh.s_fp64;
-        res.recluster_near = sh.s_rnear;
+        res.sample_near = nr;
+        res.argmin_fp64 = nf;
+        res.recluster_near = nrc;
         a.res[pi] = res;
     }
 }
@@ -619,18 +695,63 @@ kmpar_status batch_fail(kmpar_status s, const std::string &m) {
     return s;
 }
 
-template <int DP>
-cudaError_t launch_class(const kmp::BArgs &a, int first, int count, cudaStream_t s) {
+// rows per block a problem is cut into: problems larger than this run as a cluster
+// (kmpar_batch_set_split; 0: never split)
+std::atomic<int64_t> g_rows_per_block{25000};
+
+int cluster_size(int64_t n) {
+    const int64_t rpb = g_rows_per_block.load(std::memory_order_relaxed);
+    int cs = 1;
+    while (rpb > 0 && cs < 8 && (n + cs - 1) / cs > rpb) cs *= 2;
+    return cs;
+}
+
+template <int DP, int CS>
+cudaError_t launch_cs(const kmp::BArgs &a, int first, int count, cudaStream_t s) {
     if (count == 0) return cudaSuccess;
-    kmp::batch_kernel<DP><<<count, kmp::kBT, 0, s>>>(a, first);
+    if (CS == 1) {
+        kmp::batch_kernel<DP, 1><<<count, kmp::kBT, 0, s>>>(a, first);
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(count * CS));
+        cfg.blockDim = dim3(kmp::kBT);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, kmp::batch_kernel<DP, CS>, a, first);
+        if (e != cudaSuccess) return e;
+    }
     kmp::count_launches(1);
     return cudaGetLastError();
+}
+
+template <int DP>
+cudaError_t launch_class(const kmp::BArgs &a, int cs, int first, int count, cudaStream_t s) {
+    switch (cs) {
+        case 1: return launch_cs<DP, 1>(a, first, count, s);
+        case 2: return launch_cs<DP, 2>(a, first, count, s);
+        case 4: return launch_cs<DP, 4>(a, first, count, s);
+        case 8: return launch_cs<DP, 8>(a, first, count, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace
 }  // namespace kmp
 
 extern "C" {
+
+kmpar_status kmpar_batch_set_split(int32_t rows_per_block) {
+    if (rows_per_block < 0) return kmp::batch_fail(KMPAR_ERR_ARG, "rows_per_block < 0");
+    kmp::g_rows_per_block.store(rows_per_block, std::memory_order_relaxed);
+    return KMPAR_OK;
+}
 
 int64_t kmpar_batch_cand_capacity(double ell, int32_t rounds) {
     if (!(ell > 0.0) || rounds < 0) return 0;
@@ -672,19 +793,22 @@ kmpar_status kmpar_batch_run(const float *X, const kmpar_problem *problems, int3
         const int dp = q.d <= 32 ? 32 : (q.d <= 64 ? 64 : 128);
         work[(size_t)i] = (double)q.n * dp * (1.0 + q.rounds * q.ell + (double)(q.max_iter + 1) * q.k);
     }
-    // each dimension class in one launch, largest problems first
+    // one launch per (dimension class, cluster size), largest problems first in each
     std::vector<int32_t> order;
     order.reserve((size_t)count);
-    int first[3] = {0, 0, 0}, cnt[3] = {0, 0, 0};
+    struct Cls { int dp, cs, first, count; };
+    std::vector<Cls> classes;
     for (int c = 0; c < 3; ++c) {
-        first[c] = (int)order.size();
         const int lo = c == 0 ? 1 : (c == 1 ? 33 : 65), hi = c == 0 ? 32 : (c == 1 ? 64 : 128);
-        std::vector<int32_t> ids;
-        for (int i = 0; i < count; ++i)
-            if (problems[i].d >= lo && problems[i].d <= hi) ids.push_back(i);
-        std::stable_sort(ids.begin(), ids.end(), [&](int32_t x, int32_t y) { return work[x] > work[y]; });
-        order.insert(order.end(), ids.begin(), ids.end());
-        cnt[c] = (int)ids.size();
+        for (int cs = 8; cs >= 1; cs /= 2) {
+            std::vector<int32_t> ids;
+            for (int i = 0; i < count; ++i)
+                if (problems[i].d >= lo && problems[i].d <= hi && cluster_size(problems[i].n) == cs) ids.push_back(i);
+            if (ids.empty()) continue;
+            std::stable_sort(ids.begin(), ids.end(), [&](int32_t x, int32_t y) { return work[x] > work[y]; });
+            classes.push_back({c == 0 ? 32 : (c == 1 ? 64 : 128), cs, (int)order.size(), (int)ids.size()});
+            order.insert(order.end(), ids.begin(), ids.end());
+        }
     }
     // one device block holds the table, the order, the results and the work space
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
@@ -705,8 +829,10 @@ kmpar_status kmpar_batch_run(const float *X, const kmpar_problem *problems, int3
         return batch_fail(e == cudaErrorMemoryAllocation ? KMPAR_ERR_OOM : KMPAR_ERR_CUDA,
                           std::string("batch work space: ") + cudaGetErrorString(e));
     std::vector<BRes> hres((size_t)count);
-    cudaStream_t side[2] = {nullptr, nullptr};
-    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+    const int nside = (int)classes.size() - 1;
+    std::vector<cudaStream_t> side((size_t)std::max(0, nside), nullptr);
+    std::vector<cudaEvent_t> ev_join((size_t)std::max(0, nside), nullptr);
+    cudaEvent_t ev_fork = nullptr;
     BArgs a{};
     a.X = X;
     a.probs = reinterpret_cast<const BProb *>(ws + o_probs);
@@ -726,21 +852,25 @@ kmpar_status kmpar_batch_run(const float *X, const kmpar_problem *problems, int3
     e = cudaMemcpyAsync(ws + o_probs, hp.data(), sizeof(BProb) * (size_t)count, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ws + o_order, order.data(), sizeof(int32_t) * (size_t)count, cudaMemcpyHostToDevice, s);
-    // the three classes run concurrently: the caller's stream and two side streams
-    // forked from it and joined back (also valid inside a stream capture)
+    // the classes run concurrently: the caller's stream and side streams forked from
+    // it and joined back (also valid inside a stream capture)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-        e = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_join[i], cudaEventDisableTiming);
+    for (int i = 0; i < nside && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&side[(size_t)i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_join[(size_t)i], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaEventRecord(ev_fork, s);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(side[i], ev_fork, 0);
-    if (e == cudaSuccess) e = launch_class<128>(a, first[2], cnt[2], s);
-    if (e == cudaSuccess) e = launch_class<64>(a, first[1], cnt[1], side[0]);
-    if (e == cudaSuccess) e = launch_class<32>(a, first[0], cnt[0], side[1]);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-        e = cudaEventRecord(ev_join[i], side[i]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_join[i], 0);
+    for (int i = 0; i < nside && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(side[(size_t)i], ev_fork, 0);
+    for (size_t c = 0; c < classes.size() && e == cudaSuccess; ++c) {
+        const Cls &q = classes[c];
+        cudaStream_t cs = c == 0 ? s : side[c - 1];
+        if (q.dp == 32) e = launch_class<32>(a, q.cs, q.first, q.count, cs);
+        else if (q.dp == 64) e = launch_class<64>(a, q.cs, q.first, q.count, cs);
+        else e = launch_class<128>(a, q.cs, q.first, q.count, cs);
+    }
+    for (int i = 0; i < nside && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(ev_join[(size_t)i], side[(size_t)i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_join[(size_t)i], 0);
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(hres.data(), ws + o_res, sizeof(BRes) * (size_t)count, cudaMemcpyDeviceToHost, s);
@@ -748,9 +878,9 @@ kmpar_status kmpar_batch_run(const float *X, const kmpar_problem *problems, int3
     if (e == cudaSuccess) e = ef;
     const cudaError_t es = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = es;
-    for (int i = 0; i < 2; ++i) {
-        if (side[i]) cudaStreamDestroy(side[i]);
-        if (ev_join[i]) cudaEventDestroy(ev_join[i]);
+    for (int i = 0; i < nside; ++i) {
+        if (side[(size_t)i]) cudaStreamDestroy(side[(size_t)i]);
+        if (ev_join[(size_t)i]) cudaEventDestroy(ev_join[(size_t)i]);
     }
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (e != cudaSuccess) return batch_fail(KMPAR_ERR_CUDA, std::string("batch kernels: ") + cudaGetErrorString(e));

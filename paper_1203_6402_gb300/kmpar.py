@@ -26,6 +26,7 @@ EXPORTED = ["kmpar_init", "kmpar_round", "kmpar_weight", "kmpar_recluster", "kmp
             "kmpar_fit", "kmpar_state", "kmpar_get_stats", "kmpar_uniforms", "kmpar_set_timing",
             "kmpar_launch_count", "kmpar_cost_noalloc", "kmpar_destroy", "kmpar_release_cached_memory",
             "kmpar_set_sampling", "kmpar_batch_run", "kmpar_batch_cand_capacity", "kmpar_weighted_lloyd",
+            "kmpar_batch_set_split",
             "kmpar_status_string", "kmpar_last_error"]
 
 
@@ -107,6 +108,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kmpar_launch_count": (i64, []),
         "kmpar_cost_noalloc": (i32, [P, i64, i32, P, i32, ctypes.POINTER(f64), P]),
         "kmpar_batch_cand_capacity": (i64, [f64, i32]),
+        "kmpar_batch_set_split": (i32, [i32]),
         "kmpar_weighted_lloyd": (i32, [P, P, i32, ctypes.POINTER(i32)]),
         "kmpar_batch_run": (i32, [P, ctypes.POINTER(kmpar_problem), i32, P, P, P, P,
                                   ctypes.POINTER(kmpar_problem_result), P]),
@@ -194,6 +196,10 @@ def kmpar_fit(X_ptr: int, n: int, d: int, k: int, ell: float, rounds: int, seed:
 
 def kmpar_batch_cand_capacity(ell: float, rounds: int) -> int:
     return load().kmpar_batch_cand_capacity(ell, rounds)
+
+
+def kmpar_batch_set_split(rows_per_block: int) -> None:
+    _check(load().kmpar_batch_set_split(rows_per_block))
 
 
 def kmpar_batch_run(X_ptr: int, problems: list, centers_ptr: int, labels_ptr: int | None = None,

@@ -151,3 +151,68 @@ def test_problem_struct_layout():
     assert ctypes.sizeof(kmpar.kmpar_problem) == 72
     assert kmpar.kmpar_problem.seed.offset == 40
     assert ctypes.sizeof(kmpar.kmpar_problem_result) == 56
+
+
+@pytest.mark.gpu
+def test_batch_clusters_equal_single_problem_path(km):
+    """Problems of more than 25,000 rows run split over a thread-block cluster of 2,
+    4 or 8 blocks (rows cut into contiguous ranges, draws appended rank by rank):
+    draws, candidates and weights equal those of the
+    single-problem FP32 path; Lloyd's labels and final cost agree closely."""
+    probs = [dict(n=n, d=d, k=k, ell=2.0 * k, rounds=5, max_iter=10, seed=77 + i, data_seed=500 + i)
+             for i, (n, d, k) in enumerate([(30_000, 32, 40), (70_000, 64, 90), (150_000, 128, 200),
+                                            (200_000, 32, 16), (24_000, 128, 60)])]
+    xo = co = lo = 0
+    for p in probs:
+        p.update(x_offset=xo, c_offset=co, l_offset=lo)
+        xo += p["n"] * p["d"]
+        co += p["k"] * p["d"]
+        lo += p["n"]
+    ncand = _layout(km, probs)
+    X = datagen.batched_points(probs)
+    Xd = torch.from_numpy(X).cuda()
+    C = torch.zeros(co, dtype=torch.float32, device="cuda")
+    L = torch.zeros(lo, dtype=torch.int32, device="cuda")
+    cand = torch.full((ncand,), -1, dtype=torch.int32, device="cuda")
+    w = torch.zeros(ncand, dtype=torch.int64, device="cuda")
+    st, res = km.kmpar_batch_run(Xd.data_ptr(), probs, C.data_ptr(), L.data_ptr(), cand.data_ptr(), w.data_ptr())
+    assert st in (km.KMPAR_OK, km.KMPAR_WARN_FEW_CANDIDATES)
+    for p, r in zip(probs, res):
+        n, d, k = p["n"], p["d"], p["k"]
+        Xi = Xd[p["x_offset"]: p["x_offset"] + n * d].view(n, d)
+        g = km.KMeansPar(Xi, k, p["ell"], p["rounds"], p["seed"], precision="fp32")
+        for i in range(1, p["rounds"] + 1):
+            g.round(i)
+        gc, gw = g.candidates()
+        Cs, _ = g.recluster()
+        out = g.lloyd(Cs, p["max_iter"], labels=True)
+        g.close()
+        m = r["m"]
+        assert m == len(gc), p
+        assert np.array_equal(cand[p["cand_offset"]: p["cand_offset"] + m].cpu().numpy(), gc.cpu().numpy()), p
+        assert np.array_equal(w[p["cand_offset"]: p["cand_offset"] + m].cpu().numpy(), gw.cpu().numpy()), p
+        # Lloyd: the two paths round the centroids of equal sums differently in the last
+        # bit (one compensated chain against 256-member pieces), so a near tie may part
+        # them; the labels and costs must still agree closely
+        assert abs(r["iters"] - out["iters"]) <= 1, (p, r)
+        same = (L[p["l_offset"]: p["l_offset"] + n].cpu().numpy() == out["labels"].cpu().numpy()).mean()
+        assert same >= 0.9999, (p, same)
+        assert math.isclose(r["final_cost"], out["final_cost"], rel_tol=1e-6), (r, out["final_cost"])
+
+
+def test_batch_tuning_table_and_split_setting():
+    """The committed autotuner table names one of the measured thresholds, the one
+    with the smallest time; the setter rejects a negative threshold."""
+    from paper_1203_6402_gb300 import batch_tune
+    t = batch_tune.load_table()
+    assert t is not None and str(t["rows_per_block"]) in t["ms"]
+    assert t["ms"][str(t["rows_per_block"])] == min(t["ms"].values())
+    assert all(int(r) in batch_tune.CANDIDATES for r in t["ms"])
+    from paper_1203_6402_gb300 import kmpar
+    try:
+        kmpar.load()
+    except (FileNotFoundError, OSError):
+        pytest.skip("library not built")
+    with pytest.raises(kmpar.KmparError):
+        kmpar.kmpar_batch_set_split(-1)
+    kmpar.kmpar_batch_set_split(25000)

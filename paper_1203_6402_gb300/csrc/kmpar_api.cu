@@ -259,7 +259,8 @@ kmpar_status kmpar_init(kmpar_ctx **out, const float *X, int64_t n, int32_t d, i
     KMP_INIT_CUDA(alloc(c, &c.cand, c.cap_total), "alloc candidates");
     KMP_INIT_CUDA(alloc(c, &c.C, (size_t)c.cap_total * d), "alloc candidate rows");
     KMP_INIT_CUDA(alloc(c, &c.w, c.cap_total), "alloc weights");
-    KMP_INIT_CUDA(alloc(c, &c.rD2, c.cap_total), "alloc recluster D2");
+    // two buffers (alternating draws) of the padded candidate count
+    KMP_INIT_CUDA(alloc(c, &c.rD2, 2 * (size_t)((c.cap_total + 31) / 32 * 32)), "alloc recluster D2");
     KMP_INIT_CUDA(alloc(c, &c.chosen, k), "alloc chosen");
     KMP_INIT_CUDA(alloc(c, &c.rc_cmass, 2 * (size_t)((c.cap_total + 31) / 32) + 2048), "alloc recluster masses");
     unsigned char *rc_sync = nullptr;

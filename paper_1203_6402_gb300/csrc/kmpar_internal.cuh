@@ -63,8 +63,8 @@ struct Ctx {
     int32_t *cand = nullptr;      // cap_total row numbers
     float *C = nullptr;           // cap_total x d candidate rows
     long long *w = nullptr;       // cap_total
-    float *rD2 = nullptr;         // recluster D^2 (cap_total)
-    double *rc_cmass = nullptr;   // recluster chunk masses, 2 x ceil(cap_total / 32), then 2 x 1024 CTA totals
+    float *rD2 = nullptr;         // recluster D^2, 2 x cap_total rounded up to 32
+    double *rc_cmass = nullptr;   // recluster chunk masses, 2 x ceil(cap_total / 32), then 2048 doubles of CTA slots
     float *rCT = nullptr;         // recluster grid form: candidates transposed (d x cap_total padded to 32)
     int32_t *wl_lab[2] = {nullptr, nullptr};   // weighted Lloyd: candidate labels (cap_total each)
     void *rc_sync = nullptr;      // recluster grid barrier / pick flag

@@ -127,6 +127,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// asynchronous global -> shared copies of 16 and 4 bytes (one commit group per call site)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // K-major operand, 128-byte swizzle: 8-row x 128 B atoms (1024 B), SBO = 1024 B.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -171,13 +181,15 @@ struct Cfg {
     static constexpr int B_BYTES = KA * BN * 128;
     static constexpr int GW = BN / kGroups;   // columns per epilogue warp
     static constexpr int CHUNKS = GW / 32;
+    static constexpr int NB = GW + 4;         // floats of one warp's norm buffer (+ the tile scale)
     static_assert(GW / 2 <= (1 << kColBits) && GW % 32 == 0, "pair field");
 };
 
 template <int KA, int BN, int S, int A16B, int EPI>
 constexpr size_t smem_bytes() {
     return 1024 + (size_t)S * Cfg<KA, BN>::B_BYTES + (size_t)A16B * Cfg<KA, BN>::A16_BYTES + sizeof(Smem) +
-           (EPI == EPI_LIST ? sizeof(int32_t) * kListSlots * kEpiThreads : 0);
+           (EPI == EPI_LIST ? sizeof(int32_t) * kListSlots * kEpiThreads : 0) +
+           sizeof(float) * kEpiWarps * 2 * Cfg<KA, BN>::NB;
 }
 
 // bounded wait on an mbarrier phase; false if this or another warp gave up.  The
@@ -224,6 +236,9 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
     uint8_t *a16 = bst + S * C::B_BYTES;                   // A16B A tiles
     Smem &sm = *reinterpret_cast<Smem *>(a16 + A16B * C::A16_BYTES);
     int32_t *lsm = reinterpret_cast<int32_t *>(&sm + 1);   // EPI_LIST: kListSlots x kEpiThreads
+    // per epilogue warp, two buffers of its column group's norms (and the FP8 tile
+    // scale), filled one tile ahead by cp.async
+    float *nbuf = reinterpret_cast<float *>(lsm + (EPI == EPI_LIST ? kListSlots * kEpiThreads : 0));
     volatile int *abort = &sm.abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -352,6 +367,18 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
         // kValMask as a runtime value: held in a register, the column is then the
         // one immediate of a single logic op per key
         const uint32_t vmask = p.vmask;
+        // norms of center tile tn into buffer slot: one 16-byte copy per lane (a
+        // tile's copies were issued one tile earlier, so their latency is hidden)
+        float *nbw = nbuf + (size_t)e * 2 * C::NB;
+        auto prefetch_norms = [&](int tn, int slot) {
+            if (NE) {
+                float *dst = nbw + slot * C::NB;
+                if (lane < C::GW / 4) cp_async16(dst + lane * 4, p.ncol + (size_t)tn * BN + grp * C::GW + lane * 4);
+                if (FMT == FMT_FP8 && lane == C::GW / 4) cp_async4(dst + C::GW, p.tscale + tn);
+                cp_async_commit();
+            }
+        };
+        if (nrt > blockIdx.x) prefetch_norms(0, 0);
         int lt = 0, g = 0;
         for (int rt = blockIdx.x; rt < nrt; rt += gridDim.x, ++lt) {
             const int mb = lt & 1;
@@ -368,9 +395,18 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
             bool ok = true;
             for (int t = 0; t < T; ++t, ++g) {
                 const int buf = g & 1;
+                const float *nct = nullptr;
+                if (NE) {
+                    // every lane is done with the other slot (tile g - 1): refill it with
+                    // the next tile's norms, then wait for this tile's
+                    __syncwarp();
+                    prefetch_norms(t + 1 < T ? t + 1 : 0, (g + 1) & 1);
+                    cp_async_wait<1>();
+                    __syncwarp();
+                    nct = nbw + (g & 1) * C::NB;
+                }
                 float f = fx;
-                if (FMT == FMT_FP8) f = fx * __ldg(p.tscale + t);
-                const float *nct = NE ? p.ncol + (size_t)t * BN + grp * C::GW : nullptr;
+                if (FMT == FMT_FP8) f = fx * nct[C::GW];
                 if (!wait_bar(&sm.acc_full[buf], (g >> 1) & 1, abort, p.err, 18)) { ok = false; break; }
                 tc_fence_after();
                 // two independent top-2 chains (alternate column pairs), merged per tile
@@ -400,9 +436,8 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
                                 // group in the low mantissa bits (a compile-time constant)
                                 float nv[8];
                                 if (NE) {
-                                    const float4 n0 = __ldg(reinterpret_cast<const float4 *>(nct + (c + cc) * 32 + q));
-                                    const float4 n1 =
-                                        __ldg(reinterpret_cast<const float4 *>(nct + (c + cc) * 32 + q + 4));
+                                    const float4 n0 = *reinterpret_cast<const float4 *>(nct + (c + cc) * 32 + q);
+                                    const float4 n1 = *reinterpret_cast<const float4 *>(nct + (c + cc) * 32 + q + 4);
                                     nv[0] = n0.x; nv[1] = n0.y; nv[2] = n0.z; nv[3] = n0.w;
                                     nv[4] = n1.x; nv[5] = n1.y; nv[6] = n1.z; nv[7] = n1.w;
                                 } else {
@@ -452,7 +487,7 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
 #pragma unroll
                             for (int q = 0; q < 32; q += 4) {
                                 float4 n4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                                if (NE) n4 = __ldg(reinterpret_cast<const float4 *>(nct + (c + cc) * 32 + q));
+                                if (NE) n4 = *reinterpret_cast<const float4 *>(nct + (c + cc) * 32 + q);
                                 v[q] = screened<NE>(r[cc][q], f, n4.x);
                                 v[q + 1] = screened<NE>(r[cc][q + 1], f, n4.y);
                                 v[q + 2] = screened<NE>(r[cc][q + 2], f, n4.z);
@@ -543,6 +578,7 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
         }
     }
 
+    cp_async_wait<0>();   // norm copies still in flight (a no-op for the other roles)
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {

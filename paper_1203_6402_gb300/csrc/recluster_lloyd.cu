@@ -32,58 +32,48 @@ cudaError_t launch_weights(Ctx &c) {
 
 // ------------------------------------------------------------------ step 8
 // Weighted k-means++ (Alg. 1 with multiplicities w): k sequential draws over the m
-// candidates.  One cooperative launch, one CTA of 1024 threads per SM; the
-// candidates are cut into fixed chunks of 32 (one warp each, FP64 shuffle scans)
-// and CTA b owns the contiguous chunk range [b cpc, (b+1) cpc).  Per draw t:
+// candidates.  One cooperative launch, one CTA of 768 threads per SM; the
+// candidates are cut into fixed chunks of 32 (FP64 shuffle scans) and CTA b owns
+// the contiguous chunk range [b cpc, (b+1) cpc); its warps 1.. take its chunks in
+// phases A and C, warp 0 takes phase B.  Per draw t:
 //   A  each warp: masses e_j = w_j (t = 0) or w_j D^2_j, inclusive warp scan;
-//      chunk totals -> gchunk, the CTA's total (its chunks in a fixed order) ->
-//      gctot                                               ... grid barrier
-//   B  every CTA (warp 0) finds the same pick from the published totals: a
-//      fixed-order prefix over the CTA totals gives the owning CTA of the target
-//      u_t * total, a prefix over that CTA's chunk totals the chunk, a scan of the
-//      chunk's masses the first candidate whose prefix exceeds the target
+//      chunk totals -> gchunk; the CTA's total (its chunks in a fixed order) is
+//      published, after a fence, as one word tagged with the draw
+//   B  CTA 0 (warp 0) waits until all G words carry the draw's tag (this wait is
+//      the draw's grid barrier), then finds the pick from the totals: a fixed-order
+//      prefix over the CTA totals gives the owning CTA of the target u_t * total, a
+//      prefix over that CTA's chunk totals the chunk, a scan of the chunk's masses
+//      the first candidate whose prefix exceeds the target; it publishes the pick
+//      as one tagged word, which one lane of every other CTA polls
 //   C  every warp: D^2_j <- min(D^2_j, ||c_j - c_pick||^2) in the exact FP32 form,
 //      reading the candidates from a transposed copy (coordinate-major), so a
 //      warp's 32 candidates are one coalesced 128-byte load per coordinate.
-// One grid barrier per draw; every wait is bounded (by `wait` clock cycles, about
-// 2 s by default): a timeout raises the error word and every CTA returns.
-constexpr int kRcThreads = 1024;
+// The D^2 values in global memory (read in B for the picked chunk) and the chunk
+// totals alternate between two buffers by the parity of the draw: a CTA can only
+// write draw t + 2's values after every CTA has published draw t + 1, that is after
+// every CTA has finished reading draw t's.  One wait per draw, bounded by `wait`
+// clock cycles (about 2 s by default): a timeout raises the error word and every CTA
+// returns.
+constexpr int kRcThreads = 768;
+constexpr int kRcPre = 16;        // coordinates per lane loaded ahead of the pick
+constexpr int kRcLaneWords = 8;   // CTA totals per lane of warp 0: G <= 256
 constexpr unsigned long long kRcWait = 4000000000ull;
 
 struct RcSync {
-    unsigned int count, gen;   // grid barrier
-    int abort;
+    int abort;   // set by the CTA whose wait ran out; the others return
 };
 
-__device__ __forceinline__ bool rc_grid_sync(RcSync *s, unsigned int nblocks, int *err, unsigned long long wait) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        volatile unsigned int *gen = &s->gen;
-        const unsigned int g = *gen;
-        __threadfence();
-        if (atomicAdd(&s->count, 1u) == nblocks - 1) {
-            s->count = 0;
-            __threadfence();
-            atomicExch(&s->gen, g + 1);
-        } else {
-            const unsigned long long t0 = clock64();
-            while (*gen == g) {
-                if (*(volatile int *)&s->abort) { ok = 0; break; }
-                if (clock64() - t0 > wait) {
-                    atomicCAS(err, 0, 1);
-                    atomicExch(&s->abort, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return ok != 0;
+// A CTA's total of one draw is published as one 64-bit word: the FP64 bits with
+// the low 8 mantissa bits replaced by a tag of the draw (0x80 | (t >> 1) & 0x7f,
+// never 0, and different for draws t and t - 2, which share a buffer).  A reader
+// polls the word until the tag is its draw's; the value is then the word with the
+// tag bits cleared (the total truncated by at most 2^-44 of itself, the same value
+// in every CTA).
+__device__ __forceinline__ unsigned long long rc_tag(int step) {
+    return 0x80ull | ((unsigned long long)(step >> 1) & 0x7full);
+}
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
+    return *reinterpret_cast<const volatile unsigned long long *>(p);
 }
 
 __device__ __forceinline__ double warp_incl_scan_f64(double v, int lane) {
@@ -142,20 +132,20 @@ __device__ __forceinline__ int prefix_find(const double *v, int lo, int hi, doub
     return __shfl_sync(0xffffffffu, hit, src);
 }
 
-// prefix_find with the values cached in registers (at most 16 per lane): one pass
+// prefix_find with the values cached in registers (at most 8 per lane): one pass
 // over global memory for the sum, the scan and the search
 __device__ __forceinline__ int prefix_find_reg(const double *v, int lo, int hi, double start, double target, int lane,
                                                double *before, double *total_out) {
     const int cnt = hi - lo;
     const int q = (cnt + 31) / 32;
-    if (q > 16) return prefix_find(v, lo, hi, start, target, lane, before, total_out);
+    if (q > 8) return prefix_find(v, lo, hi, start, target, lane, before, total_out);
     const int a = lo + min(cnt, lane * q), b = lo + min(cnt, lane * q + q);
-    double vals[16];
+    double vals[8];
 #pragma unroll
-    for (int t = 0; t < 16; ++t) vals[t] = (t < q && a + t < b) ? __ldcg(v + a + t) : 0.0;
+    for (int t = 0; t < 8; ++t) vals[t] = (t < q && a + t < b) ? __ldcg(v + a + t) : 0.0;
     double ls = 0.0;
 #pragma unroll
-    for (int t = 0; t < 16; ++t)
+    for (int t = 0; t < 8; ++t)
         if (t < q && a + t < b) ls += vals[t];
     const double incl = warp_incl_scan_f64(ls, lane);
     double excl = __shfl_up_sync(0xffffffffu, incl, 1);
@@ -164,7 +154,7 @@ __device__ __forceinline__ int prefix_find_reg(const double *v, int lo, int hi, 
     int hit = -1;
     double bf = 0.0, run = start + excl;
 #pragma unroll
-    for (int t = 0; t < 16; ++t) {
+    for (int t = 0; t < 8; ++t) {
         if (hit < 0 && t < q && a + t < b) {
             const double pre = run;
             run = run + vals[t];
@@ -190,16 +180,18 @@ __device__ __forceinline__ int last_positive(const double *v, int lo, int hi, in
 
 __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
     const float *__restrict__ C, const float *__restrict__ CT, int mp, const long long *__restrict__ w, DevState *st,
-    int d, int k, uint64_t seed, float *rD2, int32_t *chosen, float *centers, double *gchunk, int nchunk_cap,
-    double *gctot, int cpc_cap, RcSync *sync, int *err, unsigned long long wait) {
+    int d, int k, uint64_t seed, float *rD2buf, int32_t *chosen, float *centers, double *gchunk, int nchunk_cap,
+    unsigned long long *slots, int cpc_cap, int qs, RcSync *sync, int *err, unsigned long long wait) {
     // shared: cpc_cap chunk totals, the CTA's candidates' weights (FP64) and D^2,
-    // then d floats of the pick's row
+    // d floats of the pick's row, then the first qs coordinates of the CTA's
+    // candidates (coordinate-major, staged once: they do not change across draws)
     extern __shared__ double rsm[];
     double *ctl = rsm;
     double *wl = rsm + cpc_cap;
     float *dl = reinterpret_cast<float *>(wl + (size_t)cpc_cap * 32);
     float *cnew = dl + (size_t)cpc_cap * 32;
-    __shared__ int s_pick, s_near, s_done;
+    float *cts = cnew + ((d + 31) & ~31);
+    __shared__ int s_pick, s_near, s_done, s_abort;
     const int m = st->m;
     const int nchunk = (m + 31) / 32;
     const int G = gridDim.x;
@@ -207,17 +199,30 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
     const int b = blockIdx.x;
     const int c0 = min(nchunk, b * cpc), c1 = min(nchunk, c0 + cpc);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = kRcThreads / 32;
+    const int nl = (c1 - c0) * 32;   // the CTA's candidate slots
+    const int qg = (G + 31) / 32;   // CTA totals read per lane of warp 0 (G <= 32 kRcLaneWords)
+    const int ga = min(G, lane * qg), gb = min(G, lane * qg + qg);
     for (int ch = c0 + wid; ch < c1; ch += nwarps) {
         const int j = ch * 32 + lane;
         wl[(ch - c0) * 32 + lane] = j < m ? (double)w[j] : 0.0;
+    }
+    for (int f = threadIdx.x; f < qs * nl; f += kRcThreads) {
+        const int q = f / nl, jl = f - q * nl;
+        const int j = c0 * 32 + jl;
+        cts[(size_t)q * nl + jl] = j < m ? CT[(int64_t)q * mp + j] : 0.f;
     }
     __syncthreads();
 
     for (int step = 0; step < k; ++step) {
         double *gch = gchunk + (size_t)(step & 1) * nchunk_cap;
-        double *gct = gctot + (size_t)(step & 1) * G;
-        // ---- A: chunk masses and the CTA total
-        for (int ch = c0 + wid; ch < c1; ch += nwarps) {
+        unsigned long long *gs = slots + (size_t)(step & 1) * G;
+        const unsigned long long tag = rc_tag(step);
+        const float *rD2prev = rD2buf + (size_t)((step + 1) & 1) * mp;   // D^2 after draw step - 1
+        float *rD2 = rD2buf + (size_t)(step & 1) * mp;
+        // ---- A (warps 1..): chunk masses and the CTA total.  A chunk is scanned by
+        // the warp that updates its D^2 in phase C, so its D^2 values in shared
+        // memory pass between phases within one warp
+        for (int ch = c0 + wid - 1; wid > 0 && ch < c1; ch += nwarps - 1) {
             const int j = ch * 32 + lane;
             const int jl = (ch - c0) * 32 + lane;
             double e = 0.0;
@@ -228,32 +233,62 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
                 gch[ch] = incl;
             }
         }
+        __threadfence();   // every thread's chunk totals (and last draw's D^2) before the flag
         __syncthreads();
         if (wid == 0) {
             double s = 0.0;
             for (int i = lane; i < c1 - c0; i += 32) s += ctl[i];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-            if (lane == 0) gct[b] = s;
+            if (lane == 0) {
+                *reinterpret_cast<volatile unsigned long long *>(gs + b) =
+                    (__double_as_longlong(s) & ~0xffull) | tag;
+            }
         }
-        __threadfence();
-        if (!rc_grid_sync(sync, G, err, wait)) return;
-        // ---- B: the pick, found identically by every CTA
-        if (wid == 0) {
+        // ---- B, CTA 0 (warp 0): wait until every CTA's word carries this draw's tag
+        // (the words of all G CTAs are polled together, so the wait ends one load
+        // after the last CTA publishes), find the pick and publish it as one tagged
+        // word; the other CTAs (one lane) poll that word.  One CTA reads the published
+        // totals and the owning chunk: no contention of G CTAs on the same lines.
+        unsigned long long *pw = slots + 2 * (size_t)G + (step & 1);
+        if (wid == 0 && b == 0) {
+            unsigned long long gw[kRcLaneWords];
+            int ok = 1;
+            const unsigned long long t0 = clock64();
+            for (;;) {
+                bool mine = true;
+#pragma unroll
+                for (int t = 0; t < kRcLaneWords; ++t) {
+                    if (t < qg && ga + t < gb) {
+                        gw[t] = ld_volatile_u64(gs + ga + t);
+                        mine = mine && (gw[t] & 0xffull) == tag;
+                    }
+                }
+                if (__all_sync(0xffffffffu, mine)) break;
+                int stop = 0;
+                if (lane == 0) {
+                    if (*(volatile int *)&sync->abort) stop = 1;
+                    else if (clock64() - t0 > wait) {
+                        atomicCAS(err, 0, 1);
+                        atomicExch(&sync->abort, 1);
+                        stop = 1;
+                    }
+                }
+                if (__shfl_sync(0xffffffffu, stop, 0)) { ok = 0; break; }
+            }
+            __threadfence();   // the chunk totals and D^2 the words were published after
             double total = 0.0, before = 0.0;
+            int pick = -1, near = 0;
+            double gv[kRcLaneWords];
+#pragma unroll
+            for (int t = 0; t < kRcLaneWords; ++t)
+                gv[t] = (ok && t < qg && ga + t < gb) ? __longlong_as_double((long long)(gw[t] & ~0xffull)) : 0.0;
             const double u = uniform53((uint64_t)step, 0, TAG_RECLUSTER, seed);
-            // total first (the target depends on it), then the owning CTA
             // the total first (the target depends on it): a sum with the same association
             // as the search below
-            int pick = -1, near = 0;
-            const int qg = (G + 31) / 32;
-            const int ga = min(G, lane * qg), gb = min(G, lane * qg + qg);
-            double gv[16];
-#pragma unroll
-            for (int t = 0; t < 16; ++t) gv[t] = (t < qg && ga + t < gb) ? __ldcg(gct + ga + t) : 0.0;
             double ls = 0.0;
 #pragma unroll
-            for (int t = 0; t < 16; ++t)
+            for (int t = 0; t < kRcLaneWords; ++t)
                 if (t < qg && ga + t < gb) ls += gv[t];
             const double gincl = warp_incl_scan_f64(ls, lane);
             total = __shfl_sync(0xffffffffu, gincl, 31);
@@ -264,7 +299,7 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
                 int hit = -1;
                 double bf = 0.0, run = gex;
 #pragma unroll
-                for (int t = 0; t < 16; ++t) {
+                for (int t = 0; t < kRcLaneWords; ++t) {
                     if (hit < 0 && t < qg && ga + t < gb) {
                         const double pre = run;
                         run = run + gv[t];
@@ -279,14 +314,24 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
                     ob = __shfl_sync(0xffffffffu, hit, src);
                 }
                 double pre_b = before;
-                if (ob < 0) { ob = last_positive(gct, 0, G, lane); pre_b = 0.0; near = 1; }
+                if (ob < 0) {   // rounding left the target at the end: the last CTA with mass
+                    int lb = -1;
+#pragma unroll
+                    for (int t = 0; t < kRcLaneWords; ++t)
+                        if (t < qg && ga + t < gb && gv[t] > 0.0) lb = ga + t;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) lb = max(lb, __shfl_xor_sync(0xffffffffu, lb, o));
+                    ob = lb;
+                    pre_b = 0.0;
+                    near = 1;
+                }
                 const int oc0 = min(nchunk, ob * cpc), oc1 = min(nchunk, oc0 + cpc);
                 int ch = near ? -1 : prefix_find_reg(gch, oc0, oc1, pre_b, target, lane, &before, nullptr);
                 double pre_c = before;
                 if (ch < 0) { ch = last_positive(gch, oc0, oc1, lane); near = 1; }
                 const int j = ch * 32 + lane;
                 double e = 0.0;
-                if (j < m) e = step == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)__ldcg(rD2 + j));
+                if (j < m) e = step == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)__ldcg(rD2prev + j));
                 const double incl = warp_incl_scan_f64(e, lane);
                 const unsigned pos = __ballot_sync(0xffffffffu, j < m && e > 0.0);
                 if (!near) {
@@ -307,9 +352,43 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
                 s_pick = pick;
                 s_near = near;
                 s_done = !(total > 0.0);
+                s_abort = !ok;
+                if (ok)
+                    *reinterpret_cast<volatile unsigned long long *>(pw) =
+                        ((unsigned long long)(uint32_t)max(pick, 0) << 32) | ((unsigned long long)near << 8) |
+                        ((unsigned long long)(total > 0.0 ? 0 : 1) << 9) | tag;
             }
+        } else if (wid == 0 && lane == 0) {
+            int ok = 1;
+            unsigned long long v;
+            const unsigned long long t0 = clock64();
+            for (;;) {
+                v = ld_volatile_u64(pw);
+                if ((v & 0xffull) == tag) break;
+                if (*(volatile int *)&sync->abort) { ok = 0; break; }
+                if (clock64() - t0 > wait) {
+                    atomicCAS(err, 0, 1);
+                    atomicExch(&sync->abort, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+            s_pick = (int)(v >> 32);
+            s_near = (int)((v >> 8) & 1);
+            s_done = (int)((v >> 9) & 1);
+            s_abort = !ok;
+        }
+        // warps 1.. (phase C's workers) load the first kRcPre global coordinates of
+        // their first chunk while the pick is found: they do not depend on it
+        float pre[kRcPre];
+        const int chp = c0 + wid - 1;
+        const bool use_pre = wid > 0 && chp < c1 && qs + kRcPre <= d && chp * 32 + lane < m;
+        if (use_pre) {
+#pragma unroll
+            for (int u2 = 0; u2 < kRcPre; ++u2) pre[u2] = __ldg(CT + (int64_t)(qs + u2) * mp + chp * 32 + lane);
         }
         __syncthreads();
+        if (s_abort) return;
         if (s_done) {
             // positive mass exhausted: the remaining draws repeat the first center
             if (b == 0) {
@@ -334,35 +413,52 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
             if (b == 0) centers[(int64_t)step * d + qq] = v;
         }
         __syncthreads();
-        // ---- C: D^2 update of own candidates (t = x_q - c_q, fma, q ascending); 16
-        // coordinates are loaded before their FMA chain runs
-        for (int ch = c0 + wid; ch < c1; ch += nwarps) {
+        // ---- C (warps 1..): D^2 update of own candidates (t = x_q - c_q, fma, q
+        // ascending): the first qs coordinates from shared memory, the rest from the
+        // transposed copy, 32 loads issued before their FMA chain runs
+        auto update = [&](int ch, bool with_pre) {
             const int j = ch * 32 + lane;
             const int jl = (ch - c0) * 32 + lane;
-            if (j < m) {
-                float v = 0.f;
-                const float *col = CT + j;
-                int q = 0;
-                for (; q + 16 <= d; q += 16) {
-                    float buf[16];
+            if (j >= m) return;
+            float v = 0.f;
+            const float *col = CT + j;
+            int q = 0;
+            for (; q < qs; ++q) {
+                const float t = __fsub_rn(cts[(size_t)q * nl + jl], cnew[q]);
+                v = __fmaf_rn(t, t, v);
+            }
+            if (with_pre) {
 #pragma unroll
-                    for (int u2 = 0; u2 < 16; ++u2) buf[u2] = __ldg(col + (int64_t)(q + u2) * mp);
+                for (int u2 = 0; u2 < kRcPre; ++u2) {
+                    const float t = __fsub_rn(pre[u2], cnew[q + u2]);
+                    v = __fmaf_rn(t, t, v);
+                }
+                q += kRcPre;
+            }
+            // batches of up to 32 loads issued together, then their FMA chain in order
+            for (; q < d; q += 32) {
+                const int nb = min(32, d - q);
+                float buf[32];
 #pragma unroll
-                    for (int u2 = 0; u2 < 16; ++u2) {
+                for (int u2 = 0; u2 < 32; ++u2) buf[u2] = u2 < nb ? __ldg(col + (int64_t)(q + u2) * mp) : 0.f;
+#pragma unroll
+                for (int u2 = 0; u2 < 32; ++u2) {
+                    if (u2 < nb) {
                         const float t = __fsub_rn(buf[u2], cnew[q + u2]);
                         v = __fmaf_rn(t, t, v);
                     }
                 }
-                for (; q < d; ++q) {
-                    const float t = __fsub_rn(__ldg(col + (int64_t)q * mp), cnew[q]);
-                    v = __fmaf_rn(t, t, v);
-                }
-                const float nv = step == 0 ? v : fminf(dl[jl], v);
-                dl[jl] = nv;
-                rD2[j] = nv;
             }
+            const float nv = step == 0 ? v : fminf(dl[jl], v);
+            dl[jl] = nv;
+            rD2[j] = nv;
+        };
+        if (wid > 0 && chp < c1) {
+            if (use_pre) update(chp, true);
+            else update(chp, false);
+            for (int ch = chp + nwarps - 1; ch < c1; ch += nwarps - 1) update(ch, false);
         }
-        // the next draw's barrier orders these writes before any CTA reads them
+        // the next draw's flags order these writes before any CTA reads them
     }
 }
 
@@ -663,10 +759,19 @@ cudaError_t launch_recluster(Ctx &c, float *centers) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // one co-resident CTA per SM
     const int nchunk_cap = (c.cap_total + 31) / 32;
-    int G = std::max(1, std::min(c.num_sms, nchunk_cap));
+    int G = std::max(1, std::min(std::min(c.num_sms, 32 * kRcLaneWords), nchunk_cap));
     const int cpc_cap = (nchunk_cap + G - 1) / G;
-    const size_t smem = sizeof(double) * (size_t)cpc_cap * 33 + sizeof(float) * ((size_t)cpc_cap * 32 + c.d);
-    if (smem > 200 * 1024) return cudaErrorInvalidValue;   // beyond ~500,000 candidates per SM
+    const size_t base_smem = sizeof(double) * (size_t)cpc_cap * 33 +
+                             sizeof(float) * ((size_t)cpc_cap * 32 + (size_t)((c.d + 31) & ~31));
+    int dev = 0, optin = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    const size_t budget = (size_t)optin - 1024;   // the kernel's static shared memory and slack
+    if (base_smem > budget) return cudaErrorInvalidValue;   // beyond ~500,000 candidates per SM
+    // as many leading coordinates of the CTA's candidates as fit
+    int qs = (int)((budget - base_smem) / (sizeof(float) * (size_t)cpc_cap * 32));
+    qs = std::max(0, std::min(qs, c.d));
+    const size_t smem = base_smem + sizeof(float) * (size_t)qs * cpc_cap * 32;
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(recluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
             cudaSuccess)
@@ -680,13 +785,16 @@ cudaError_t launch_recluster(Ctx &c, float *centers) {
     const float *CTp = c.rCT;
     const long long *wp = c.w;
     DevState *stp = c.st;
-    int d = c.d, k = c.k, mpv = mp, ncap = nchunk_cap, cpcv = cpc_cap;
+    int d = c.d, k = c.k, mpv = mp, ncap = nchunk_cap, cpcv = cpc_cap, qsv = qs;
     uint64_t seed = c.seed;
     float *rD2 = c.rD2;
     int32_t *chosen = c.chosen;
     double *gch = c.rc_cmass;
-    double *gct = c.rc_cmass + 2 * (size_t)nchunk_cap;
+    unsigned long long *slots = reinterpret_cast<unsigned long long *>(c.rc_cmass + 2 * (size_t)nchunk_cap);
     RcSync *sy = reinterpret_cast<RcSync *>(c.rc_sync);
+    // words from an earlier call could carry this call's tags
+    if ((e = cudaMemsetAsync(slots, 0, sizeof(unsigned long long) * (2 * (size_t)G + 2), c.stream)) != cudaSuccess)
+        return e;
     int *err = c.rc_err;
     // KMPAR_WAIT_CYCLES bounds the grid barrier's wait (fault injection: a budget too
     // short for the CTAs to meet makes the call return KMPAR_ERR_TIMEOUT)
@@ -696,8 +804,8 @@ cudaError_t launch_recluster(Ctx &c, float *centers) {
         const unsigned long long x = std::strtoull(wv, &end, 10);
         if (end && *end == 0 && *wv) wait = x;
     }
-    void *args[] = {&Cp, &CTp, &mpv, &wp, &stp, &d, &k, &seed, &rD2, &chosen, &centers, &gch, &ncap, &gct, &cpcv,
-                    &sy, &err, &wait};
+    void *args[] = {&Cp, &CTp, &mpv, &wp, &stp, &d, &k, &seed, &rD2, &chosen, &centers, &gch, &ncap, &slots, &cpcv,
+                    &qsv, &sy, &err, &wait};
     e = cudaLaunchCooperativeKernel((const void *)recluster_kernel, dim3(G), dim3(kRcThreads), args, smem, c.stream);
     count_launches(1);
     return e;

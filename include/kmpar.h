@@ -32,7 +32,7 @@
  *                          and kmpar_batch_run)
  *   KMPAR_CTX_LIMIT_BYTES  most device memory one context may hold; a larger
  *                          allocation fails with KMPAR_ERR_OOM (read at every one)
- *   KMPAR_WAIT_CYCLES      clock-cycle budget of the grid barrier of the
+ *   KMPAR_WAIT_CYCLES      clock-cycle budget of each per-draw wait of the
  *                          cooperative reclustering kernel (default ~2 s); a wait
  *                          that runs out returns KMPAR_ERR_TIMEOUT
  *   KMPAR_RECLUSTER_GRID   1: use the cooperative grid form of step 8 at any size

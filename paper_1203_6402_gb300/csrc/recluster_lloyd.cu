@@ -796,8 +796,8 @@ cudaError_t launch_recluster(Ctx &c, float *centers) {
     if ((e = cudaMemsetAsync(slots, 0, sizeof(unsigned long long) * (2 * (size_t)G + 2), c.stream)) != cudaSuccess)
         return e;
     int *err = c.rc_err;
-    // KMPAR_WAIT_CYCLES bounds the grid barrier's wait (fault injection: a budget too
-    // short for the CTAs to meet makes the call return KMPAR_ERR_TIMEOUT)
+    // KMPAR_WAIT_CYCLES bounds each per-draw wait (fault injection: a budget too short
+    // for the CTAs to meet makes the call return KMPAR_ERR_TIMEOUT)
     unsigned long long wait = kRcWait;
     if (const char *wv = std::getenv("KMPAR_WAIT_CYCLES")) {
         char *end = nullptr;

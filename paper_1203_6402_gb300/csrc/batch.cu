@@ -542,18 +542,25 @@ __global__ void __launch_bounds__(kBT, DP == 128 ? 1 : 2) batch_kernel(BArgs a, 
                     if (qq < d) C[(int64_t)t * d + qq] = v;
                 }
                 __syncthreads();
-                // D^2 of every candidate to the centers drawn so far: the candidate's row
-                // is loaded into registers first (all loads in flight at once), then the
-                // exact FP32 chain (t = x_q - c_q, fma, q ascending; padded zeros add 0)
+                // D^2 of every candidate to the centers drawn so far, in the exact FP32
+                // chain (t = x_q - c_q, fma, q ascending; padded zeros add 0), 16
+                // coordinates at a time loaded into registers together.  The partial
+                // sums never decrease, so once one reaches the candidate's D^2 the rest
+                // cannot lower it and is skipped (most candidates are far from the pick).
                 for (int j = tid; j < m; j += kBT) {
                     const float *xj = X + (int64_t)cand[j] * d;
-                    float xr[DP];
-#pragma unroll
-                    for (int q = 0; q < DP; ++q) xr[q] = q < d ? __ldg(xj + q) : 0.f;
+                    const float lim = t == 0 ? __uint_as_float(0x7f800000u) : rD2[j];
                     float v = 0.f;
 #pragma unroll
-                    for (int q = 0; q < DP; ++q) sq_acc(xr[q], sh.tile[q], v);
-                    rD2[j] = t == 0 ? v : fminf(rD2[j], v);
+                    for (int q0 = 0; q0 < DP; q0 += 16) {
+                        float xr[16];
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) xr[u] = q0 + u < d ? __ldg(xj + q0 + u) : 0.f;
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) sq_acc(xr[u], sh.tile[q0 + u], v);
+                        if (v >= lim) break;
+                    }
+                    if (v < lim) rD2[j] = v;
                 }
                 __syncthreads();
             }

@@ -55,7 +55,6 @@ cudaError_t launch_weights(Ctx &c) {
 // clock cycles (about 2 s by default): a timeout raises the error word and every CTA
 // returns.
 constexpr int kRcThreads = 768;
-constexpr int kRcPre = 16;        // coordinates per lane loaded ahead of the pick
 constexpr int kRcLaneWords = 8;   // CTA totals per lane of warp 0: G <= 256
 constexpr unsigned long long kRcWait = 4000000000ull;
 
@@ -378,15 +377,6 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
             s_done = (int)((v >> 9) & 1);
             s_abort = !ok;
         }
-        // warps 1.. (phase C's workers) load the first kRcPre global coordinates of
-        // their first chunk while the pick is found: they do not depend on it
-        float pre[kRcPre];
-        const int chp = c0 + wid - 1;
-        const bool use_pre = wid > 0 && chp < c1 && qs + kRcPre <= d && chp * 32 + lane < m;
-        if (use_pre) {
-#pragma unroll
-            for (int u2 = 0; u2 < kRcPre; ++u2) pre[u2] = __ldg(CT + (int64_t)(qs + u2) * mp + chp * 32 + lane);
-        }
         __syncthreads();
         if (s_abort) return;
         if (s_done) {
@@ -416,48 +406,54 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
         // ---- C (warps 1..): D^2 update of own candidates (t = x_q - c_q, fma, q
         // ascending): the first qs coordinates from shared memory, the rest from the
         // transposed copy, 32 loads issued before their FMA chain runs
-        auto update = [&](int ch, bool with_pre) {
+        // A candidate's squared distance is a sum of non-negative terms added in a
+        // fixed order, so its FP32 partial sums never decrease: once every lane's
+        // partial sum has reached its D^2 (a warp vote every 16 coordinates), no D^2
+        // of the warp can change and the rest of the sum is skipped.  Most
+        // candidates are far from the new center, so most warps stop within the
+        // coordinates held in shared memory.
+        auto update = [&](int ch) {
             const int j = ch * 32 + lane;
             const int jl = (ch - c0) * 32 + lane;
-            if (j >= m) return;
+            const bool act = j < m;
+            const float lim = (step == 0 || !act) ? __uint_as_float(0x7f800000u) : dl[jl];
             float v = 0.f;
-            const float *col = CT + j;
+            const float *col = CT + (act ? j : 0);
             int q = 0;
-            for (; q < qs; ++q) {
-                const float t = __fsub_rn(cts[(size_t)q * nl + jl], cnew[q]);
-                v = __fmaf_rn(t, t, v);
-            }
-            if (with_pre) {
-#pragma unroll
-                for (int u2 = 0; u2 < kRcPre; ++u2) {
-                    const float t = __fsub_rn(pre[u2], cnew[q + u2]);
+            bool settled = false;
+            while (q < qs && !settled) {
+                const int qe = min(qs, q + 16);
+                for (; q < qe; ++q) {
+                    const float t = __fsub_rn(cts[(size_t)q * nl + jl], cnew[q]);
                     v = __fmaf_rn(t, t, v);
                 }
-                q += kRcPre;
+                settled = __all_sync(0xffffffffu, !act || v >= lim);
             }
-            // batches of up to 32 loads issued together, then their FMA chain in order
-            for (; q < d; q += 32) {
-                const int nb = min(32, d - q);
-                float buf[32];
+            // the remaining coordinates from the transposed copy: batches of up to 16
+            // loads issued together, then their FMA chain in order
+            while (q < d && !settled) {
+                const int nb = min(16, d - q);
+                float buf[16];
 #pragma unroll
-                for (int u2 = 0; u2 < 32; ++u2) buf[u2] = u2 < nb ? __ldg(col + (int64_t)(q + u2) * mp) : 0.f;
+                for (int u2 = 0; u2 < 16; ++u2) buf[u2] = (act && u2 < nb) ? __ldg(col + (int64_t)(q + u2) * mp) : 0.f;
 #pragma unroll
-                for (int u2 = 0; u2 < 32; ++u2) {
+                for (int u2 = 0; u2 < 16; ++u2) {
                     if (u2 < nb) {
                         const float t = __fsub_rn(buf[u2], cnew[q + u2]);
                         v = __fmaf_rn(t, t, v);
                     }
                 }
+                q += nb;
+                settled = __all_sync(0xffffffffu, !act || v >= lim);
             }
+            if (!act) return;
+            // a settled partial sum is >= D^2, so the minimum keeps D^2 as the full sum would
             const float nv = step == 0 ? v : fminf(dl[jl], v);
             dl[jl] = nv;
             rD2[j] = nv;
         };
-        if (wid > 0 && chp < c1) {
-            if (use_pre) update(chp, true);
-            else update(chp, false);
-            for (int ch = chp + nwarps - 1; ch < c1; ch += nwarps - 1) update(ch, false);
-        }
+        if (wid > 0)
+            for (int ch = c0 + wid - 1; ch < c1; ch += nwarps - 1) update(ch);
         // the next draw's flags order these writes before any CTA reads them
     }
 }
@@ -514,25 +510,47 @@ __host__ __device__ __forceinline__ size_t cl_smem_bytes(int cpc, int d, bool ro
            sizeof(int) * (size_t)cpc;
 }
 
-// exact FP32 difference form, row in shared memory (8-byte loads for even d)
-__device__ __forceinline__ float cl_dist2(const float *x, const float *c, int d) {
+// exact FP32 difference form of a row in shared memory (8-byte loads for even d),
+// stopping once its partial sum reaches lim: the partial sums of non-negative terms
+// never decrease, so a returned value >= lim means the full sum is >= lim too (the
+// caller only needs to know whether it is below lim)
+__device__ __forceinline__ float cl_dist2_lim(const float *x, const float *c, int d, float lim) {
     float s = 0.f;
     if ((d & 1) == 0) {
         const float2 *x2 = reinterpret_cast<const float2 *>(x), *c2 = reinterpret_cast<const float2 *>(c);
-#pragma unroll 4
-        for (int p = 0; p < (d >> 1); ++p) {
-            const float2 a = x2[p], b = c2[p];
-            float t = __fsub_rn(a.x, b.x);
-            s = __fmaf_rn(t, t, s);
-            t = __fsub_rn(a.y, b.y);
-            s = __fmaf_rn(t, t, s);
+        for (int p0 = 0; p0 < (d >> 1); p0 += 8) {
+            const int pe = min(d >> 1, p0 + 8);
+            for (int p = p0; p < pe; ++p) {
+                const float2 a = x2[p], b = c2[p];
+                float t = __fsub_rn(a.x, b.x);
+                s = __fmaf_rn(t, t, s);
+                t = __fsub_rn(a.y, b.y);
+                s = __fmaf_rn(t, t, s);
+            }
+            if (s >= lim) return s;
         }
     } else {
-#pragma unroll 4
-        for (int q = 0; q < d; ++q) {
+        for (int q0 = 0; q0 < d; q0 += 16) {
+            const int qe = min(d, q0 + 16);
+            for (int q = q0; q < qe; ++q) {
+                const float t = __fsub_rn(x[q], c[q]);
+                s = __fmaf_rn(t, t, s);
+            }
+            if (s >= lim) return s;
+        }
+    }
+    return s;
+}
+__device__ __forceinline__ float dist2_fp32_lim(const float *__restrict__ x, const float *__restrict__ c, int d,
+                                                float lim) {
+    float s = 0.f;
+    for (int q0 = 0; q0 < d; q0 += 16) {
+        const int qe = min(d, q0 + 16);
+        for (int q = q0; q < qe; ++q) {
             const float t = __fsub_rn(x[q], c[q]);
             s = __fmaf_rn(t, t, s);
         }
+        if (s >= lim) return s;
     }
     return s;
 }
@@ -689,9 +707,11 @@ __global__ void __launch_bounds__(kClThreads, 1)
             if (rank == 0) centers[(int64_t)step * d + qq] = v;
         }
         __syncthreads();
+        // partial sums stop once they reach the candidate's D^2 (then no update)
         for (int j = j0 + t_id; j < j1; j += kClThreads) {
-            const float v = rows_in_smem ? cl_dist2(rows + (int64_t)(j - j0) * rs, cnew, d)
-                                         : dist2_fp32(rows + (int64_t)(j - j0) * d, cnew, d);
+            const float lim = step == 0 ? __uint_as_float(0x7f800000u) : rd2[j - j0];
+            const float v = rows_in_smem ? cl_dist2_lim(rows + (int64_t)(j - j0) * rs, cnew, d, lim)
+                                         : dist2_fp32_lim(rows + (int64_t)(j - j0) * d, cnew, d, lim);
             if (step == 0 || v < rd2[j - j0]) {
                 rd2[j - j0] = v;
                 dirty[(j - j0) >> 5] = 1;

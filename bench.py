@@ -465,7 +465,9 @@ def run_ours(args, rank, world):
         if traffic is None:
             roofline["traffic_note"] = ("no ncu capture of the current kernel source" if cap_sha is None else
                                         f"capture taken on kernel source {cap_sha}, which has changed since")
-    roofline.update({"avg_launch_ms": per_launch_ms, "launches": kl})
+    roofline.update({"avg_launch_ms": per_launch_ms, "launches": kl,
+                     "classes": {c: {"ms": kern[c][0], "launches": kern[c][1],
+                                     "avg_launch_ms": kern[c][0] / max(kern[c][1], 1)} for c in kern}})
 
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -362,6 +362,33 @@ __global__ void __launch_bounds__(256) anchor_final_kernel(const double *__restr
 // (||c'|| <= ||x'|| + sqrt(ub (1 + 2 W)); farther ones exceed ub (1 + 2 W) by the
 // triangle inequality).  Any center left off the list then has an exact distance
 // above ub (1 + 2 W) (see the list refine).
+// list threshold of a row whose nearest distance is at most u (exact FP32): every
+// center whose screened value exceeds it is provably farther than the nearest one
+// (twice the screening bound plus the FP32 tie window); +inf without a bound
+__device__ __forceinline__ float list_threshold(float u, float xnorm, float cmax, float ep, float en, float ec,
+                                                float W) {
+    const float xn = fmaxf(xnorm, 0.f);
+    const float X = sqrtf(xn);
+    float t = __uint_as_float(0x7F800000u);
+    if (u < FLT_MAX) {
+        const float lim = fmaxf(u, 0.f) * (1.f + 2.f * W);
+        const float ceff = fminf(cmax, X + sqrtf(lim));
+        const float Eo = ep * X * ceff + en * (xn + ceff * ceff) + ec * X * cmax;
+        t = u - xn + 1.02f * (Eo + 2.f * W * fmaxf(u, 0.f)) + 1e-30f;
+    }
+    return t;
+}
+
+__global__ void __launch_bounds__(256) row_thresholds_kernel(const float *__restrict__ ub, int64_t n, int d,
+                                                             const float *__restrict__ xnorm,
+                                                             const unsigned int *cmax_bits, float ep, float en,
+                                                             float ec, float *__restrict__ thr) {
+    const float W = fp32_tie_window(d);
+    const float cmax = __uint_as_float(*cmax_bits);
+    for (int64_t R = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; R < n; R += (int64_t)gridDim.x * blockDim.x)
+        thr[R] = list_threshold(ub[R], xnorm[R], cmax, ep, en, ec, W);
+}
+
 __global__ void __launch_bounds__(256) gather_rows_kernel(const uint8_t *__restrict__ img,
                                                           const float *__restrict__ xscale, int d, int KA,
                                                           const int32_t *__restrict__ rows, const int *cnt,
@@ -383,17 +410,7 @@ __global__ void __launch_bounds__(256) gather_rows_kernel(const uint8_t *__restr
         *reinterpret_cast<uint4 *>(dst) = __ldg(reinterpret_cast<const uint4 *>(src));
         if (a == 0 && ch == 0) {
             cscale[i] = xscale ? xscale[R] : 1.f;
-            const float u = ub[R];
-            const float xn = fmaxf(xnorm[R], 0.f);
-            const float X = sqrtf(xn);
-            float t = __uint_as_float(0x7F800000u);
-            if (u < FLT_MAX) {
-                const float lim = fmaxf(u, 0.f) * (1.f + 2.f * W);
-                const float ceff = fminf(cmax, X + sqrtf(lim));
-                const float Eo = ep * X * ceff + en * (xn + ceff * ceff) + ec * X * cmax;
-                t = u - xn + 1.02f * (Eo + 2.f * W * fmaxf(u, 0.f)) + 1e-30f;
-            }
-            thr[i] = t;
+            thr[i] = list_threshold(ub[R], xnorm[R], cmax, ep, en, ec, W);
         }
     }
 }
@@ -527,6 +544,15 @@ cudaError_t launch_gather_rows(const uint8_t *img, const float *xscale, int d, i
                                cudaStream_t s) {
     gather_rows_kernel<<<grid, 256, 0, s>>>(img, fmt == FMT_FP8 ? xscale : nullptr, d, tc_katoms(d, fmt), rows, cnt,
                                             ub, xnorm, cmax_bits, ep, en, ec, cimg, cscale, thr);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_thresholds(const float *ub, int64_t n, int d, const float *xnorm,
+                                  const unsigned int *cmax_bits, float ep, float en, float ec, float *thr,
+                                  cudaStream_t s) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(4096, (n + 255) / 256));
+    row_thresholds_kernel<<<grid, 256, 0, s>>>(ub, n, d, xnorm, cmax_bits, ep, en, ec, thr);
     count_launches(1);
     return cudaGetLastError();
 }

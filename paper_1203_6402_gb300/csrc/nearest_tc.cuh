@@ -20,8 +20,9 @@ enum Fmt {
 
 // what the epilogue keeps per row
 enum Epi {
-    EPI_PAIR = 0,    // the best pair of adjacent centers and the best screened value outside it
-    EPI_LIST = 1     // every center whose screened value is at most the row's threshold
+    EPI_PAIR = 0,     // the best pair of adjacent centers and the best screened value outside it
+    EPI_LIST = 1,     // every center whose screened value is at most the row's threshold
+    EPI_PAIRLIST = 2  // both (groups of four): the pair result and the list, for every row
 };
 
 constexpr int kListSlots = 8;   // list entries per row and column group (4 groups per row)
@@ -44,9 +45,9 @@ struct TcParams {
     int32_t *cand1;          // EPI_PAIR: per row, first center of the best screened group (-1: none)
     float *v2;               // EPI_PAIR: per row, smallest screened value outside that group (key-truncated)
     const int *nrows_dev;    // EPI_LIST: number of listed rows
-    const float *thr;        // EPI_LIST: per listed row, the screened-value threshold
-    int32_t *lst;            // EPI_LIST: per listed row, 4 x kListSlots pass-local center numbers
-    int32_t *lcnt;           // EPI_LIST: per listed row and group, entries found (> kListSlots: overflow)
+    const float *thr;        // EPI_LIST: per listed row (EPI_PAIRLIST: per row), the screened-value threshold
+    int32_t *lst;            // EPI_LIST / EPI_PAIRLIST: per row, 4 x kListSlots pass-local center numbers
+    int32_t *lcnt;           // per row and group, entries found (> kListSlots: overflow)
     int32_t *fix_rows;       // rows left to the exact CUDA-core pass
     int *fix_cnt;
     unsigned long long *fp64_cnt;
@@ -86,6 +87,11 @@ cudaError_t launch_gather_rows(const uint8_t *img, const float *xscale, int d, i
                                cudaStream_t s);
 // screening error bound E(x, c) = ep ||x'|| ||c'|| + en (||x'||^2 + ||c'||^2) + ec ||x'|| max ||c'||
 void tc_bound(int d, int fmt, float *ep, float *en, float *ec);
+// per row R < n, the list threshold of a row whose nearest distance is at most ub[R]
+// (the same threshold as launch_gather_rows writes for a listed row)
+cudaError_t launch_row_thresholds(const float *ub, int64_t n, int d, const float *xnorm,
+                                  const unsigned int *cmax_bits, float ep, float en, float ec, float *thr,
+                                  cudaStream_t s);
 
 }  // namespace tc
 }  // namespace kmp

@@ -7,6 +7,7 @@ namespace tc {
 
 cudaError_t dispatch_bf16x3(const TcParams &p, int mode_round, int epi, int KA, int grid, cudaStream_t s) {
     if (epi == EPI_LIST) return cudaErrorInvalidValue;   // the split format has no list pass
+    if (epi == EPI_PAIRLIST) return cudaErrorInvalidValue;   // groups of four only
     return dispatch_fmt<FMT_BF16X3, EPI_PAIR>(p, mode_round, KA, grid, s);
 }
 

@@ -188,7 +188,7 @@ struct Cfg {
 template <int KA, int BN, int S, int A16B, int EPI>
 constexpr size_t smem_bytes() {
     return 1024 + (size_t)S * Cfg<KA, BN>::B_BYTES + (size_t)A16B * Cfg<KA, BN>::A16_BYTES + sizeof(Smem) +
-           (EPI == EPI_LIST ? sizeof(int32_t) * kListSlots * kEpiThreads : 0) +
+           (EPI != EPI_PAIR ? sizeof(int32_t) * kListSlots * kEpiThreads : 0) +
            sizeof(float) * kEpiWarps * 2 * Cfg<KA, BN>::NB;
 }
 
@@ -230,6 +230,9 @@ template <int KA, int BN, int S, int A16B, int FMT, int EPI, int GS>
 __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int mode_round) {
     using C = Cfg<KA, BN>;
     constexpr bool NE = FMT == FMT_BF16N || FMT == FMT_FP8;
+    constexpr bool PAIR = EPI != EPI_LIST;       // the best group and the best value outside it
+    constexpr bool PLIST = EPI == EPI_PAIRLIST;  // and the listing of groups at or below thr
+    static_assert(!PLIST || (GS == 4 && NE), "listing pair screening: groups of four, norms in the epilogue");
     extern __shared__ __align__(1024) uint8_t dsmem[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~(uintptr_t)1023);
     uint8_t *bst = base;                                   // S B stages
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
     int32_t *lsm = reinterpret_cast<int32_t *>(&sm + 1);   // EPI_LIST: kListSlots x kEpiThreads
     // per epilogue warp, two buffers of its column group's norms (and the FP8 tile
     // scale), filled one tile ahead by cp.async
-    float *nbuf = reinterpret_cast<float *>(lsm + (EPI == EPI_LIST ? kListSlots * kEpiThreads : 0));
+    float *nbuf = reinterpret_cast<float *>(lsm + (EPI != EPI_PAIR ? kListSlots * kEpiThreads : 0));
     volatile int *abort = &sm.abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -388,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
             if (FMT == FMT_FP8) fx = R < n ? -2.f * p.xscale[R] : 0.f;
             // EPI_LIST: the row's threshold (pad rows list nothing)
             float thr = -INF;
-            if (EPI == EPI_LIST && R < n) thr = p.thr[R];
+            if (EPI != EPI_PAIR && R < n) thr = p.thr[R];
             int lcount = 0;
             float K1 = INF, K2 = INF;
             int T1 = 0;
@@ -428,7 +431,7 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
 #pragma unroll
                     for (int cc = 0; cc < 2; ++cc) {
                         if (c + cc >= C::CHUNKS) break;
-                        if (EPI == EPI_PAIR) {
+                        if (PAIR) {
 #pragma unroll
                             for (int q = 0; q < 32; q += 8) {
                                 // value-only minimum of each pair of adjacent centers, then a
@@ -452,6 +455,18 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
                                     const uint32_t gc = (uint32_t)(((c + cc) * 32 + q) >> 2);
                                     const float m0 = fminf(min3f(v[0], v[1], v[2]), v[3]);
                                     const float m1 = fminf(min3f(v[4], v[5], v[6]), v[7]);
+                                    if (PLIST && lcount <= kListSlots && fminf(m0, m1) <= thr) {
+                                        // (rarely) list the centers at or below the row's threshold;
+                                        // an overflowed list stops here (its row takes the list pass)
+                                        const int col0 = t * BN + grp * C::GW + (c + cc) * 32 + q;
+#pragma unroll
+                                        for (int u = 0; u < 8; ++u) {
+                                            if (v[u] <= thr) {
+                                                if (lcount < kListSlots) lsm[lcount * kEpiThreads + etid] = col0 + u;
+                                                ++lcount;
+                                            }
+                                        }
+                                    }
                                     const float a = __uint_as_float((__float_as_uint(m0) & vmask) | gc);
                                     const float b = __uint_as_float((__float_as_uint(m1) & vmask) | (gc + 1));
                                     const float lo = fminf(a, b), hi = fmaxf(a, b);
@@ -515,7 +530,7 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
                         }
                     }
                 }
-                if (EPI == EPI_PAIR) {
+                if (PAIR) {
                     const float k1 = fminf(k1a, k1b);
                     const float k2 = min3f(fmaxf(k1a, k1b), k2a, k2b);
                     if (k1 < K1) { K2 = fminf(K1, k2); K1 = k1; T1 = t; }
@@ -523,14 +538,14 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
                 }
             }
             if (!ok) break;
-            if (EPI == EPI_LIST) {
+            if (EPI != EPI_PAIR) {
                 // each column group writes its own part of the row's list
                 if (R < n) {
                     p.lcnt[R * kGroups + grp] = lcount;
                     const int w = lcount < kListSlots ? lcount : kListSlots;
                     for (int s = 0; s < w; ++s) p.lst[(R * kGroups + grp) * kListSlots + s] = lsm[s * kEpiThreads + etid];
                 }
-                continue;
+                if (EPI == EPI_LIST) continue;
             }
             // merge the column groups through shared memory (bounded waits only)
             if (grp > 0) {

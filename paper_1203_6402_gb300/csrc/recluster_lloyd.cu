@@ -32,7 +32,7 @@ cudaError_t launch_weights(Ctx &c) {
 
 // ------------------------------------------------------------------ step 8
 // Weighted k-means++ (Alg. 1 with multiplicities w): k sequential draws over the m
-// candidates.  One cooperative launch, one CTA of 768 threads per SM; the
+// candidates.  One cooperative launch, one CTA of 704 threads per SM; the
 // candidates are cut into fixed chunks of 32 (FP64 shuffle scans) and CTA b owns
 // the contiguous chunk range [b cpc, (b+1) cpc); its warps 1.. take its chunks in
 // phases A and C, warp 0 takes phase B.  Per draw t:
@@ -54,7 +54,8 @@ cudaError_t launch_weights(Ctx &c) {
 // every CTA has finished reading draw t's.  One wait per draw, bounded by `wait`
 // clock cycles (about 2 s by default): a timeout raises the error word and every CTA
 // returns.
-constexpr int kRcThreads = 768;
+constexpr int kRcThreads = 704;   // 21 chunk workers + the pick warp; 88 registers a thread
+constexpr int kRcPre = 16;        // global coordinates per lane loaded while the pick is found
 constexpr int kRcLaneWords = 8;   // CTA totals per lane of warp 0: G <= 256
 constexpr unsigned long long kRcWait = 4000000000ull;
 
@@ -377,6 +378,16 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
             s_done = (int)((v >> 9) & 1);
             s_abort = !ok;
         }
+        // warps 1.. load the first global coordinates of their first chunk while the
+        // pick is found (they do not depend on it)
+        float pre[kRcPre];
+        const int chp = c0 + wid - 1;
+        const int np = (wid > 0 && chp < c1) ? max(0, min(kRcPre, d - qs)) : 0;
+        {
+            const int jp = min(chp * 32 + lane, m - 1);
+#pragma unroll
+            for (int u2 = 0; u2 < kRcPre; ++u2) pre[u2] = u2 < np ? __ldg(CT + (int64_t)(qs + u2) * mp + jp) : 0.f;
+        }
         __syncthreads();
         if (s_abort) return;
         if (s_done) {
@@ -412,7 +423,7 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
         // of the warp can change and the rest of the sum is skipped.  Most
         // candidates are far from the new center, so most warps stop within the
         // coordinates held in shared memory.
-        auto update = [&](int ch) {
+        auto update = [&](int ch, bool first) {
             const int j = ch * 32 + lane;
             const int jl = (ch - c0) * 32 + lane;
             const bool act = j < m;
@@ -429,15 +440,27 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
                 }
                 settled = __all_sync(0xffffffffu, !act || v >= lim);
             }
-            // the remaining coordinates from the transposed copy: batches of up to 16
-            // loads issued together, then their FMA chain in order
+            // the remaining coordinates from the transposed copy: those loaded ahead,
+            // then batches of up to 32 loads issued together, each followed by its FMA
+            // chain in order
+            if (first && !settled && np > 0) {
+#pragma unroll
+                for (int u2 = 0; u2 < kRcPre; ++u2) {
+                    if (u2 < np) {
+                        const float t = __fsub_rn(pre[u2], cnew[q + u2]);
+                        v = __fmaf_rn(t, t, v);
+                    }
+                }
+                q += np;
+                settled = __all_sync(0xffffffffu, !act || v >= lim);
+            }
             while (q < d && !settled) {
-                const int nb = min(16, d - q);
-                float buf[16];
+                const int nb = min(32, d - q);
+                float buf[32];
 #pragma unroll
-                for (int u2 = 0; u2 < 16; ++u2) buf[u2] = (act && u2 < nb) ? __ldg(col + (int64_t)(q + u2) * mp) : 0.f;
+                for (int u2 = 0; u2 < 32; ++u2) buf[u2] = (act && u2 < nb) ? __ldg(col + (int64_t)(q + u2) * mp) : 0.f;
 #pragma unroll
-                for (int u2 = 0; u2 < 16; ++u2) {
+                for (int u2 = 0; u2 < 32; ++u2) {
                     if (u2 < nb) {
                         const float t = __fsub_rn(buf[u2], cnew[q + u2]);
                         v = __fmaf_rn(t, t, v);
@@ -452,8 +475,10 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
             dl[jl] = nv;
             rD2[j] = nv;
         };
-        if (wid > 0)
-            for (int ch = c0 + wid - 1; ch < c1; ch += nwarps - 1) update(ch);
+        if (wid > 0 && chp < c1) {
+            update(chp, true);
+            for (int ch = chp + nwarps - 1; ch < c1; ch += nwarps - 1) update(ch, false);
+        }
         // the next draw's flags order these writes before any CTA reads them
     }
 }

@@ -573,6 +573,15 @@ cudaError_t count_fixups(Ctx &c, const int *exact_cnt) {
     return cudaGetLastError();
 }
 
+// the two halves of count_fixups when the undecided rows pass through several stages
+__global__ void count_stage_kernel(const int *fallback_cnt, const int *exact_cnt, int64_t n, DevState *st) {
+    if (fallback_cnt) {
+        st->screen_fallback += (unsigned long long)*fallback_cnt;
+        st->screen_rows += (unsigned long long)n;
+    }
+    if (exact_cnt) st->screen_exact += (unsigned long long)*exact_cnt;
+}
+
 // Exact FP32 distances and the decision for the rows the tensor screening has
 // brought down to one pair of adjacent centers (cand1 = the pair's first center,
 // -1: none).  Both centers of the pair get the exact FP32 difference form
@@ -1343,7 +1352,7 @@ __device__ __forceinline__ float dist2_fp32_v4(const float *__restrict__ x, cons
 // left off the list (screened value above thr[i]) is, by the screening bound,
 // beyond the tie window of the deciding distance (bound_certain).  Certain rows
 // take decide_top2, the others go to the exact scan's list (rows2).
-template <int MODE>
+template <int MODE, bool BYROW>
 __global__ void __launch_bounds__(256) refine_list_kernel(
     const float *__restrict__ X, int d, const float *__restrict__ C, int c_cnt, const int32_t *__restrict__ rows,
     const int *rows_cnt, const int32_t *__restrict__ lst, const int32_t *__restrict__ lcnt,
@@ -1360,7 +1369,8 @@ __global__ void __launch_bounds__(256) refine_list_kernel(
     const float FMAX = FLT_MAX;
     for (int64_t i = gw; i < nrows; i += W) {   // uniform per warp
         const int64_t R = rows[i];
-        const int cg = lane < 4 ? lcnt[i * 4 + lane] : 0;
+        const int64_t li = BYROW ? R : i;   // the row's lists and threshold: by row, or by list position
+        const int cg = lane < 4 ? lcnt[li * 4 + lane] : 0;
         const bool over = __any_sync(0xffffffffu, cg > S);
         const int c0 = __shfl_sync(0xffffffffu, cg, 0), c1 = __shfl_sync(0xffffffffu, cg, 1);
         const int c2 = __shfl_sync(0xffffffffu, cg, 2), c3 = __shfl_sync(0xffffffffu, cg, 3);
@@ -1373,7 +1383,7 @@ __global__ void __launch_bounds__(256) refine_list_kernel(
             else if ((sidx -= c1) < c2) g = 2;
             else if ((sidx -= c2) < c3) g = 3;
             if (g >= 0) {
-                const int col = lst[(i * 4 + g) * S + sidx];
+                const int col = lst[(li * 4 + g) * S + sidx];
                 if (col >= 0 && col < cnt) {
                     const int j = begin + col;
                     b1 = dist2_fp32_v4(X + R * d, C + (int64_t)j * d, d);
@@ -1391,7 +1401,7 @@ __global__ void __launch_bounds__(256) refine_list_kernel(
             bool certain = false;
             if (!over) {
                 const float m = deciding<MODE>(D2, R, i1 != INT_MAX ? b1 : FMAX);
-                certain = m < FMAX && bound_certain(sb, sb.xnorm[R], m, thr[i], d);
+                certain = m < FMAX && bound_certain(sb, sb.xnorm[R], m, thr[li], d);
             }
             if (certain) {
                 if (i2 == INT_MAX) { i2 = -1; b2 = FMAX; }
@@ -1429,14 +1439,26 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
     const bool direct = rp.parts == 0 && (c.d & 3) == 0 &&
                         ((reinterpret_cast<uintptr_t>(c.X) | reinterpret_cast<uintptr_t>(C)) & 15u) == 0;
     p.group = (direct && tc::tc_norms_in_epilogue(fmt)) ? 4 : 2;
-    cudaEvent_t ev = nullptr;
-    if ((e = timing_begin(c, &ev)) != cudaSuccess) return e;
-    if ((e = tc::launch_nearest_tc(p, mode_round, tc::EPI_PAIR, c.num_sms, c.stream)) != cudaSuccess) return e;
-    if ((e = timing_end(c, ev, timing_cls)) != cudaSuccess) return e;
     ScreenBound sb{};
     sb.xnorm = c.tc_xnorm; sb.cmax_bits = c.tc_cmax; sb.st = c.st;
     sb.fix_rows = c.fix_rows; sb.fix_cnt = c.fix_cnt; sb.ub = c.tc_ub;
     tc::tc_bound(c.d, fmt, &sb.ep, &sb.en, &sb.ec);
+    // a round pass whose rows already have a nearest distance D^2 lists, in the
+    // screening pass itself, every center within that distance (plus the bound):
+    // the rows the groups leave undecided then need no second screening
+    const bool plist = mode_round && p.group == 4 && c.tc_list;
+    if (plist) {
+        if ((e = tc::launch_row_thresholds(c.D2, c.n, c.d, c.tc_xnorm, c.tc_cmax, sb.ep, sb.en, sb.ec, c.tc_thr,
+                                           c.stream)) != cudaSuccess)
+            return e;
+        p.thr = c.tc_thr; p.lst = c.tc_lst; p.lcnt = c.tc_lcnt;
+    }
+    cudaEvent_t ev = nullptr;
+    if ((e = timing_begin(c, &ev)) != cudaSuccess) return e;
+    if ((e = tc::launch_nearest_tc(p, mode_round, plist ? tc::EPI_PAIRLIST : tc::EPI_PAIR, c.num_sms, c.stream)) !=
+        cudaSuccess)
+        return e;
+    if ((e = timing_end(c, ev, timing_cls)) != cudaSuccess) return e;
     if (rp.parts > 0) {
         const int rw = rp.warps;
         const size_t rsm = resident_smem_bytes(rp.hold, c.d, rw);
@@ -1493,32 +1515,54 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
         if ((e = count_fixups(c, nullptr)) != cudaSuccess) return e;
         return launch_fixup(c, mode_round, C, k, labels, prev, changed, dmin, c.fix_rows, c.fix_cnt);
     }
-    // rows the pair screening left undecided: a second screening of just those rows
-    // that lists every center within twice the screening bound of the row's deciding
-    // distance, the exact FP32 form of the listed centers, and the exact scan only
-    // for rows whose lists overflowed or stayed uncertain
-    if ((e = cudaMemsetAsync(c.fix_cnt2, 0, sizeof(int), c.stream)) != cudaSuccess) return e;
-    if ((e = tc::launch_gather_rows(c.tc_ximg, c.tc_xscale, c.d, fmt, c.fix_rows, c.fix_cnt, c.tc_ub, c.tc_xnorm,
-                                    c.tc_cmax, sb.ep, sb.en, sb.ec, c.tc_cimg, c.tc_cscale, c.tc_thr,
-                                    c.num_sms * 8, c.stream)) != cudaSuccess)
-        return e;
-    tc::TcParams pl = p;
-    pl.ximg = c.tc_cimg; pl.xscale = c.tc_cscale;
-    pl.nrows_dev = c.fix_cnt; pl.thr = c.tc_thr; pl.lst = c.tc_lst; pl.lcnt = c.tc_lcnt;
-    if ((e = tc::launch_nearest_tc(pl, mode_round, tc::EPI_LIST, c.num_sms, c.stream)) != cudaSuccess) return e;
     const int lgrid = c.num_sms * 8;
-    if (mode_round)
-        refine_list_kernel<MODE_ROUND><<<lgrid, 256, 0, c.stream>>>(
-            c.X, c.d, C, 0, c.fix_rows, c.fix_cnt, c.tc_lst, c.tc_lcnt, c.tc_thr, sb, c.fix_rows2, c.fix_cnt2, c.D2,
-            c.idx, nullptr, nullptr, nullptr, nullptr, &c.st->argmin_fp64, &c.st->argmin_wide);
-    else
-        refine_list_kernel<MODE_ASSIGN><<<lgrid, 256, 0, c.stream>>>(
-            c.X, c.d, C, k, c.fix_rows, c.fix_cnt, c.tc_lst, c.tc_lcnt, c.tc_thr, sb, c.fix_rows2, c.fix_cnt2,
-            nullptr, nullptr, labels, prev, changed, dmin, &c.st->argmin_fp64, &c.st->argmin_wide);
+    // rows the pair screening left undecided (rows_in, cnt_in): a second screening of
+    // just those rows that lists every center within twice the screening bound of
+    // the row's deciding distance, the exact FP32 form of the listed centers, and the
+    // exact scan only for rows whose lists overflowed or stayed uncertain (rows_out)
+    auto list_pass = [&](int32_t *rows_in, int *cnt_in, int32_t *rows_out, int *cnt_out) -> cudaError_t {
+        cudaError_t e2;
+        if ((e2 = cudaMemsetAsync(cnt_out, 0, sizeof(int), c.stream)) != cudaSuccess) return e2;
+        if ((e2 = tc::launch_gather_rows(c.tc_ximg, c.tc_xscale, c.d, fmt, rows_in, cnt_in, c.tc_ub, c.tc_xnorm,
+                                         c.tc_cmax, sb.ep, sb.en, sb.ec, c.tc_cimg, c.tc_cscale, c.tc_thr,
+                                         c.num_sms * 8, c.stream)) != cudaSuccess)
+            return e2;
+        tc::TcParams pl = p;
+        pl.ximg = c.tc_cimg; pl.xscale = c.tc_cscale;
+        pl.nrows_dev = cnt_in; pl.thr = c.tc_thr; pl.lst = c.tc_lst; pl.lcnt = c.tc_lcnt;
+        if ((e2 = tc::launch_nearest_tc(pl, mode_round, tc::EPI_LIST, c.num_sms, c.stream)) != cudaSuccess) return e2;
+        if (mode_round)
+            refine_list_kernel<MODE_ROUND, false><<<lgrid, 256, 0, c.stream>>>(
+                c.X, c.d, C, 0, rows_in, cnt_in, c.tc_lst, c.tc_lcnt, c.tc_thr, sb, rows_out, cnt_out, c.D2, c.idx,
+                nullptr, nullptr, nullptr, nullptr, &c.st->argmin_fp64, &c.st->argmin_wide);
+        else
+            refine_list_kernel<MODE_ASSIGN, false><<<lgrid, 256, 0, c.stream>>>(
+                c.X, c.d, C, k, rows_in, cnt_in, c.tc_lst, c.tc_lcnt, c.tc_thr, sb, rows_out, cnt_out, nullptr,
+                nullptr, labels, prev, changed, dmin, &c.st->argmin_fp64, &c.st->argmin_wide);
+        count_launches(1);
+        return cudaGetLastError();
+    };
+    if (!plist) {
+        if ((e = list_pass(c.fix_rows, c.fix_cnt, c.fix_rows2, c.fix_cnt2)) != cudaSuccess) return e;
+        if ((e = count_fixups(c, c.fix_cnt2)) != cudaSuccess) return e;
+        return launch_fixup(c, mode_round, C, k, labels, prev, changed, dmin, c.fix_rows2, c.fix_cnt2);
+    }
+    // the lists the screening pass kept: the exact FP32 form of the listed centers;
+    // rows whose lists overflowed or stayed uncertain take the list pass, and the
+    // rows that one leaves, the exact scan
+    if ((e = cudaMemsetAsync(c.fix_cnt2, 0, sizeof(int), c.stream)) != cudaSuccess) return e;
+    refine_list_kernel<MODE_ROUND, true><<<lgrid, 256, 0, c.stream>>>(
+        c.X, c.d, C, 0, c.fix_rows, c.fix_cnt, c.tc_lst, c.tc_lcnt, c.tc_thr, sb, c.fix_rows2, c.fix_cnt2, c.D2, c.idx,
+        nullptr, nullptr, nullptr, nullptr, &c.st->argmin_fp64, &c.st->argmin_wide);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = count_fixups(c, c.fix_cnt2)) != cudaSuccess) return e;
-    return launch_fixup(c, mode_round, C, k, labels, prev, changed, dmin, c.fix_rows2, c.fix_cnt2);
+    count_stage_kernel<<<1, 1, 0, c.stream>>>(c.fix_cnt, nullptr, c.n, c.st);
+    count_launches(1);
+    if ((e = list_pass(c.fix_rows2, c.fix_cnt2, c.fix_rows, c.fix_cnt)) != cudaSuccess) return e;
+    count_stage_kernel<<<1, 1, 0, c.stream>>>(nullptr, c.fix_cnt, c.n, c.st);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_fixup(c, mode_round, C, k, labels, prev, changed, dmin, c.fix_rows, c.fix_cnt);
 }
 
 }  // namespace kmp

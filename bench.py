@@ -499,14 +499,22 @@ def run_ours(args, rank, world):
 
 
 def screen_shape(precision: str, d: int):
-    """(K columns the MMA executes, centers per tile) of the screening pass."""
+    """(K elements the MMA executes, centers per tile) of the screening pass, as the
+    library chooses them: K bytes per row for the format (BF16 adds two norm columns
+    unless they would cost a 128-byte K atom, then the norms go to the epilogue),
+    MMAs of 32 bytes of K, 256-wide center tiles up to two K atoms and 128-wide beyond."""
     if precision == "bf16x3":
-        kk = (3 * d + 2 + 15) // 16 * 16
+        kbytes, esz = 2 * (3 * d + 2), 2
     elif precision == "fp8":
-        kk = (d + 31) // 32 * 32
+        kbytes, esz = d, 1
     else:
-        kk = (d + 2 + 15) // 16 * 16
-    bn = 256 if kk <= 128 or precision == "fp8" else 128
+        kbytes = 2 * (d + 2)
+        if (d + 2 + 63) // 64 > (d + 63) // 64:
+            kbytes = 2 * d
+        esz = 2
+    katoms = (kbytes + 127) // 128
+    kk = (kbytes + 31) // 32 * (32 // esz)
+    bn = 256 if katoms <= 2 else 128
     return kk, bn
 
 

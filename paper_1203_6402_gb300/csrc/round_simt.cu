@@ -1446,7 +1446,9 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
     // a round pass whose rows already have a nearest distance D^2 lists, in the
     // screening pass itself, every center within that distance (plus the bound):
     // the rows the groups leave undecided then need no second screening
-    const bool plist = mode_round && p.group == 4 && c.tc_list;
+    // (Not in the first round: its rows' D^2 is the distance to the first center alone,
+    // far above the spread of any cluster, so their lists would only overflow.)
+    const bool plist = mode_round && p.group == 4 && c.tc_list && c.rounds_done >= 1;
     if (plist) {
         if ((e = tc::launch_row_thresholds(c.D2, c.n, c.d, c.tc_xnorm, c.tc_cmax, sb.ep, sb.en, sb.ec, c.tc_thr,
                                            c.stream)) != cudaSuccess)

@@ -113,6 +113,9 @@ typedef struct {
                                      to the list pass, or, in BF16X3, to the exact
                                      CUDA-core scan)                                 */
     int64_t screen_exact;         /* rows the exact CUDA-core scan decided             */
+    int64_t screen_listed;        /* undecided rows of round passes that went to the
+                                     exact refine over the lists the screening pass
+                                     itself kept (the others took the list pass)     */
 } kmpar_stats;
 
 /*

@@ -604,6 +604,7 @@ kmpar_status kmpar_get_stats(kmpar_ctx *ctx, kmpar_stats *out) {
     out->screen_rows = (int64_t)st.screen_rows;
     out->screen_fallback = (int64_t)st.screen_fallback;
     out->screen_exact = (int64_t)st.screen_exact;
+    out->screen_listed = (int64_t)st.screen_listed;
     KMP_CUDA(&c, kmp::timing_drain(c), "timing");
     for (int i = 0; i < 2; ++i) {
         out->kernel_ms[i] = c.kernel_ms[i];

@@ -37,6 +37,7 @@ struct DevState {
     unsigned long long sample_near, sample_refined, argmin_fp64, argmin_wide, recluster_near;
     unsigned long long screen_rows, screen_fallback;   // tensor passes: rows screened, rows the pair screening left
     unsigned long long screen_exact;                   // rows that needed the exact scan
+    unsigned long long screen_listed;                  // undecided round rows refined from the pass's own lists
 };
 
 struct Ctx {

@@ -575,8 +575,9 @@ cudaError_t count_fixups(Ctx &c, const int *exact_cnt) {
 
 // the two halves of count_fixups when the undecided rows pass through several stages
 __global__ void count_stage_kernel(const int *fallback_cnt, const int *exact_cnt, int64_t n, DevState *st) {
-    if (fallback_cnt) {
+    if (fallback_cnt) {   // the rows the pair screening left, all refined from their own lists
         st->screen_fallback += (unsigned long long)*fallback_cnt;
+        st->screen_listed += (unsigned long long)*fallback_cnt;
         st->screen_rows += (unsigned long long)n;
     }
     if (exact_cnt) st->screen_exact += (unsigned long long)*exact_cnt;

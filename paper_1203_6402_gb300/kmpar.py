@@ -41,7 +41,7 @@ class kmpar_stats(ctypes.Structure):
                 ("capacity_overflow", ctypes.c_int32), ("recluster_warn", ctypes.c_int32),
                 ("kernel_ms", ctypes.c_double * 2), ("kernel_launches", ctypes.c_int64 * 2),
                 ("screen_rows", ctypes.c_int64), ("screen_fallback", ctypes.c_int64),
-                ("screen_exact", ctypes.c_int64)]
+                ("screen_exact", ctypes.c_int64), ("screen_listed", ctypes.c_int64)]
 
     def to_dict(self) -> dict:
         r = self.rounds_done
@@ -52,7 +52,8 @@ class kmpar_stats(ctypes.Structure):
                     recluster_near=self.recluster_near, capacity_overflow=self.capacity_overflow,
                     recluster_warn=self.recluster_warn, kernel_ms=list(self.kernel_ms),
                     kernel_launches=list(self.kernel_launches), screen_rows=self.screen_rows,
-                    screen_fallback=self.screen_fallback, screen_exact=self.screen_exact)
+                    screen_fallback=self.screen_fallback, screen_exact=self.screen_exact,
+                    screen_listed=self.screen_listed)
 
 
 class kmpar_problem(ctypes.Structure):

@@ -278,6 +278,33 @@ def test_tensor_paths_match_fp32_path_wide_rows(km):
         assert st["screen_fallback"] > 0 and st["screen_exact"] < st["screen_fallback"], (prec, st)
 
 
+def test_round_pass_lists_match_fp32_path(km):
+    """Round batches too large for the resident refine (d = 128, l = 800): the screening
+    takes groups of four and, from the second round on, keeps every row's list of the
+    centers within the bound of its D^2 in the screening pass itself; the rows it leaves
+    undecided are refined from those lists.  Every round's D^2 and idx, the candidates and
+    the weights equal the FP32 path's."""
+    X = datagen.gauss_mixture(200000, 128, 400, 100.0, seed=23)
+    Xd = _dev(X)
+    res = {}
+    for prec in ("fp32", "bf16", "fp8"):
+        g = km.KMeansPar(Xd, 400, 800.0, 4, 5, precision=prec)
+        per = []
+        for r in range(1, 5):
+            g.round(r)
+            D2, idx = g.state()
+            per.append((D2.cpu().numpy(), idx.cpu().numpy()))
+        cand, w = g.candidates()
+        res[prec] = (per, cand.cpu().numpy(), w.cpu().numpy(), g.stats())
+        g.close()
+    for prec in ("bf16", "fp8"):
+        for r, ((a1, b1), (a2, b2)) in enumerate(zip(res["fp32"][0], res[prec][0])):
+            assert np.array_equal(a1, a2) and np.array_equal(b1, b2), (prec, r + 1)
+        assert np.array_equal(res["fp32"][1], res[prec][1]) and np.array_equal(res["fp32"][2], res[prec][2])
+        st = res[prec][3]
+        assert 0 < st["screen_listed"] <= st["screen_fallback"], (prec, st)
+
+
 def test_tensor_precision_rejects_large_d(km):
     # BF16 carries d + 2 K columns, split BF16 3d + 2; three 64-column atoms are built
     X = _dev(datagen.uniform_box(200, 200, seed=1))

@@ -85,6 +85,52 @@ __device__ __forceinline__ double warp_incl_scan_f64(double v, int lane) {
     return v;
 }
 
+// Masses and their prefix sums in the grid form, as unevaluated sums of two floats
+// (hi + lo, about 48 significant bits): the products w D^2 are exact (the weight
+// split into two floats, the product's rounding error recovered with an FMA) and
+// each addition carries its rounding error (Knuth's two-sum), so a chunk's prefix is
+// within ~2^-44 of its exact value.  FP64 arithmetic runs at a small fraction of the
+// FP32 rate on this part; these sums stay on the FP32 pipes, and the picks they give
+// can differ from exact arithmetic only inside the near-tie window that flags a draw.
+struct Df {
+    float hi, lo;
+};
+__device__ __forceinline__ Df df_add(Df a, Df b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bv = __fsub_rn(s, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bv)), __fsub_rn(b.hi, bv));
+    const float t = __fadd_rn(__fadd_rn(a.lo, b.lo), err);
+    const float hi = __fadd_rn(s, t);
+    return {hi, __fsub_rn(t, __fsub_rn(hi, s))};
+}
+// the mass of a candidate: w (first draw) or w D^2, with w = wv.x + wv.y exactly
+__device__ __forceinline__ Df df_mass(float2 wv, float d2, bool first) {
+    if (first) return {wv.x, wv.y};
+    const float p = __fmul_rn(wv.x, d2);
+    const float lo = __fmaf_rn(wv.y, d2, __fmaf_rn(wv.x, d2, -p));   // (wv.x d2 - p) exactly, + wv.y d2
+    const float hi = __fadd_rn(p, lo);
+    return {hi, __fsub_rn(lo, __fsub_rn(hi, p))};
+}
+__device__ __forceinline__ Df warp_incl_scan_df(Df v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Df u = {__shfl_up_sync(0xffffffffu, v.hi, o), __shfl_up_sync(0xffffffffu, v.lo, o)};
+        if (lane >= o) v = df_add(u, v);
+    }
+    return v;
+}
+__device__ __forceinline__ double df_to_double(Df a) { return (double)a.hi + (double)a.lo; }
+
+// weights as two floats whose sum is exact (w < 2^48)
+__global__ void weight_split_kernel(const long long *__restrict__ w, const DevState *st, float2 *__restrict__ wf2) {
+    const int m = st->m;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+        const long long wj = w[j];
+        const float hi = __ll2float_rn(wj);
+        wf2[j] = make_float2(hi, __ll2float_rn(wj - __float2ll_rn(hi)));
+    }
+}
+
 // candidates (m x d, row-major) -> CT (d x mp, coordinate-major), 32 x 32 tiles
 __global__ void transpose_cand_kernel(const float *__restrict__ C, int d, const DevState *st, int mp,
                                       float *__restrict__ CT) {
@@ -179,7 +225,7 @@ __device__ __forceinline__ int last_positive(const double *v, int lo, int hi, in
 }
 
 __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
-    const float *__restrict__ C, const float *__restrict__ CT, int mp, const long long *__restrict__ w, DevState *st,
+    const float *__restrict__ C, const float *__restrict__ CT, int mp, const float2 *__restrict__ wf2, DevState *st,
     int d, int k, uint64_t seed, float *rD2buf, int32_t *chosen, float *centers, double *gchunk, int nchunk_cap,
     unsigned long long *slots, int cpc_cap, int qs, RcSync *sync, int *err, unsigned long long wait) {
     // shared: cpc_cap chunk totals, the CTA's candidates' weights (FP64) and D^2,
@@ -188,10 +234,13 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
     extern __shared__ double rsm[];
     double *ctl = rsm;
     double *wl = rsm + cpc_cap;
+    float2 *wl2 = reinterpret_cast<float2 *>(wl);   // the weights as two floats (8 bytes each)
     float *dl = reinterpret_cast<float *>(wl + (size_t)cpc_cap * 32);
     float *cnew = dl + (size_t)cpc_cap * 32;
     float *cts = cnew + ((d + 31) & ~31);
     __shared__ int s_pick, s_near, s_done, s_abort;
+    __shared__ double s_tot, s_tgt, s_preb, s_prec;   // CTA 0: the draw's total, target and prefixes
+    __shared__ int s_ob, s_nearL, s_chr;               // CTA 0: owning CTA, its fallback flag, chunk
     const int m = st->m;
     const int nchunk = (m + 31) / 32;
     const int G = gridDim.x;
@@ -204,7 +253,7 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
     const int ga = min(G, lane * qg), gb = min(G, lane * qg + qg);
     for (int ch = c0 + wid; ch < c1; ch += nwarps) {
         const int j = ch * 32 + lane;
-        wl[(ch - c0) * 32 + lane] = j < m ? (double)w[j] : 0.0;
+        wl2[(ch - c0) * 32 + lane] = j < m ? wf2[j] : make_float2(0.f, 0.f);
     }
     for (int f = threadIdx.x; f < qs * nl; f += kRcThreads) {
         const int q = f / nl, jl = f - q * nl;
@@ -225,12 +274,13 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
         for (int ch = c0 + wid - 1; wid > 0 && ch < c1; ch += nwarps - 1) {
             const int j = ch * 32 + lane;
             const int jl = (ch - c0) * 32 + lane;
-            double e = 0.0;
-            if (j < m) e = step == 0 ? wl[jl] : __dmul_rn(wl[jl], (double)dl[jl]);
-            const double incl = warp_incl_scan_f64(e, lane);
+            Df e = {0.f, 0.f};
+            if (j < m) e = df_mass(wl2[jl], dl[jl], step == 0);
+            const Df incl = warp_incl_scan_df(e, lane);
             if (lane == 31) {
-                ctl[ch - c0] = incl;
-                gch[ch] = incl;
+                const double tot = df_to_double(incl);
+                ctl[ch - c0] = tot;
+                gch[ch] = tot;
             }
         }
         __threadfence();   // every thread's chunk totals (and last draw's D^2) before the flag
@@ -251,7 +301,13 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
         // word; the other CTAs (one lane) poll that word.  One CTA reads the published
         // totals and the owning chunk: no contention of G CTAs on the same lines.
         unsigned long long *pw = slots + 2 * (size_t)G + (step & 1);
-        if (wid == 0 && b == 0) {
+        // With at most one owned chunk per worker warp, CTA 0's worker warps fetch the
+        // owning CTA's masses (one chunk each, one round trip) while warp 0 waits, and
+        // the chunk and candidate are found from them; otherwise warp 0 reads the
+        // owner's published chunk totals and then the chunk's masses.
+        const bool par = cpc <= nwarps - 1;
+        if (b == 0) {
+        if (wid == 0) {
             unsigned long long gw[kRcLaneWords];
             int ok = 1;
             const unsigned long long t0 = clock64();
@@ -325,14 +381,18 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
                     pre_b = 0.0;
                     near = 1;
                 }
+                if (par) {
+                    if (lane == 0) { s_tgt = target; s_preb = pre_b; s_ob = ob; s_nearL = near; }
+                } else {
                 const int oc0 = min(nchunk, ob * cpc), oc1 = min(nchunk, oc0 + cpc);
                 int ch = near ? -1 : prefix_find_reg(gch, oc0, oc1, pre_b, target, lane, &before, nullptr);
                 double pre_c = before;
                 if (ch < 0) { ch = last_positive(gch, oc0, oc1, lane); near = 1; }
                 const int j = ch * 32 + lane;
-                double e = 0.0;
-                if (j < m) e = step == 0 ? (double)w[j] : __dmul_rn((double)w[j], (double)__ldcg(rD2prev + j));
-                const double incl = warp_incl_scan_f64(e, lane);
+                Df ef = {0.f, 0.f};
+                if (j < m) ef = df_mass(wf2[j], __ldcg(rD2prev + j), step == 0);
+                const Df inclf = warp_incl_scan_df(ef, lane);
+                const double e = df_to_double(ef), incl = df_to_double(inclf);
                 const unsigned pos = __ballot_sync(0xffffffffu, j < m && e > 0.0);
                 if (!near) {
                     const double cum = pre_c + incl, cum0 = pre_c + (incl - e);
@@ -347,17 +407,93 @@ __global__ void __launch_bounds__(kRcThreads, 1) recluster_kernel(
                     }
                 }
                 if (pick < 0) pick = ch * 32 + 31 - __clz(pos);   // last positive mass of the chunk
+                }
             }
             if (lane == 0) {
-                s_pick = pick;
-                s_near = near;
+                s_tot = total;
                 s_done = !(total > 0.0);
                 s_abort = !ok;
-                if (ok)
-                    *reinterpret_cast<volatile unsigned long long *>(pw) =
-                        ((unsigned long long)(uint32_t)max(pick, 0) << 32) | ((unsigned long long)near << 8) |
-                        ((unsigned long long)(total > 0.0 ? 0 : 1) << 9) | tag;
+                // the pick is published here unless the worker warps take part in it
+                if (!par || !(total > 0.0) || !ok) {
+                    s_pick = pick;
+                    s_near = near;
+                    if (ok)
+                        *reinterpret_cast<volatile unsigned long long *>(pw) =
+                            ((unsigned long long)(uint32_t)max(pick, 0) << 32) | ((unsigned long long)near << 8) |
+                            ((unsigned long long)(total > 0.0 ? 0 : 1) << 9) | tag;
+                }
             }
+        }
+        if (par) {
+            __syncthreads();
+            const bool go = !s_abort && s_tot > 0.0;
+            const int ob = go ? s_ob : 0;
+            const int oc0 = min(nchunk, ob * cpc), oc1 = min(nchunk, oc0 + cpc);
+            // worker warp w: the masses of the owner's chunk oc0 + w - 1 and their scan
+            // (the same FP64 products and association as the owner's own scan)
+            const int chw = oc0 + wid - 1;
+            const int jw = chw * 32 + lane;
+            double e = 0.0, incl = 0.0;
+            if (go && wid > 0 && chw < oc1) {
+                Df ef = {0.f, 0.f};
+                if (jw < m) ef = df_mass(wf2[jw], __ldcg(rD2prev + jw), step == 0);
+                const Df inclf = warp_incl_scan_df(ef, lane);
+                incl = df_to_double(inclf);
+                e = df_to_double(ef);
+                if (lane == 31) ctl[wid - 1] = incl;
+            }
+            __syncthreads();
+            if (go && wid == 0) {
+                // the chunk: a fixed-order prefix over the owner's chunk totals from the
+                // prefix before the owner (as the search over published chunk totals)
+                const int cnt = oc1 - oc0;
+                const double val = lane < cnt ? ctl[lane] : 0.0;
+                const double vin = warp_incl_scan_f64(val, lane);
+                double ex = __shfl_up_sync(0xffffffffu, vin, 1);
+                if (lane == 0) ex = 0.0;
+                const double pre = s_preb + ex;
+                const double run = pre + val;
+                int nearc = s_nearL;
+                const unsigned hitm = nearc ? 0u : __ballot_sync(0xffffffffu, lane < cnt && run > s_tgt);
+                int chr;
+                double prec = 0.0;
+                if (hitm) {
+                    chr = __ffs(hitm) - 1;
+                    prec = __shfl_sync(0xffffffffu, pre, chr);
+                } else {   // the last chunk with mass
+                    const unsigned posm = __ballot_sync(0xffffffffu, lane < cnt && val > 0.0);
+                    chr = posm ? 31 - __clz(posm) : 0;
+                    nearc = 1;
+                }
+                if (lane == 0) { s_chr = chr; s_prec = prec; s_nearL = nearc; }
+            }
+            __syncthreads();
+            if (go && wid == s_chr + 1) {
+                // the candidate, from this warp's masses
+                const double target = s_tgt, total = s_tot, pre_c = s_prec;
+                int near = s_nearL, pick = -1;
+                const unsigned pos = __ballot_sync(0xffffffffu, jw < m && e > 0.0);
+                if (!near) {
+                    const double cum = pre_c + incl, cum0 = pre_c + (incl - e);
+                    const unsigned hit = __ballot_sync(0xffffffffu, jw < m && cum > target);
+                    if (hit) {
+                        const int hl = __ffs(hit) - 1;
+                        pick = chw * 32 + hl;
+                        const int nr = fabs(target - cum0) <= 1e-6 * total || fabs(cum - target) <= 1e-6 * total;
+                        near = __shfl_sync(0xffffffffu, nr, hl);
+                    } else {
+                        near = 1;
+                    }
+                }
+                if (pick < 0) pick = chw * 32 + 31 - __clz(pos);   // last positive mass of the chunk
+                if (lane == 0) {
+                    s_pick = pick;
+                    s_near = near;
+                    *reinterpret_cast<volatile unsigned long long *>(pw) =
+                        ((unsigned long long)(uint32_t)pick << 32) | ((unsigned long long)near << 8) | tag;
+                }
+            }
+        }
         } else if (wid == 0 && lane == 0) {
             int ok = 1;
             unsigned long long v;
@@ -785,7 +921,8 @@ size_t recluster_grid_floats(const Ctx &c) {
     const char *force_grid = std::getenv("KMPAR_RECLUSTER_GRID");
     const bool grid_only = force_grid && force_grid[0] == '1';
     if (!grid_only && cluster_plan(c, &cpc, &rows)) return 0;
-    return (size_t)((c.cap_total + 31) / 32) * 32 * c.d;
+    // the transposed candidates (d x mp) and the weights split into two floats (mp float2)
+    return (size_t)((c.cap_total + 31) / 32) * 32 * (c.d + 2);
 }
 
 cudaError_t launch_recluster(Ctx &c, float *centers) {
@@ -828,7 +965,12 @@ cudaError_t launch_recluster(Ctx &c, float *centers) {
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     const float *Cp = c.C;
     const float *CTp = c.rCT;
-    const long long *wp = c.w;
+    // weights as two floats each, after the transposed candidates
+    const float2 *wp = reinterpret_cast<const float2 *>(c.rCT + (size_t)c.d * mp);
+    weight_split_kernel<<<std::max(1, std::min(c.num_sms * 4, (mp + 255) / 256)), 256, 0, c.stream>>>(
+        c.w, c.st, const_cast<float2 *>(wp));
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     DevState *stp = c.st;
     int d = c.d, k = c.k, mpv = mp, ncap = nchunk_cap, cpcv = cpc_cap, qsv = qs;
     uint64_t seed = c.seed;

@@ -222,6 +222,24 @@ template <bool NE>
 __device__ __forceinline__ float screened(uint32_t raw, float f, float nc) {
     return NE ? __fmaf_rn(__uint_as_float(raw), f, nc) : __uint_as_float(raw);
 }
+// two adjacent columns at once: with norms in the epilogue one packed FP32x2 FMA
+// (each half rounded like the scalar FMA, so the values are the same)
+template <bool NE>
+__device__ __forceinline__ void screened2(uint32_t r0, uint32_t r1, float f, float n0, float n1, float &v0,
+                                          float &v1) {
+    if (!NE) {
+        v0 = __uint_as_float(r0);
+        v1 = __uint_as_float(r1);
+        return;
+    }
+    uint64_t d;
+    asm("{\n\t.reg .b64 ta, tb, tc;\n\tmov.b64 ta, {%1, %2};\n\tmov.b64 tb, {%3, %3};\n\tmov.b64 tc, {%4, %5};\n\t"
+        "fma.rn.f32x2 %0, ta, tb, tc;\n\t}"
+        : "=l"(d)
+        : "r"(r0), "r"(r1), "r"(__float_as_uint(f)), "r"(__float_as_uint(n0)), "r"(__float_as_uint(n1)));
+    v0 = __uint_as_float((uint32_t)d);
+    v1 = __uint_as_float((uint32_t)(d >> 32));
+}
 
 // GS: centers per screened group (2: pairs; 4: groups of four adjacent centers,
 // whose minimum costs fewer ALU operations per value; the refine then computes all
@@ -449,7 +467,8 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
                                 }
                                 float v[8];
 #pragma unroll
-                                for (int u = 0; u < 8; ++u) v[u] = screened<NE>(r[cc][q + u], f, nv[u]);
+                                for (int u = 0; u < 8; u += 2)
+                                    screened2<NE>(r[cc][q + u], r[cc][q + u + 1], f, nv[u], nv[u + 1], v[u], v[u + 1]);
                                 if (GS == 4) {
                                     // two groups of four: minimum, key, one top-2 insertion
                                     const uint32_t gc = (uint32_t)(((c + cc) * 32 + q) >> 2);
@@ -503,10 +522,8 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
                             for (int q = 0; q < 32; q += 4) {
                                 float4 n4 = make_float4(0.f, 0.f, 0.f, 0.f);
                                 if (NE) n4 = *reinterpret_cast<const float4 *>(nct + (c + cc) * 32 + q);
-                                v[q] = screened<NE>(r[cc][q], f, n4.x);
-                                v[q + 1] = screened<NE>(r[cc][q + 1], f, n4.y);
-                                v[q + 2] = screened<NE>(r[cc][q + 2], f, n4.z);
-                                v[q + 3] = screened<NE>(r[cc][q + 3], f, n4.w);
+                                screened2<NE>(r[cc][q], r[cc][q + 1], f, n4.x, n4.y, v[q], v[q + 1]);
+                                screened2<NE>(r[cc][q + 2], r[cc][q + 3], f, n4.z, n4.w, v[q + 2], v[q + 3]);
                             }
                             float m4[4];
 #pragma unroll

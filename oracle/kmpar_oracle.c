@@ -14,6 +14,8 @@
  *   - Algorithm 2 (k-means||) steps 1-2 (init), 4-5 (rounds),
  *     7 (weights), 8 (recluster with k-means++, Sec. 4.2)       Sec. 3.3
  *   - Algorithm 1 (k-means++), in its weighted form, for step 8 Sec. 3.1
+ *     (one draw at a time, or the same law drawn in batches by rejection
+ *     from a stale D^2 snapshot)                                Sec. 3.1
  *   - the exactly-l-per-round variant of step 4                  Sec. 5.3
  *   - Lloyd's iteration                                         Sec. 1, Sec. 3.1
  *   - Lloyd's iteration on the weighted candidates (the alternative
@@ -53,6 +55,7 @@
 #define ORC_TAG_SAMPLE 2u
 #define ORC_TAG_RECLUSTER 3u
 #define ORC_TAG_EXACT 4u
+#define ORC_TAG_RECLUSTER_RS 5u
 
 /* ---------------------------------------------------------------------------
  * Philox4x32-10 (SC'11).  Each of the ten rounds multiplies the even words by the
@@ -359,6 +362,146 @@ int orc_recluster(const double *cand, const int64_t *w, int64_t m, int d, int64_
         }
     }
     free(D2);
+    return warn;
+}
+
+/* squared distance between two FP64 candidate rows, in ascending coordinates */
+static double orc_dist2_dd(const double *x, const double *y, int d) {
+    double s = 0.0;
+    for (int q = 0; q < d; ++q) {
+        double t = x[q] - y[q];
+        s = s + t * t;
+    }
+    return s;
+}
+
+/* ---------------------------------------------------------------------------
+ * Algorithm 2, step 8 with k-means++ (Sec. 4.2), weighted (Alg. 1 with
+ * multiplicities w), the draws after the first taken in batches by rejection from
+ * a stale snapshot of D^2.  The law of the chosen sequence is the one of
+ * orc_recluster: every draw t >= 1 picks j with probability
+ * w_j D^2(j) / sum_j w_j D^2(j), D^2 to all centers drawn before it.
+ *
+ *   draw 0: as in orc_recluster (u from counter (0, 0, RECLUSTER), mass w_j).
+ *   then, until k centers: a snapshot S = D^2 fixes the masses e_j = w_j S_j
+ *   (prefix sums in ascending j, FP64) and 2B proposals i = 0..2B-1 are drawn from
+ *   them, proposal i with u from counter (p + i, 0, RS) and the inverse-CDF rule of
+ *   orc_recluster.  In proposal order, proposal j is accepted as the next center
+ *   iff v S_j < D(j), v from counter (p + i, 1, RS) and D(j) = the smaller of S_j
+ *   and the distances from j to the centers accepted since the snapshot: a
+ *   proposal is made with probability w_j S_j / sum e and kept with probability
+ *   D(j) / S_j, so the kept j has probability proportional to w_j D(j).  The
+ *   snapshot ends after 2B proposals, B acceptances or at k; D^2 then takes the
+ *   new centers and the next snapshot starts at counter p + 2B.
+ *
+ * near[t] flags draw t when a proposal examined for it (since the previous
+ * acceptance) had its target within 1e-6 of the snapshot total of a prefix
+ * boundary, or v S_j within 1e-4 S_j of D(j) (the FP32 distances of a GPU path
+ * can differ from these by up to ~(d + 2) 2^-24 relative).  *snapshots receives
+ * the number of snapshots.  Returns 1 if the positive mass ran out before k
+ * draws (the remaining draws repeat chosen[0]), else 0.
+ * ------------------------------------------------------------------------- */
+int orc_recluster_rejection(const double *cand, const int64_t *w, int64_t m, int d, int64_t k, int64_t B,
+                            uint64_t seed, int64_t *chosen, int8_t *near, int64_t *snapshots) {
+    if (snapshots) *snapshots = 0;
+    if (k <= 0) return 0;
+    const int64_t P = 2 * B;
+    double *D2 = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    double *S = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    double *prefix = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    int64_t *prop = (int64_t *)malloc(sizeof(int64_t) * (size_t)P);
+    int8_t *pnear = (int8_t *)malloc((size_t)P);
+    int warn = 0;
+
+    /* draw 0, proportional to w */
+    double wtot = 0.0;
+    for (int64_t j = 0; j < m; ++j) wtot = wtot + (double)w[j];
+    if (!(wtot > 0.0)) {
+        for (int64_t s = 0; s < k; ++s) { chosen[s] = 0; if (near) near[s] = 0; }
+        free(D2); free(S); free(prefix); free(prop); free(pnear);
+        return 1;
+    }
+    {
+        double u = orc_uniform(0, 0, ORC_TAG_RECLUSTER, seed);
+        double target = u * wtot, pre = 0.0;
+        int64_t pick = -1, last_pos = -1;
+        int8_t nt = 0;
+        for (int64_t j = 0; j < m; ++j) {
+            double before = pre;
+            pre = pre + (double)w[j];
+            if (w[j] > 0) last_pos = j;
+            if (pick < 0 && pre > target) {
+                pick = j;
+                if (fabs(target - before) <= 1e-6 * wtot || fabs(pre - target) <= 1e-6 * wtot) nt = 1;
+            }
+        }
+        if (pick < 0) { pick = last_pos; nt = 1; }
+        chosen[0] = pick;
+        if (near) near[0] = nt;
+        for (int64_t j = 0; j < m; ++j) D2[j] = orc_dist2_dd(cand + j * (int64_t)d, cand + pick * (int64_t)d, d);
+    }
+
+    int64_t t = 1;
+    uint64_t p = 0;
+    int8_t pending = 0;
+    while (t < k) {
+        double total = 0.0;
+        for (int64_t j = 0; j < m; ++j) {
+            S[j] = D2[j];
+            total = total + (double)w[j] * S[j];
+            prefix[j] = total;
+        }
+        if (!(total > 0.0)) {
+            for (int64_t s = t; s < k; ++s) { chosen[s] = chosen[0]; if (near) near[s] = 0; }
+            warn = 1;
+            break;
+        }
+        if (snapshots) *snapshots += 1;
+        for (int64_t i = 0; i < P; ++i) {
+            double u = orc_uniform(p + (uint64_t)i, 0, ORC_TAG_RECLUSTER_RS, seed);
+            double target = u * total;
+            int64_t pick = -1, last_pos = -1;
+            int8_t nt = 0;
+            for (int64_t j = 0; j < m; ++j) {
+                double e = (double)w[j] * S[j];
+                double before = j > 0 ? prefix[j - 1] : 0.0;
+                if (e > 0.0) last_pos = j;
+                if (pick < 0 && prefix[j] > target) {
+                    pick = j;
+                    if (fabs(target - before) <= 1e-6 * total || fabs(prefix[j] - target) <= 1e-6 * total) nt = 1;
+                }
+            }
+            if (pick < 0) { pick = last_pos; nt = 1; }
+            prop[i] = pick;
+            pnear[i] = nt;
+        }
+        const int64_t first_new = t;
+        for (int64_t i = 0; i < P && t < k && t - first_new < B; ++i) {
+            const int64_t j = prop[i];
+            double dj = S[j];
+            for (int64_t a = first_new; a < t; ++a) {
+                double s = orc_dist2_dd(cand + j * (int64_t)d, cand + chosen[a] * (int64_t)d, d);
+                if (s < dj) dj = s;
+            }
+            double v = orc_uniform(p + (uint64_t)i, 1, ORC_TAG_RECLUSTER_RS, seed);
+            double lhs = v * S[j];
+            pending |= pnear[i];
+            if (fabs(lhs - dj) <= 1e-4 * S[j]) pending = 1;
+            if (lhs < dj) {
+                chosen[t] = j;
+                if (near) near[t] = pending;
+                pending = 0;
+                ++t;
+            }
+        }
+        p += (uint64_t)P;
+        for (int64_t a = first_new; a < t; ++a)
+            for (int64_t j = 0; j < m; ++j) {
+                double s = orc_dist2_dd(cand + j * (int64_t)d, cand + chosen[a] * (int64_t)d, d);
+                if (s < D2[j]) D2[j] = s;
+            }
+    }
+    free(D2); free(S); free(prefix); free(prop); free(pnear);
     return warn;
 }
 

@@ -63,6 +63,7 @@ def _load():
         "orc_update": (f64, [P, i64, i32, P, i64, i64, P, P, P]),
         "orc_weights": (None, [P, i64, i64, P]),
         "orc_recluster": (i32, [P, P, i64, i32, i64, u64, P, P]),
+        "orc_recluster_rejection": (i32, [P, P, i64, i32, i64, i64, u64, P, P, P]),
         "orc_lloyd": (i64, [P, i64, i32, P, i64, i64, P, P, P, P]),
         "orc_weighted_lloyd": (i64, [P, P, i64, i32, P, i64, i64, P, P]),
     }
@@ -188,6 +189,21 @@ def recluster(cand, w, k: int, seed: int):
     return chosen, near.astype(bool), bool(warn)
 
 
+def recluster_rejection(cand, w, k: int, seed: int, batch: int):
+    """Algorithm 2 step 8, the same weighted k-means++ law drawn in batches: up to
+    `batch` draws per D^2 snapshot, from 2 batch proposals accepted by rejection.
+    Returns (chosen, near, warn, snapshots)."""
+    cand = np.ascontiguousarray(cand, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.int64)
+    m, d = cand.shape
+    chosen = np.empty(k, np.int64)
+    near = np.empty(k, np.int8)
+    snaps = ctypes.c_int64(0)
+    warn = _load().orc_recluster_rejection(_p(cand), _p(w), m, d, k, batch, seed, _p(chosen), _p(near),
+                                           ctypes.byref(snaps))
+    return chosen, near.astype(bool), bool(warn), int(snaps.value)
+
+
 def lloyd(X, C, max_iter: int):
     """Lloyd's iteration from centers C (FP64 copy); returns the final state."""
     X = _f32(X)
@@ -247,10 +263,11 @@ def weighted_lloyd(cand_rows, w, C, max_iter: int):
 
 
 def kmeans_par(X, k: int, ell: float, rounds: int, seed: int, sampling: str = "bernoulli",
-               w: float = 0.0) -> KMeansParResult:
+               w: float = 0.0, recluster_batch: int = 0) -> KMeansParResult:
     """Algorithm 2 steps 1-8, with per-round snapshots.  sampling="exact" draws
     exactly floor(l) points per round without replacement (Sec. 5.3); w is the
-    relative window of its boundary flag."""
+    relative window of its boundary flag.  recluster_batch > 0 draws step 8 in
+    batches of that size by rejection (recluster_rejection), else one at a time."""
     X = _f32(X)
     n = X.shape[0]
     i0 = init_index(n, seed)
@@ -271,14 +288,19 @@ def kmeans_par(X, k: int, ell: float, rounds: int, seed: int, sampling: str = "b
     res.D2, res.idx = D2, idx
     res.w = weights(idx, len(cand))
     candX = X[res.cand].astype(np.float64)
-    res.chosen, res.recluster_near, res.recluster_warn = recluster(candX, res.w, k, seed)
+    if recluster_batch > 0:
+        res.chosen, res.recluster_near, res.recluster_warn, _ = recluster_rejection(candX, res.w, k, seed,
+                                                                                    recluster_batch)
+    else:
+        res.chosen, res.recluster_near, res.recluster_warn = recluster(candX, res.w, k, seed)
     res.seed_centers = candX[res.chosen]
     res.seed_cost = cost(X, res.seed_centers)
     return res
 
 
-def fit(X, k: int, ell: float, rounds: int, seed: int, max_iter: int, sampling: str = "bernoulli"):
+def fit(X, k: int, ell: float, rounds: int, seed: int, max_iter: int, sampling: str = "bernoulli",
+        recluster_batch: int = 0):
     """k-means|| seeding followed by Lloyd's iteration."""
-    par = kmeans_par(X, k, ell, rounds, seed, sampling)
+    par = kmeans_par(X, k, ell, rounds, seed, sampling, recluster_batch=recluster_batch)
     C, labels, it, fc, hist, near = lloyd(X, par.seed_centers, max_iter)
     return par, dict(centers=C, labels=labels, iters=it, final_cost=fc, cost_hist=hist, near=near)

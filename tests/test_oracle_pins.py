@@ -314,6 +314,73 @@ def test_recluster_distinct_and_covering(orc):
     assert sorted(ch.tolist()) == list(range(9)) and not warn
 
 
+def _kmpp_law3(cand, w):
+    """Exact law of the first three weighted k-means++ draws (Alg. 1 with
+    multiplicities): P(a) = w_a / W, P(b | a) = w_b D^2(b, a) / sum_j w_j D^2(j, a),
+    P(c | a, b) = w_c min(D^2(c, a), D^2(c, b)) / sum_j w_j min(...)."""
+    m = len(w)
+    D = cdist(cand, cand, "sqeuclidean")
+    P = np.zeros((m, m, m))
+    for a in range(m):
+        e1 = w * D[:, a]
+        for b in range(m):
+            if e1[b] == 0:
+                continue
+            e2 = w * np.minimum(D[:, a], D[:, b])
+            P[a, b] = (w[a] / w.sum()) * (e1[b] / e1.sum()) * e2 / e2.sum()
+    return P
+
+
+@pytest.mark.parametrize("batch", [1, 2, 5])
+def test_recluster_rejection_joint_law(orc, batch):
+    # batch 1: one draw per snapshot (the snapshot refresh carries the law);
+    # batch >= 2: draws 1 and 2 come from the same snapshot, the second kept with
+    # probability D^2 / S after the first is accepted (the rejection step)
+    cand = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 3.0], [4.0, 4.0], [1.0, 1.0]])
+    w = np.array([5, 1, 2, 0, 3], np.int64)
+    P = _kmpp_law3(cand, w)
+    trials = 30000
+    obs = np.zeros_like(P)
+    snaps = 0
+    for s in range(trials):
+        ch, _, warn, ns = orc.recluster_rejection(cand, w, 3, seed=s, batch=batch)
+        assert not warn
+        obs[ch[0], ch[1], ch[2]] += 1
+        snaps += ns
+    assert obs[P == 0].sum() == 0                      # w = 0 or D^2 = 0 is never drawn
+    mask = P > 0
+    assert stats.chisquare(obs[mask], P[mask] * trials).pvalue > 1e-4
+    # draws 1..2 need ceil(2 / batch) snapshots, more when a batch's proposals run out
+    assert snaps >= trials * -(-2 // batch)
+
+
+def test_recluster_rejection_first_draw_is_the_sequential_one(orc):
+    # draw 0 uses the same counter and rule as the one-at-a-time form
+    rng = np.random.default_rng(8)
+    cand = rng.normal(size=(40, 3))
+    w = rng.integers(0, 5, size=40).astype(np.int64)
+    for s in range(50):
+        a, _, _ = orc.recluster(cand, w, 1, seed=s)
+        b, _, _, _ = orc.recluster_rejection(cand, w, 1, seed=s, batch=4)
+        assert a[0] == b[0]
+
+
+@pytest.mark.parametrize("batch", [1, 3, 16])
+def test_recluster_rejection_distinct_and_covering(orc, batch):
+    # k = m distinct candidates with weight: each is drawn once, whatever the batch
+    cand = np.random.default_rng(5).normal(size=(9, 3))
+    ch, _, warn, _ = orc.recluster_rejection(cand, np.arange(1, 10, dtype=np.int64), 9, seed=2, batch=batch)
+    assert sorted(ch.tolist()) == list(range(9)) and not warn
+
+
+def test_recluster_rejection_runs_out_of_mass(orc):
+    # two distinct candidates, k = 4: after both are drawn the mass is zero
+    cand = np.array([[0.0, 0.0], [0.0, 0.0], [2.0, 0.0]])
+    ch, _, warn, _ = orc.recluster_rejection(cand, np.array([1, 1, 1], np.int64), 4, seed=3, batch=2)
+    assert warn and ch[2] == ch[0] and ch[3] == ch[0]
+    assert 2 in ch[:2] and len({0, 1} & set(ch[:2].tolist())) == 1
+
+
 # ----------------------------------------------------------------- Theorem 2 / Corollary 3
 def _theorem2_setup(seed):
     rng = np.random.default_rng(seed)

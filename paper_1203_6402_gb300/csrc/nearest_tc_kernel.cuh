@@ -127,6 +127,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// the same wait, with the loaded registers as operands: no use of them can be
+// scheduled before it
+__device__ __forceinline__ void tmem_wait_ld_dep(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+          "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+          "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+          "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+        :: "memory");
+}
 // asynchronous global -> shared copies of 16 and 4 bytes (one commit group per call site)
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
@@ -437,18 +447,28 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
 #pragma unroll
                 for (int c = 0; c < C::CHUNKS; c += 2) {
                     uint32_t r[2][32];
+                    // the second chunk's load is in flight while the first chunk is
+                    // reduced; once the warp's columns are all in registers the
+                    // accumulator buffer goes back to the MMA warp, so the next tile's
+                    // MMAs overlap this warp's remaining work
                     tmem_ld32(tbase + c * 32, r[0]);
-                    if (c + 1 < C::CHUNKS) tmem_ld32(tbase + (c + 1) * 32, r[1]);
-                    tmem_wait_ld();
-                    // the warp's columns are in registers: the accumulator buffer goes
-                    // back to the MMA warp now, so the next tile's MMAs overlap this
-                    // warp's work on these values
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&sm.acc_empty[buf]);
+                    tmem_wait_ld_dep(r[0]);
+                    if (c + 1 < C::CHUNKS) {
+                        tmem_ld32(tbase + (c + 1) * 32, r[1]);
+                    } else {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&sm.acc_empty[buf]);
+                    }
 #pragma unroll
                     for (int cc = 0; cc < 2; ++cc) {
                         if (c + cc >= C::CHUNKS) break;
+                        if (cc == 1) {
+                            tmem_wait_ld_dep(r[1]);
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&sm.acc_empty[buf]);
+                        }
                         if (PAIR) {
 #pragma unroll
                             for (int q = 0; q < 32; q += 8) {

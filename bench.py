@@ -137,13 +137,15 @@ def _phase_events(torch, stream, names):
     return ev
 
 
-def run_step(km, torch, X, k, ell, rounds, seed, prec, stream, sampling, max_iter, timing=False, phases=None):
+def run_step(km, torch, X, k, ell, rounds, seed, prec, stream, sampling, max_iter, timing=False, phases=None,
+             recluster_batch=0):
     """One pass of the whole path through the C ABI; returns (stats, lloyd output)."""
     def mark(nm, i):
         if phases is not None:
             phases[nm][i].record(stream)
     mark("init", 0)
-    g = km.KMeansPar(X, k, ell, rounds, seed=seed, precision=prec, stream=stream, sampling=sampling)
+    g = km.KMeansPar(X, k, ell, rounds, seed=seed, precision=prec, stream=stream, sampling=sampling,
+                     recluster_batch=recluster_batch)
     if timing:
         km.kmpar_set_timing(g.ctx, True)
     mark("init", 1)
@@ -334,7 +336,8 @@ def run_ours(args, rank, world):
     seed = 7 + rank
 
     def step(timing=False, phases=None, precision=prec):
-        return run_step(km, torch, X, k, ell, rounds, seed, precision, stream, args.sampling, max_iter, timing, phases)
+        return run_step(km, torch, X, k, ell, rounds, seed, precision, stream, args.sampling, max_iter, timing, phases,
+                        args.recluster_batch)
 
     for _ in range(args.warmup):
         step()
@@ -377,7 +380,7 @@ def run_ours(args, rank, world):
 
     # end to end through the public API with host buffers (pinned), copies inside the timer
     Xpin = torch.from_numpy(Xh).pin_memory()
-    fit_flags = km.KMPAR_EXACT_SAMPLING if args.sampling == "exact" else 0
+    fit_flags = (km.KMPAR_EXACT_SAMPLING if args.sampling == "exact" else 0) | (args.recluster_batch << 16)
     Cpin = torch.empty(k, d, dtype=torch.float32).pin_memory()
     Lpin = torch.empty(n, dtype=torch.int32).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
@@ -478,6 +481,7 @@ def run_ours(args, rank, world):
         "config": {"workload": (f"{args.workload}: n={n} d={d} k={k} l={ell:g} r={rounds}, "
                                 f"Lloyd until no label changes, capped at {max_iter} updates"),
                    "precision": args.precision, "sampling": args.sampling,
+                   "recluster_batch": args.recluster_batch,
                    "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 (X {n * d * 4 / 1e6:.0f} MB > 129 MB)"},
         "init_lloyd_s": ms_max / args.steps / 1e3,
@@ -491,7 +495,7 @@ def run_ours(args, rank, world):
         "roofline": roofline, "clocks": clocks,
         "refine": {key: st_t[key] for key in ("sample_near", "sample_refined", "argmin_fp64", "argmin_wide",
                                              "screen_rows", "screen_fallback", "screen_exact",
-                                             "recluster_near")},
+                                             "recluster_near", "recluster_snapshots")},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args)
@@ -539,7 +543,7 @@ def oracle_sample(args):
 
 def _oracle_job(argv):
     """Runs in a child process: one oracle pass of the sample; (seconds, dist-evals, info)."""
-    root, wname, smp, data_seed, run_seed, sampling = argv
+    root, wname, smp, data_seed, run_seed, sampling, rbatch = argv
     if root not in sys.path:
         sys.path.insert(0, root)
     from oracle import oracle
@@ -550,7 +554,8 @@ def _oracle_job(argv):
     else:
         Xs = datagen.kdd_like(smp["n"], data_seed)
     t0 = time.perf_counter()
-    par = oracle.kmeans_par(Xs, smp["k"], smp["ell"], smp["rounds"], seed=run_seed, sampling=sampling)
+    par = oracle.kmeans_par(Xs, smp["k"], smp["ell"], smp["rounds"], seed=run_seed, sampling=sampling,
+                            recluster_batch=rbatch)
     _, _, it, _, _, _ = oracle.lloyd(Xs, par.seed_centers, smp["lloyd"])
     dt = time.perf_counter() - t0
     n_s, k_s = smp["n"], smp["k"]
@@ -615,14 +620,15 @@ def cpu_baseline(args):
     from oracle import oracle
     oracle.build()
     smp = oracle_sample(args)
-    dt, evals, info = _oracle_job((ROOT, args.workload, smp, 1000, 7, args.sampling))
+    dt, evals, info = _oracle_job((ROOT, args.workload, smp, 1000, 7, args.sampling, args.recluster_batch))
     res = {"value": evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": dt,
            "sample": _sample_text(args, smp, "1 thread") + f" ({info['lloyd_iters']} updates made, "
                                                           f"{info['candidates']} candidates)"}
     cores = os.cpu_count() or 1
     if cores > 1 and not args.no_cpu_all_cores:
         ctx = mp.get_context("spawn")
-        jobs = [(ROOT, args.workload, smp, 1000 + j, 7 + j, args.sampling) for j in range(cores)]
+        jobs = [(ROOT, args.workload, smp, 1000 + j, 7 + j, args.sampling, args.recluster_batch)
+                for j in range(cores)]
         t0 = time.perf_counter()
         with ctx.Pool(cores) as pool:
             outs = pool.map(_oracle_job, jobs)
@@ -656,10 +662,10 @@ def run_reference(args, rank, world):
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     smp = oracle_sample(argparse.Namespace(**{**vars(args), "cpu_sample_n": args.ref_sample_n}))
     for _ in range(args.warmup):
-        _oracle_job((ROOT, args.workload, smp, 1000, 7, args.sampling))
+        _oracle_job((ROOT, args.workload, smp, 1000, 7, args.sampling, args.recluster_batch))
     tot_t, tot_e = 0.0, 0
     for _ in range(args.steps):
-        dt, e, _ = _oracle_job((ROOT, args.workload, smp, 1000, 7, args.sampling))
+        dt, e, _ = _oracle_job((ROOT, args.workload, smp, 1000, 7, args.sampling, args.recluster_batch))
         tot_t += dt
         tot_e += e
     value = tot_e / tot_t
@@ -669,7 +675,7 @@ def run_reference(args, rank, world):
         "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{args.workload} (bounded sample)", "precision": "fp64",
-                   "sampling": args.sampling},
+                   "sampling": args.sampling, "recluster_batch": args.recluster_batch},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -716,6 +722,8 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3", "fp8"],
                     help="screening arithmetic (default: the fastest one built for the workload's d)")
     ap.add_argument("--workload", default="gmm_n10M_d128_k10000")
+    ap.add_argument("--recluster-batch", type=int, default=64,
+                    help="step 8: draws per D^2 snapshot (batched rejection form); 0: one draw at a time")
     ap.add_argument("--sampling", default="bernoulli", choices=["bernoulli", "exact"],
                     help="round draws: independent (Alg. 2 step 4) or exactly l per round (Sec. 5.3)")
     ap.add_argument("--n", type=int, default=0, help="override n (same recipe)")

@@ -116,6 +116,7 @@ typedef struct {
     int64_t screen_listed;        /* undecided rows of round passes that went to the
                                      exact refine over the lists the screening pass
                                      itself kept (the others took the list pass)     */
+    int64_t recluster_snapshots;  /* batched reclustering: D^2 snapshots taken       */
 } kmpar_stats;
 
 /*
@@ -241,7 +242,8 @@ KMPAR_API kmpar_status kmpar_cost_noalloc(const float *X, int64_t n, int32_t d, 
  * (copied in and out inside the call); otherwise device pointers.
  * flags & KMPAR_EXACT_SAMPLING: exactly floor(l) draws per round (see
  * kmpar_set_sampling).  (flags >> 8) & 255: updates of kmpar_weighted_lloyd on
- * the candidates after the reclustering (0: none, the default).  seed_cost, final_cost and iters are host pointers
+ * the candidates after the reclustering (0: none, the default).  (flags >> 16) &
+ * 255: the reclustering batch of kmpar_set_recluster (0: one draw at a time).  seed_cost, final_cost and iters are host pointers
  * (nullable).  labels_out is nullable.
  */
 #define KMPAR_HOST_BUFFERS 1
@@ -326,6 +328,24 @@ KMPAR_API kmpar_status kmpar_batch_run(const float *X, const kmpar_problem *prob
 #define KMPAR_SAMPLE_BERNOULLI 0
 #define KMPAR_SAMPLE_EXACT 1
 KMPAR_API kmpar_status kmpar_set_sampling(kmpar_ctx *ctx, int32_t mode);
+
+/*
+ * How kmpar_recluster draws the weighted k-means++ sequence (Alg. 2 step 8,
+ * Alg. 1 with multiplicities, Sec. 4.2).  batch = 0 (the default): one draw at a
+ * time, draw t with u from counter (t, 0, 0, 3) and the inverse CDF of the
+ * masses w_j D^2(j) in ascending j.  batch = B in 1..64: the same law drawn in
+ * batches: draw 0 as above; then each snapshot S of D^2 fixes the masses
+ * w_j S_j, 2B proposals are drawn from them (proposal i with u from counter
+ * (p + i, 0, 0, 5), p = 2B x the snapshots before), and in proposal order a
+ * proposal j is kept iff v S_j < D(j), v from counter (p + i, 1, 0, 5) and D(j)
+ * the smaller of S_j and the distances to the centers kept since the snapshot;
+ * a snapshot keeps at most B draws (kmpar_stats.recluster_snapshots counts
+ * them).  A draw whose proposals had a target within 1e-6 of the total of a
+ * prefix boundary, or v S_j within 1e-4 S_j of D(j), adds one to recluster_near.
+ * The batched form allocates d x m floats for a transposed copy of the
+ * candidates and ~70 KB.  KMPAR_ERR_ARG for a batch outside 0..64.
+ */
+KMPAR_API kmpar_status kmpar_set_recluster(kmpar_ctx *ctx, int32_t batch);
 
 /* Device pointers to the context's D^2 (n FP32) and idx (n int32) arrays, valid
  * until the next call on the context; either out pointer may be NULL. */

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkmpar.so")
 SOURCES = ["kmpar_api.cu", "round_simt.cu", "recluster_lloyd.cu", "cost_noalloc.cu", "nearest_tc.cu",
            "nearest_tc_bf16.cu", "nearest_tc_bf16x3.cu", "nearest_tc_bf16n.cu", "nearest_tc_fp8.cu",
-           "exact_sample.cu", "batch.cu"]
+           "exact_sample.cu", "batch.cu", "recluster_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

@@ -127,7 +127,7 @@ void free_ctx(kmp::Ctx &c) {
                     c.piece, c.psum, c.rc_cmass, c.rc_sync, c.rc_err, c.chunk, c.tc_v2,
                     c.tc_anchor, c.tc_anchor_part, c.lloyd_rec, c.ex_keys, c.ex_ws, c.ex_ties,
                     c.tc_ncol, c.tc_tscale, c.tc_xscale, c.tc_ub, c.tc_cimg, c.tc_cscale, c.tc_thr,
-                    c.tc_lst, c.tc_lcnt, c.fix_rows2, c.fix_cnt2, c.rCT, c.wl_lab[0], c.wl_lab[1]};
+                    c.tc_lst, c.tc_lcnt, c.fix_rows2, c.fix_cnt2, c.rCT, c.wl_lab[0], c.wl_lab[1], c.rs_buf};
     // stream-ordered: the memory returns to the pool once the context's work is done
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, c.stream);
@@ -389,12 +389,22 @@ kmpar_status kmpar_recluster(kmpar_ctx *ctx, float *centers_dev) {
     if (!centers_dev) return fail(&c, KMPAR_ERR_ARG, "centers_dev is NULL");
     if (!c.weighted) return fail(&c, KMPAR_ERR_STATE, "recluster before weight");
     if (!c.rCT) {
-        const size_t nf = kmp::recluster_grid_floats(c);
+        // the grid form and the batched form read the candidates transposed
+        const size_t nf = c.rs_batch > 0 ? (size_t)((c.cap_total + 31) / 32) * 32 * (c.d + 2)
+                                         : kmp::recluster_grid_floats(c);
         if (nf) KMP_CUDA(&c, alloc(c, &c.rCT, nf), "alloc transposed candidates");
+    }
+    if (c.rs_batch > 0 && !c.rs_buf) {
+        unsigned char *b = nullptr;
+        KMP_CUDA(&c, alloc(c, &b, kmp::recluster_batch_bytes()), "alloc batched recluster buffer");
+        c.rs_buf = b;
     }
     KMP_CUDA(&c, cudaMemsetAsync(&c.st->warn, 0, sizeof(int32_t), c.stream), "memset warn");
     KMP_CUDA(&c, cudaMemsetAsync(c.rc_err, 0, sizeof(int), c.stream), "memset recluster error");
-    KMP_CUDA(&c, kmp::launch_recluster(c, centers_dev), "recluster kernel");
+    if (c.rs_batch > 0)
+        KMP_CUDA(&c, kmp::launch_recluster_batch(c, centers_dev), "batched recluster");
+    else
+        KMP_CUDA(&c, kmp::launch_recluster(c, centers_dev), "recluster kernel");
     int32_t warn = 0, rerr = 0;
     KMP_CUDA(&c, cudaMemcpyAsync(&warn, &c.st->warn, sizeof(warn), cudaMemcpyDeviceToHost, c.stream), "read warn");
     KMP_CUDA(&c, cudaMemcpyAsync(&rerr, c.rc_err, sizeof(rerr), cudaMemcpyDeviceToHost, c.stream), "read error");
@@ -605,6 +615,7 @@ kmpar_status kmpar_get_stats(kmpar_ctx *ctx, kmpar_stats *out) {
     out->screen_fallback = (int64_t)st.screen_fallback;
     out->screen_exact = (int64_t)st.screen_exact;
     out->screen_listed = (int64_t)st.screen_listed;
+    out->recluster_snapshots = (int64_t)st.recluster_snapshots;
     KMP_CUDA(&c, kmp::timing_drain(c), "timing");
     for (int i = 0; i < 2; ++i) {
         out->kernel_ms[i] = c.kernel_ms[i];
@@ -655,6 +666,7 @@ kmpar_status kmpar_fit(const float *X, int64_t n, int32_t d, int32_t k, double e
     kmpar_ctx *ctx = nullptr;
     kmpar_status st = kmpar_init(&ctx, Xd, n, d, k, ell, rounds, seed, precision, stream);
     if (st == KMPAR_OK && (flags & KMPAR_EXACT_SAMPLING)) st = kmpar_set_sampling(ctx, KMPAR_SAMPLE_EXACT);
+    if (st == KMPAR_OK && ((flags >> 16) & 0xFF)) st = kmpar_set_recluster(ctx, (flags >> 16) & 0xFF);
     for (int i = 1; st == KMPAR_OK && i <= rounds; ++i) st = kmpar_round(ctx, i, nullptr, nullptr);
     if (st == KMPAR_OK) st = kmpar_weight(ctx, nullptr, nullptr, nullptr);
     kmpar_status warn = KMPAR_OK;
@@ -684,6 +696,14 @@ kmpar_status kmpar_fit(const float *X, int64_t n, int32_t d, int32_t k, double e
         if (st == KMPAR_OK && e != cudaSuccess) return cuda_fail(nullptr, e, "fit copy-out");
     }
     return st != KMPAR_OK ? st : warn;
+}
+
+kmpar_status kmpar_set_recluster(kmpar_ctx *ctx, int32_t batch) {
+    if (!ctx) return fail(nullptr, KMPAR_ERR_ARG, "ctx is NULL");
+    kmp::Ctx &c = ctx->c;
+    if (batch < 0 || batch > kmp::kRsMaxBatch) return fail(&c, KMPAR_ERR_ARG, "recluster batch outside 0..64");
+    c.rs_batch = batch;
+    return KMPAR_OK;
 }
 
 kmpar_status kmpar_set_timing(kmpar_ctx *ctx, int32_t enable) {

@@ -38,6 +38,7 @@ struct DevState {
     unsigned long long screen_rows, screen_fallback;   // tensor passes: rows screened, rows the pair screening left
     unsigned long long screen_exact;                   // rows that needed the exact scan
     unsigned long long screen_listed;                  // undecided round rows refined from the pass's own lists
+    unsigned long long recluster_snapshots;            // batched reclustering: D^2 snapshots taken
 };
 
 struct Ctx {
@@ -68,6 +69,8 @@ struct Ctx {
     double *rc_cmass = nullptr;   // recluster chunk masses, 2 x ceil(cap_total / 32), then 2048 doubles of CTA slots
     float *rCT = nullptr;         // recluster grid form: candidates transposed (d x cap_total padded to 32)
     int32_t *wl_lab[2] = {nullptr, nullptr};   // weighted Lloyd: candidate labels (cap_total each)
+    int rs_batch = 0;             // reclustering: 0 = one draw at a time, B = up to B draws per D^2 snapshot
+    void *rs_buf = nullptr;       // batched reclustering: control word, proposals, their pair distances
     void *rc_sync = nullptr;      // recluster grid barrier / pick flag
     int *rc_err = nullptr;        // recluster timeout flag
     int32_t *chosen = nullptr;    // k
@@ -232,6 +235,12 @@ cudaError_t launch_round_distance(Ctx &c, int round);
 cudaError_t launch_phi_finalize(Ctx &c, int nparts, double *out, double *hist_slot);
 cudaError_t launch_weights(Ctx &c);
 cudaError_t launch_recluster(Ctx &c, float *centers);
+// batched reclustering (recluster_batch.cu): up to kRsMaxBatch draws per D^2 snapshot
+constexpr int kRsMaxBatch = 64;
+constexpr int kRsMaxProposals = 2 * kRsMaxBatch;
+size_t recluster_batch_bytes();
+cudaError_t launch_recluster_batch(Ctx &c, float *centers);
+cudaError_t launch_transpose_cand(Ctx &c);   // candidates -> c.rCT (d x cap_total padded to 32)
 size_t recluster_sync_bytes();
 size_t recluster_grid_floats(const Ctx &c);   // floats of the transposed copy the grid form needs (0: none)
 cudaError_t launch_weighted_centroids(const Ctx &c, int m, const int32_t *lab, float *centers);

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cstdlib>
 
+#include "dfloat.cuh"
 #include "kmpar_internal.cuh"
 
 namespace kmp {
@@ -85,50 +86,14 @@ __device__ __forceinline__ double warp_incl_scan_f64(double v, int lane) {
     return v;
 }
 
-// Masses and their prefix sums in the grid form, as unevaluated sums of two floats
-// (hi + lo, about 48 significant bits): the products w D^2 are exact (the weight
-// split into two floats, the product's rounding error recovered with an FMA) and
-// each addition carries its rounding error (Knuth's two-sum), so a chunk's prefix is
-// within ~2^-44 of its exact value.  FP64 arithmetic runs at a small fraction of the
-// FP32 rate on this part; these sums stay on the FP32 pipes, and the picks they give
-// can differ from exact arithmetic only inside the near-tie window that flags a draw.
-struct Df {
-    float hi, lo;
-};
-__device__ __forceinline__ Df df_add(Df a, Df b) {
-    const float s = __fadd_rn(a.hi, b.hi);
-    const float bv = __fsub_rn(s, a.hi);
-    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bv)), __fsub_rn(b.hi, bv));
-    const float t = __fadd_rn(__fadd_rn(a.lo, b.lo), err);
-    const float hi = __fadd_rn(s, t);
-    return {hi, __fsub_rn(t, __fsub_rn(hi, s))};
-}
-// the mass of a candidate: w (first draw) or w D^2, with w = wv.x + wv.y exactly
-__device__ __forceinline__ Df df_mass(float2 wv, float d2, bool first) {
-    if (first) return {wv.x, wv.y};
-    const float p = __fmul_rn(wv.x, d2);
-    const float lo = __fmaf_rn(wv.y, d2, __fmaf_rn(wv.x, d2, -p));   // (wv.x d2 - p) exactly, + wv.y d2
-    const float hi = __fadd_rn(p, lo);
-    return {hi, __fsub_rn(lo, __fsub_rn(hi, p))};
-}
-__device__ __forceinline__ Df warp_incl_scan_df(Df v, int lane) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const Df u = {__shfl_up_sync(0xffffffffu, v.hi, o), __shfl_up_sync(0xffffffffu, v.lo, o)};
-        if (lane >= o) v = df_add(u, v);
-    }
-    return v;
-}
-__device__ __forceinline__ double df_to_double(Df a) { return (double)a.hi + (double)a.lo; }
+// Masses and prefix sums of the grid form are double floats (dfloat.cuh): the picks
+// they give can differ from exact arithmetic only inside the near-tie window that
+// flags a draw.
 
 // weights as two floats whose sum is exact (w < 2^48)
 __global__ void weight_split_kernel(const long long *__restrict__ w, const DevState *st, float2 *__restrict__ wf2) {
     const int m = st->m;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
-        const long long wj = w[j];
-        const float hi = __ll2float_rn(wj);
-        wf2[j] = make_float2(hi, __ll2float_rn(wj - __float2ll_rn(hi)));
-    }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) wf2[j] = weight_split(w[j]);
 }
 
 // candidates (m x d, row-major) -> CT (d x mp, coordinate-major), 32 x 32 tiles
@@ -925,6 +890,13 @@ size_t recluster_grid_floats(const Ctx &c) {
     return (size_t)((c.cap_total + 31) / 32) * 32 * (c.d + 2);
 }
 
+cudaError_t launch_transpose_cand(Ctx &c) {
+    const int mp = (c.cap_total + 31) / 32 * 32;
+    transpose_cand_kernel<<<dim3(mp / 32, (c.d + 31) / 32), dim3(32, 8), 0, c.stream>>>(c.C, c.d, c.st, mp, c.rCT);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_recluster(Ctx &c, float *centers) {
     cudaError_t e;
     int cpc = 0, rows = 0;
@@ -936,9 +908,7 @@ cudaError_t launch_recluster(Ctx &c, float *centers) {
     if (!c.rCT) return cudaErrorInvalidValue;   // kmpar_recluster allocates the transposed copy first
     if ((e = cudaMemsetAsync(c.rc_sync, 0, sizeof(RcSync), c.stream)) != cudaSuccess) return e;
     const int mp = (c.cap_total + 31) / 32 * 32;
-    transpose_cand_kernel<<<dim3(mp / 32, (c.d + 31) / 32), dim3(32, 8), 0, c.stream>>>(c.C, c.d, c.st, mp, c.rCT);
-    count_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_transpose_cand(c)) != cudaSuccess) return e;
     // one co-resident CTA per SM
     const int nchunk_cap = (c.cap_total + 31) / 32;
     int G = std::max(1, std::min(std::min(c.num_sms, 32 * kRcLaneWords), nchunk_cap));

@@ -26,7 +26,7 @@ EXPORTED = ["kmpar_init", "kmpar_round", "kmpar_weight", "kmpar_recluster", "kmp
             "kmpar_fit", "kmpar_state", "kmpar_get_stats", "kmpar_uniforms", "kmpar_set_timing",
             "kmpar_launch_count", "kmpar_cost_noalloc", "kmpar_destroy", "kmpar_release_cached_memory",
             "kmpar_set_sampling", "kmpar_batch_run", "kmpar_batch_cand_capacity", "kmpar_weighted_lloyd",
-            "kmpar_batch_set_split",
+            "kmpar_batch_set_split", "kmpar_set_recluster",
             "kmpar_status_string", "kmpar_last_error"]
 
 
@@ -41,7 +41,8 @@ class kmpar_stats(ctypes.Structure):
                 ("capacity_overflow", ctypes.c_int32), ("recluster_warn", ctypes.c_int32),
                 ("kernel_ms", ctypes.c_double * 2), ("kernel_launches", ctypes.c_int64 * 2),
                 ("screen_rows", ctypes.c_int64), ("screen_fallback", ctypes.c_int64),
-                ("screen_exact", ctypes.c_int64), ("screen_listed", ctypes.c_int64)]
+                ("screen_exact", ctypes.c_int64), ("screen_listed", ctypes.c_int64),
+                ("recluster_snapshots", ctypes.c_int64)]
 
     def to_dict(self) -> dict:
         r = self.rounds_done
@@ -53,7 +54,7 @@ class kmpar_stats(ctypes.Structure):
                     recluster_warn=self.recluster_warn, kernel_ms=list(self.kernel_ms),
                     kernel_launches=list(self.kernel_launches), screen_rows=self.screen_rows,
                     screen_fallback=self.screen_fallback, screen_exact=self.screen_exact,
-                    screen_listed=self.screen_listed)
+                    screen_listed=self.screen_listed, recluster_snapshots=self.recluster_snapshots)
 
 
 class kmpar_problem(ctypes.Structure):
@@ -106,6 +107,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "kmpar_uniforms": (i32, [i64, u32, u32, u64, P, P]),
         "kmpar_set_timing": (i32, [P, i32]),
         "kmpar_set_sampling": (i32, [P, i32]),
+        "kmpar_set_recluster": (i32, [P, i32]),
         "kmpar_launch_count": (i64, []),
         "kmpar_cost_noalloc": (i32, [P, i64, i32, P, i32, ctypes.POINTER(f64), P]),
         "kmpar_batch_cand_capacity": (i64, [f64, i32]),
@@ -242,6 +244,10 @@ def kmpar_set_sampling(ctx: int, mode: int) -> None:
     _check(load().kmpar_set_sampling(ctx, mode), ctx)
 
 
+def kmpar_set_recluster(ctx: int, batch: int) -> None:
+    _check(load().kmpar_set_recluster(ctx, batch), ctx)
+
+
 def kmpar_launch_count() -> int:
     return load().kmpar_launch_count()
 
@@ -259,7 +265,7 @@ class KMeansPar:
     """A k-means|| context over a CUDA float32 tensor X (n x d), borrowed."""
 
     def __init__(self, X, k: int, ell: float, rounds: int, seed: int, precision: str | int = "fp32",
-                 stream=None, sampling: str | int = "bernoulli"):
+                 stream=None, sampling: str | int = "bernoulli", recluster_batch: int = 0):
         import torch
         if not (X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.is_contiguous()):
             raise ValueError("X must be a contiguous CUDA float32 n x d tensor")
@@ -271,13 +277,15 @@ class KMeansPar:
                               self.stream.cuda_stream)
         self.rounds = rounds
         mode = SAMPLINGS[sampling] if isinstance(sampling, str) else sampling
-        if mode != KMPAR_SAMPLE_BERNOULLI:
-            try:
+        try:
+            if mode != KMPAR_SAMPLE_BERNOULLI:
                 kmpar_set_sampling(self.ctx, mode)
-            except KmparError:
-                kmpar_destroy(self.ctx)
-                self.ctx = None
-                raise
+            if recluster_batch:
+                kmpar_set_recluster(self.ctx, recluster_batch)
+        except KmparError:
+            kmpar_destroy(self.ctx)
+            self.ctx = None
+            raise
 
     def round(self, i: int, sync: bool = False):
         return kmpar_round(self.ctx, i, sync)

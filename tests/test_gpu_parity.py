@@ -39,14 +39,16 @@ def _close_d2(gpu, ref):
     return np.abs(gpu - ref) <= D2_RTOL * np.abs(ref) + 1e-30
 
 
-def run_and_compare(km, orc, X, k, ell, rounds, seed, precision="fp32", max_iter=100, sampling="bernoulli"):
+def run_and_compare(km, orc, X, k, ell, rounds, seed, precision="fp32", max_iter=100, sampling="bernoulli",
+                    recluster_batch=0):
     """Runs the GPU path step by step and the oracle beside it; asserts the bar.
 
     Returns a dict of diagnostics.  If the trajectories part at a reported near
     tie, the remaining steps are checked for validity only (diag['parted'])."""
     n, d = X.shape
     Xd = _dev(X)
-    g = km.KMeansPar(Xd, k, ell, rounds, seed, precision=precision, sampling=sampling)
+    g = km.KMeansPar(Xd, k, ell, rounds, seed, precision=precision, sampling=sampling,
+                     recluster_batch=recluster_batch)
     diag = dict(parted=None, boundary_near=[])
     # exactly-l rounds: the relative window in which FP32 and exact clocks may swap
     wwin = (2 * d + 16) * 2.0 ** -24
@@ -95,7 +97,15 @@ def run_and_compare(km, orc, X, k, ell, rounds, seed, precision="fp32", max_iter
     # the seed centers are rows of X from the candidate set
     rows = gcand
     if diag["parted"] is None:
-        chosen, rnear, rwarn = orc.recluster(X[rows].astype(np.float64), gw, k, seed)
+        if recluster_batch:
+            chosen, rnear, rwarn, snaps = orc.recluster_rejection(X[rows].astype(np.float64), gw, k, seed,
+                                                                  recluster_batch)
+            gst = g.stats()
+            if not rnear.any() and gst["recluster_near"] == 0:
+                assert gst["recluster_snapshots"] == snaps
+            diag["recluster_snapshots"] = gst["recluster_snapshots"]
+        else:
+            chosen, rnear, rwarn = orc.recluster(X[rows].astype(np.float64), gw, k, seed)
         assert (st == km.KMPAR_WARN_FEW_CANDIDATES) == rwarn
         same = np.all(Ch == X[rows[chosen]], axis=1)
         if not same.all():
@@ -379,6 +389,46 @@ def test_recluster_forms_match_oracle(km, orc, form, monkeypatch):
     X = datagen.kdd_like(6000, seed=41)
     diag = run_and_compare(km, orc, X, 80, 160.0, 5, 17)
     assert diag["parted"] is None, diag
+
+
+@pytest.mark.parametrize("batch", [1, 4, 64])
+def test_recluster_batched_matches_oracle(km, orc, batch):
+    """Step 8 drawn in batches by rejection from a D^2 snapshot (the same weighted
+    k-means++ law): the chosen rows and the number of snapshots equal the oracle's."""
+    X = datagen.kdd_like(6000, seed=41)
+    diag = run_and_compare(km, orc, X, 80, 160.0, 5, 17, recluster_batch=batch)
+    assert diag["parted"] is None, diag
+    assert diag["recluster_snapshots"] >= -(-79 // batch)
+
+
+def test_recluster_batched_many_snapshots(km, orc):
+    """~20,000 candidates, k = 1,500, 64 draws per snapshot: the reclustering alone
+    (on the GPU's own candidate set) against the oracle, draw by draw up to the
+    first reported near tie."""
+    X = datagen.gauss_mixture(60000, 16, 300, 10.0, seed=5)
+    k = 1500
+    g = km.KMeansPar(_dev(X), k, 4000.0, 5, 23, recluster_batch=64)
+    for r in range(1, 6):
+        g.round(r)
+    g.weight()
+    gcand, gw = g.candidates()
+    gcand, gw = gcand.cpu().numpy(), gw.cpu().numpy()
+    C, st = g.recluster()
+    gst = g.stats()
+    g.close()
+    assert len(gcand) > 15000
+    chosen, rnear, rwarn, snaps = orc.recluster_rejection(X[gcand].astype(np.float64), gw, k, 23, 64)
+    assert not rwarn and st == km.KMPAR_OK
+    same = np.all(C.cpu().numpy() == X[gcand[chosen]], axis=1)
+    # the sequences may part only at a draw the oracle flags (a target or an
+    # acceptance test near a boundary); flagged draws mostly still agree
+    bad = np.flatnonzero(~same)
+    if bad.size:
+        assert rnear[: bad[0] + 1].any(), f"draw {bad[0]} differs without a reported near tie"
+        assert bad[0] >= 100, f"the sequences part early, at draw {bad[0]}"
+    else:
+        assert gst["recluster_snapshots"] == snaps
+    assert snaps >= -(-(k - 1) // 64)
 
 
 @pytest.mark.parametrize("k,d,precision", [(420, 128, "fp32"), (37, 15, "fp32"), (1000, 42, "bf16x3")],

@@ -517,9 +517,13 @@ kmpar_status kmpar_lloyd(kmpar_ctx *ctx, float *centers_dev, int32_t max_iter, i
                 KMP_CUDA(&c, kmp::launch_sum_f64(c.partials, c.num_partials, c.cost_dev, nullptr, c.stream),
                          "cost sum");
             } else {
-                KMP_CUDA(&c, kmp::launch_tc_pass(c, 0, centers_dev, c.k, c.labels[cur],
-                                                 tt > 0 ? c.labels[cur ^ 1] : nullptr, changed, c.dmin, 1),
-                         "tensor assign pass");
+                // after a centroid update, perm holds the rows sorted by their previous
+                // label: the exact refine walks them in that order
+                c.refine_order = tt > 0 ? c.perm : nullptr;
+                const cudaError_t pe = kmp::launch_tc_pass(c, 0, centers_dev, c.k, c.labels[cur],
+                                                           tt > 0 ? c.labels[cur ^ 1] : nullptr, changed, c.dmin, 1);
+                c.refine_order = nullptr;
+                KMP_CUDA(&c, pe, "tensor assign pass");
                 KMP_CUDA(&c, kmp::launch_sum_rows(c.dmin, c.n, c.partials, c.num_partials, c.cost_dev, nullptr,
                                                   c.stream),
                          "cost sum");

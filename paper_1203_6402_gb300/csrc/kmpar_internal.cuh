@@ -79,6 +79,7 @@ struct Ctx {
     // Lloyd
     int32_t *labels[2] = {nullptr, nullptr};
     int32_t *perm = nullptr;
+    const int32_t *refine_order = nullptr;   // Lloyd: rows sorted by their previous label (perm), or null
     int32_t *hist = nullptr;      // nsb x k
     int32_t *base = nullptr;      // k + 1
     int32_t *piece = nullptr;     // k + 1: first piece of each cluster

@@ -827,10 +827,14 @@ __global__ void __launch_bounds__(256) refine_direct_kernel(const float *__restr
                                                            const float *__restrict__ v2s, ScreenBound sb, float *D2,
                                                            int32_t *idx, int32_t *labels, const int32_t *prev,
                                                            int *changed, float *dmin, unsigned long long *fp64_cnt,
-                                                           unsigned long long *wide_cnt) {
-    const int64_t R = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                                                           unsigned long long *wide_cnt, const int32_t *order) {
+    // rows in the order given (a permutation of 0..n-1, e.g. the rows sorted by
+    // their previous label: neighbouring threads then mostly read the same center
+    // rows, which L1 serves), or in storage order
+    const int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = T < n;
+    const int64_t R = order && valid ? (int64_t)order[T] : T;
     const int lane = threadIdx.x & 31;
-    const bool valid = R < n;
     const int end = MODE == MODE_ROUND ? sb.st->batch_begin + sb.st->batch_cnt : c_cnt;
     const int j = valid ? cand1[R] : -1;
     bool fix = valid && j < 0;
@@ -1487,12 +1491,12 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
         refine_direct_kernel<MODE_ROUND, G><<<grid, 256, 0, c.stream>>>(c.X, c.n, c.d, C, 0, c.cand1, c.tc_v2, sb, \
                                                                         c.D2, c.idx, nullptr, nullptr, nullptr,  \
                                                                         nullptr, &c.st->argmin_fp64,             \
-                                                                        &c.st->argmin_wide);                     \
+                                                                        &c.st->argmin_wide, nullptr);            \
     else                                                                                                        \
         refine_direct_kernel<MODE_ASSIGN, G><<<grid, 256, 0, c.stream>>>(c.X, c.n, c.d, C, k, c.cand1, c.tc_v2,  \
                                                                          sb, nullptr, nullptr, labels, prev,     \
                                                                          changed, dmin, &c.st->argmin_fp64,      \
-                                                                         &c.st->argmin_wide);
+                                                                         &c.st->argmin_wide, c.refine_order);
         if (p.group == 4) { KMP_DIRECT(4) } else { KMP_DIRECT(2) }
 #undef KMP_DIRECT
         count_launches(1);

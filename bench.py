@@ -495,7 +495,7 @@ def run_ours(args, rank, world):
         "roofline": roofline, "clocks": clocks,
         "refine": {key: st_t[key] for key in ("sample_near", "sample_refined", "argmin_fp64", "argmin_wide",
                                              "screen_rows", "screen_fallback", "screen_exact",
-                                             "recluster_near", "recluster_snapshots")},
+                                             "recluster_near", "recluster_snapshots", "lloyd_settled")},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args)

@@ -117,6 +117,9 @@ typedef struct {
                                      exact refine over the lists the screening pass
                                      itself kept (the others took the list pass)     */
     int64_t recluster_snapshots;  /* batched reclustering: D^2 snapshots taken       */
+    int64_t lloyd_settled;        /* Lloyd assignments (rows x iterations) that the
+                                     bounds between iterations settled without the
+                                     tensor pass (tensor modes; same results)        */
 } kmpar_stats;
 
 /*

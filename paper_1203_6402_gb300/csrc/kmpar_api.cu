@@ -127,7 +127,8 @@ void free_ctx(kmp::Ctx &c) {
                     c.piece, c.psum, c.rc_cmass, c.rc_sync, c.rc_err, c.chunk, c.tc_v2,
                     c.tc_anchor, c.tc_anchor_part, c.lloyd_rec, c.ex_keys, c.ex_ws, c.ex_ties,
                     c.tc_ncol, c.tc_tscale, c.tc_xscale, c.tc_ub, c.tc_cimg, c.tc_cscale, c.tc_thr,
-                    c.tc_lst, c.tc_lcnt, c.fix_rows2, c.fix_cnt2, c.rCT, c.wl_lab[0], c.wl_lab[1], c.rs_buf};
+                    c.tc_lst, c.tc_lcnt, c.fix_rows2, c.fix_cnt2, c.rCT, c.wl_lab[0], c.wl_lab[1], c.rs_buf,
+                    c.ll_ub, c.ll_lb, c.ll_rows, c.ll_cnt, c.ll_cold, c.ll_drift, c.ll_other};
     // stream-ordered: the memory returns to the pool once the context's work is done
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, c.stream);
@@ -464,6 +465,15 @@ static kmpar_status ensure_lloyd_buffers(kmp::Ctx &c) {
     KMP_ENSURE(c.psum, (size_t)kmp::max_pieces(c.n, c.k) * c.d, "alloc piece sums");
     KMP_ENSURE(c.cost_dev, 4, "alloc cost");
     if (c.precision != KMPAR_FP32) KMP_ENSURE(c.dmin, (size_t)c.n, "alloc dmin");
+    if (c.precision != KMPAR_FP32 && c.tc_cimg) {
+        KMP_ENSURE(c.ll_ub, (size_t)c.n, "alloc Lloyd bounds");
+        KMP_ENSURE(c.ll_lb, (size_t)c.n, "alloc Lloyd bounds");
+        KMP_ENSURE(c.ll_rows, (size_t)c.n, "alloc Lloyd rows");
+        KMP_ENSURE(c.ll_cnt, 1, "alloc Lloyd row count");
+        KMP_ENSURE(c.ll_cold, (size_t)c.k * c.d, "alloc previous centers");
+        KMP_ENSURE(c.ll_drift, (size_t)c.k, "alloc center drifts");
+        KMP_ENSURE(c.ll_other, (size_t)c.k, "alloc center drifts");
+    }
 #undef KMP_ENSURE
     c.lloyd_ready = true;
     return KMPAR_OK;
@@ -497,11 +507,20 @@ kmpar_status kmpar_lloyd(kmpar_ctx *ctx, float *centers_dev, int32_t max_iter, i
     std::vector<Rec> hrec((size_t)max_iter + 1);
     int *changed = reinterpret_cast<int *>(c.cost_dev + 1);
     int cur = 0, t = 0, done = -1;
+    // after the first assignment, rows whose bounds prove their center unchanged are
+    // settled without the tensor pass (the results are the same)
+    const bool bounded = kmp::lloyd_bounds_usable(c, centers_dev);
+    auto keep_centers = [&]() -> cudaError_t {
+        return bounded ? cudaMemcpyAsync(c.ll_cold, centers_dev, sizeof(float) * (size_t)c.k * c.d,
+                                         cudaMemcpyDeviceToDevice, c.stream)
+                       : cudaSuccess;
+    };
     while (done < 0) {
         const int batch = t < 8 ? 4 : 8;
         const int t_end = std::min(max_iter, t + batch - 1);
         for (int tt = t; tt <= t_end; ++tt) {
             if (tt > t) {
+                KMP_CUDA(&c, keep_centers(), "keep centers");
                 KMP_CUDA(&c, kmp::launch_centroids(c, c.labels[cur], centers_dev), "centroid kernels");
                 cur ^= 1;
             }
@@ -515,6 +534,13 @@ kmpar_status kmpar_lloyd(kmpar_ctx *ctx, float *centers_dev, int32_t max_iter, i
                          "assign kernel");
                 KMP_CUDA(&c, kmp::timing_end(c, ev, 1), "timing");
                 KMP_CUDA(&c, kmp::launch_sum_f64(c.partials, c.num_partials, c.cost_dev, nullptr, c.stream),
+                         "cost sum");
+            } else if (bounded && tt > 0) {
+                KMP_CUDA(&c, kmp::launch_lloyd_bounded_pass(c, centers_dev, c.labels[cur], c.labels[cur ^ 1],
+                                                             changed, c.dmin),
+                         "bounded assign pass");
+                KMP_CUDA(&c, kmp::launch_sum_rows(c.dmin, c.n, c.partials, c.num_partials, c.cost_dev, nullptr,
+                                                  c.stream),
                          "cost sum");
             } else {
                 // after a centroid update, perm holds the rows sorted by their previous
@@ -545,6 +571,7 @@ kmpar_status kmpar_lloyd(kmpar_ctx *ctx, float *centers_dev, int32_t max_iter, i
         if (done < 0 && t_end == max_iter) done = max_iter;
         if (done < 0) {
             // the last iteration of the batch still needs its centroid update
+            KMP_CUDA(&c, keep_centers(), "keep centers");
             KMP_CUDA(&c, kmp::launch_centroids(c, c.labels[cur], centers_dev), "centroid kernels");
             cur ^= 1;
             t = t_end + 1;
@@ -620,6 +647,7 @@ kmpar_status kmpar_get_stats(kmpar_ctx *ctx, kmpar_stats *out) {
     out->screen_exact = (int64_t)st.screen_exact;
     out->screen_listed = (int64_t)st.screen_listed;
     out->recluster_snapshots = (int64_t)st.recluster_snapshots;
+    out->lloyd_settled = (int64_t)st.lloyd_settled;
     KMP_CUDA(&c, kmp::timing_drain(c), "timing");
     for (int i = 0; i < 2; ++i) {
         out->kernel_ms[i] = c.kernel_ms[i];

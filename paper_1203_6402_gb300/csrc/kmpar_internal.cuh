@@ -39,6 +39,7 @@ struct DevState {
     unsigned long long screen_exact;                   // rows that needed the exact scan
     unsigned long long screen_listed;                  // undecided round rows refined from the pass's own lists
     unsigned long long recluster_snapshots;            // batched reclustering: D^2 snapshots taken
+    unsigned long long lloyd_settled;                  // Lloyd rows whose assignment the bounds settled
 };
 
 struct Ctx {
@@ -80,6 +81,14 @@ struct Ctx {
     int32_t *labels[2] = {nullptr, nullptr};
     int32_t *perm = nullptr;
     const int32_t *refine_order = nullptr;   // Lloyd: rows sorted by their previous label (perm), or null
+    // Lloyd's bounds (tensor modes with the direct refine): per row an upper bound
+    // of the distance to its center and a lower bound of the distance to every other
+    // center (0: none); the centers before the last update, their drifts, the
+    // largest drift of the other centers, and the rows the bounds leave open
+    float *ll_ub = nullptr, *ll_lb = nullptr;
+    float *ll_cold = nullptr, *ll_drift = nullptr, *ll_other = nullptr;
+    int32_t *ll_rows = nullptr;
+    int *ll_cnt = nullptr;
     int32_t *hist = nullptr;      // nsb x k
     int32_t *base = nullptr;      // k + 1
     int32_t *piece = nullptr;     // k + 1: first piece of each cluster
@@ -255,7 +264,13 @@ int64_t max_pieces(int64_t n, int k);
 int64_t scan_chunks(int nsb);
 cudaError_t count_fixups(Ctx &c, const int *exact_cnt);   // adds the pass's counts to the screening stats
 cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
-                           int *changed, float *dmin, int timing_cls);
+                           int *changed, float *dmin, int timing_cls, const int32_t *rows = nullptr,
+                           const int *rows_cnt = nullptr);
+// Lloyd's bounds (round_simt.cu): whether this context can use them with centers C,
+// and one assignment after a centroid update that uses them
+bool lloyd_bounds_usable(const Ctx &c, const float *C);
+cudaError_t launch_lloyd_bounded_pass(Ctx &c, const float *C, int32_t *labels, const int32_t *prev, int *changed,
+                                      float *dmin);
 cudaError_t launch_sum_rows(const float *v, int64_t n, double *partials, int max_parts, double *out, double *copy,
                             cudaStream_t s);
 cudaError_t launch_uniforms(int64_t count, uint32_t round, uint32_t tag, uint64_t seed, double *out,

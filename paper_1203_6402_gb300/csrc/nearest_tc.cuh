@@ -44,7 +44,7 @@ struct TcParams {
     const unsigned int *cmax_bits;
     int32_t *cand1;          // EPI_PAIR: per row, first center of the best screened group (-1: none)
     float *v2;               // EPI_PAIR: per row, smallest screened value outside that group (key-truncated)
-    const int *nrows_dev;    // EPI_LIST: number of listed rows
+    const int *nrows_dev;    // EPI_LIST: number of listed rows (EPI_PAIR: of a compact image's rows, or null: n)
     const float *thr;        // EPI_LIST: per listed row (EPI_PAIRLIST: per row), the screened-value threshold
     int32_t *lst;            // EPI_LIST / EPI_PAIRLIST: per row, 4 x kListSlots pass-local center numbers
     int32_t *lcnt;           // per row and group, entries found (> kListSlots: overflow)

@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
             mbar_init(&sm.b_empty[i], 1);
         }
         sm.abort = 0;
-        sm.nrows = EPI == EPI_LIST ? *p.nrows_dev : (int)p.n;
+        sm.nrows = (EPI == EPI_LIST || p.nrows_dev) ? *p.nrows_dev : (int)p.n;
         fence_mbar_init();
     }
     if (warp == 1) tmem_alloc(&sm.tmem_base, 2 * BN);

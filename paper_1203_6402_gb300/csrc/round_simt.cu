@@ -384,8 +384,6 @@ cudaError_t launch_round(Ctx &c, int round) {
     return launch_round_distance(c, round);
 }
 
-cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
-                           int *changed, float *dmin, int timing_cls);
 cudaError_t launch_sum_rows(const float *v, int64_t n, double *partials, int max_parts, double *out, double *copy,
                             cudaStream_t s);
 
@@ -393,7 +391,8 @@ cudaError_t launch_sum_rows(const float *v, int64_t n, double *partials, int max
 cudaError_t launch_round_distance(Ctx &c, int round) {
     cudaError_t e;
     if (c.precision != KMPAR_FP32) {
-        if ((e = launch_tc_pass(c, 1, c.C, 0, nullptr, nullptr, nullptr, nullptr, 0)) != cudaSuccess) return e;
+        if ((e = launch_tc_pass(c, 1, c.C, 0, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr)) != cudaSuccess)
+            return e;
         return launch_sum_rows(c.D2, c.n, c.partials, c.num_partials, &c.st->phi, &c.st->phi_hist[round], c.stream);
     }
     cudaEvent_t ev = nullptr;
@@ -561,14 +560,15 @@ __device__ __forceinline__ int decide_top2(const float *__restrict__ X, int d, c
 
 // screening statistics of a pass: rows screened, rows the pair screening left
 // undecided, and (after the list pass) rows that needed the exact scan
-__global__ void count_fixups_kernel(const int *fix_cnt, const int *exact_cnt, int64_t n, DevState *st) {
+__global__ void count_fixups_kernel(const int *fix_cnt, const int *exact_cnt, int64_t n, const int *rows_cnt,
+                                    DevState *st) {
     st->screen_fallback += (unsigned long long)*fix_cnt;
-    st->screen_rows += (unsigned long long)n;
+    st->screen_rows += (unsigned long long)(rows_cnt ? (int64_t)*rows_cnt : n);
     st->screen_exact += (unsigned long long)(exact_cnt ? *exact_cnt : *fix_cnt);
 }
 
-cudaError_t count_fixups(Ctx &c, const int *exact_cnt) {
-    count_fixups_kernel<<<1, 1, 0, c.stream>>>(c.fix_cnt, exact_cnt, c.n, c.st);
+cudaError_t count_fixups(Ctx &c, const int *exact_cnt, const int *rows_cnt = nullptr) {
+    count_fixups_kernel<<<1, 1, 0, c.stream>>>(c.fix_cnt, exact_cnt, c.n, rows_cnt, c.st);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -665,6 +665,29 @@ __device__ __forceinline__ bool bound_certain(const ScreenBound &sb, float xnorm
 __device__ __forceinline__ bool pair_certain(const ScreenBound &sb, float xnorm, float m, float v2, int d) {
     const float v2lo = v2 >= 0.f ? v2 * (1.f - kKeyTrunc) : v2 * (1.f + kKeyTrunc);
     return bound_certain(sb, xnorm, m, v2lo, d);
+}
+
+// a lower bound of the real d^2 of every center outside the examined ones, from
+// their smallest screened value (key-truncated v2, lowered): v2lo - E + ||x'||^2
+// with E at the largest center norm (no triangle-inequality cut: this bound is
+// kept for Lloyd's next iteration, where it has to hold for every center)
+__device__ __forceinline__ float outside_lb(const ScreenBound &sb, float xnorm, float v2) {
+    const float v2lo = v2 >= 0.f ? v2 * (1.f - kKeyTrunc) : v2 * (1.f + kKeyTrunc);
+    const float xn = fmaxf(xnorm, 0.f);
+    const float X = sqrtf(xn);
+    const float cmax = __uint_as_float(*sb.cmax_bits);
+    const float E = sb.ep * X * cmax + sb.en * (xn + cmax * cmax) + sb.ec * X * cmax;
+    return v2lo - E + xn;
+}
+
+// Lloyd's bounds of a row for the next iteration, as distances: u >= the real
+// distance to its center, l <= the real distance to every other center (FP32
+// values carry at most W relative error; 1e-6 covers the rounding of these few
+// operations).  l = 0: no bound.
+__device__ __forceinline__ float bound_upper(float best, float W) { return sqrtf(best * (1.f + W)) * (1.f + 1e-6f); }
+__device__ __forceinline__ float bound_lower(float l2, float xnorm, float W) {
+    const float v = l2 * (1.f - 2.f * W) - 2.f * W * fmaxf(xnorm, 0.f);
+    return v > 0.f ? sqrtf(v) * (1.f - 1e-6f) : 0.f;
 }
 
 // the distance that decides a row whose nearest screened center has exact FP32
@@ -827,16 +850,20 @@ __global__ void __launch_bounds__(256) refine_direct_kernel(const float *__restr
                                                            const float *__restrict__ v2s, ScreenBound sb, float *D2,
                                                            int32_t *idx, int32_t *labels, const int32_t *prev,
                                                            int *changed, float *dmin, unsigned long long *fp64_cnt,
-                                                           unsigned long long *wide_cnt, const int32_t *order) {
+                                                           unsigned long long *wide_cnt, const int32_t *order,
+                                                           const int *nrows_dev, float *ubd, float *lbd) {
     // rows in the order given (a permutation of 0..n-1, e.g. the rows sorted by
     // their previous label: neighbouring threads then mostly read the same center
-    // rows, which L1 serves), or in storage order
+    // rows, which L1 serves), or in storage order.  nrows_dev: a compact pass over
+    // the rows order[0 .. *nrows_dev), whose screening results are by position.
     const int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = T < n;
+    const bool valid = T < (nrows_dev ? (int64_t)*nrows_dev : n);
     const int64_t R = order && valid ? (int64_t)order[T] : T;
+    const int64_t Ri = nrows_dev ? T : R;
     const int lane = threadIdx.x & 31;
     const int end = MODE == MODE_ROUND ? sb.st->batch_begin + sb.st->batch_cnt : c_cnt;
-    const int j = valid ? cand1[R] : -1;
+    const int j = valid ? cand1[Ri] : -1;
+    if (MODE == MODE_ASSIGN && lbd && valid) lbd[R] = 0.f;   // no bound unless the row is certified below
     bool fix = valid && j < 0;
     int chg = 0;
     if (valid && j >= 0) {
@@ -872,9 +899,18 @@ __global__ void __launch_bounds__(256) refine_direct_kernel(const float *__restr
         }
         if (i2 < 0) b2 = FLT_MAX;
         const float m = deciding<MODE>(D2, R, b1);
-        if (pair_certain(sb, sb.xnorm[R], m, v2s[R], d))
+        const float v2r = v2s[Ri];
+        if (pair_certain(sb, sb.xnorm[R], m, v2r, d)) {
             chg = decide_top2<MODE>(X, d, C, R, b1, i1, b2, i2, D2, idx, labels, prev, dmin, fp64_cnt, wide_cnt);
-        else {
+            if (MODE == MODE_ASSIGN && lbd) {
+                // the group's runner-up (exact FP32) and the bound outside the group
+                const float W = fp32_tie_window(d);
+                const bool first = labels[R] == i1;
+                const float runner = first ? b2 : b1;
+                ubd[R] = bound_upper(first ? b1 : b2, W);
+                lbd[R] = bound_lower(fminf(runner, outside_lb(sb, sb.xnorm[R], v2r)), sb.xnorm[R], W);
+            }
+        } else {
             fix = true;
             sb.ub[R] = m;
         }
@@ -1420,8 +1456,11 @@ __global__ void __launch_bounds__(256) refine_list_kernel(
     }
 }
 
+// A distance pass on the tensor cores.  rows / rows_cnt (Lloyd, direct refine
+// only): the pass covers just the rows rows[0 .. *rows_cnt), gathered into a compact
+// image; the others keep what the caller wrote for them.
 cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_t *labels, const int32_t *prev,
-                           int *changed, float *dmin, int timing_cls) {
+                           int *changed, float *dmin, int timing_cls, const int32_t *rows, const int *rows_cnt) {
     cudaError_t e;
     const int fmt = c.tc_fmt;
     if ((e = tc::launch_prep_centers(C, c.d, fmt, c.st, k, mode_round, mode_round ? c.cap_round : k, c.tc_anchor,
@@ -1429,7 +1468,8 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
         return e;
     if ((e = cudaMemsetAsync(c.fix_cnt, 0, sizeof(int), c.stream)) != cudaSuccess) return e;
     // rows the screening does not reach (e.g. an empty batch) must not see a stale winner
-    if ((e = cudaMemsetAsync(c.cand1, 0xFF, sizeof(int32_t) * (size_t)c.n, c.stream)) != cudaSuccess) return e;
+    if (!rows && (e = cudaMemsetAsync(c.cand1, 0xFF, sizeof(int32_t) * (size_t)c.n, c.stream)) != cudaSuccess)
+        return e;
     tc::TcParams p{};
     p.X = c.X; p.n = c.n; p.d = c.d; p.fmt = fmt;
     p.ximg = c.tc_ximg; p.xnorm = c.tc_xnorm; p.xscale = c.tc_xscale;
@@ -1460,6 +1500,22 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
             return e;
         p.thr = c.tc_thr; p.lst = c.tc_lst; p.lcnt = c.tc_lcnt;
     }
+    if (rows) {
+        // the compact image of the listed rows (their scales too; the thresholds the
+        // gather also writes are not used by the pair epilogue)
+        if (mode_round || !direct || p.group != 4 || !c.tc_cimg) return cudaErrorInvalidValue;
+        if ((e = tc::launch_gather_rows(c.tc_ximg, c.tc_xscale, c.d, fmt, rows, rows_cnt, c.tc_ub, c.tc_xnorm,
+                                        c.tc_cmax, sb.ep, sb.en, sb.ec, c.tc_cimg, c.tc_cscale, c.tc_thr,
+                                        c.num_sms * 8, c.stream)) != cudaSuccess)
+            return e;
+        p.ximg = c.tc_cimg; p.xscale = c.tc_cscale; p.nrows_dev = rows_cnt;
+        if ((e = tc::launch_nearest_tc(p, 0, tc::EPI_PAIR, c.num_sms, c.stream)) != cudaSuccess) return e;
+        refine_direct_kernel<MODE_ASSIGN, 4><<<(int)((c.n + 255) / 256), 256, 0, c.stream>>>(
+            c.X, c.n, c.d, C, k, c.cand1, c.tc_v2, sb, nullptr, nullptr, labels, prev, changed, dmin,
+            &c.st->argmin_fp64, &c.st->argmin_wide, rows, rows_cnt, c.ll_ub, c.ll_lb);
+        count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
     cudaEvent_t ev = nullptr;
     if ((e = timing_begin(c, &ev)) != cudaSuccess) return e;
     if ((e = tc::launch_nearest_tc(p, mode_round, plist ? tc::EPI_PAIRLIST : tc::EPI_PAIR, c.num_sms, c.stream)) !=
@@ -1491,12 +1547,14 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
         refine_direct_kernel<MODE_ROUND, G><<<grid, 256, 0, c.stream>>>(c.X, c.n, c.d, C, 0, c.cand1, c.tc_v2, sb, \
                                                                         c.D2, c.idx, nullptr, nullptr, nullptr,  \
                                                                         nullptr, &c.st->argmin_fp64,             \
-                                                                        &c.st->argmin_wide, nullptr);            \
+                                                                        &c.st->argmin_wide, nullptr, nullptr,    \
+                                                                        nullptr, nullptr);                       \
     else                                                                                                        \
         refine_direct_kernel<MODE_ASSIGN, G><<<grid, 256, 0, c.stream>>>(c.X, c.n, c.d, C, k, c.cand1, c.tc_v2,  \
                                                                          sb, nullptr, nullptr, labels, prev,     \
                                                                          changed, dmin, &c.st->argmin_fp64,      \
-                                                                         &c.st->argmin_wide, c.refine_order);
+                                                                         &c.st->argmin_wide, c.refine_order,     \
+                                                                         nullptr, c.ll_ub, c.ll_lb);
         if (p.group == 4) { KMP_DIRECT(4) } else { KMP_DIRECT(2) }
 #undef KMP_DIRECT
         count_launches(1);
@@ -1518,8 +1576,9 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
         count_launches(1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    }
     if (!c.tc_list) {
-        if ((e = count_fixups(c, nullptr)) != cudaSuccess) return e;
+        if ((e = count_fixups(c, nullptr, rows_cnt)) != cudaSuccess) return e;
         return launch_fixup(c, mode_round, C, k, labels, prev, changed, dmin, c.fix_rows, c.fix_cnt);
     }
     const int lgrid = c.num_sms * 8;
@@ -1551,7 +1610,7 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
     };
     if (!plist) {
         if ((e = list_pass(c.fix_rows, c.fix_cnt, c.fix_rows2, c.fix_cnt2)) != cudaSuccess) return e;
-        if ((e = count_fixups(c, c.fix_cnt2)) != cudaSuccess) return e;
+        if ((e = count_fixups(c, c.fix_cnt2, rows_cnt)) != cudaSuccess) return e;
         return launch_fixup(c, mode_round, C, k, labels, prev, changed, dmin, c.fix_rows2, c.fix_cnt2);
     }
     // the lists the screening pass kept: the exact FP32 form of the listed centers;
@@ -1570,6 +1629,152 @@ cudaError_t launch_tc_pass(Ctx &c, int mode_round, const float *C, int k, int32_
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_fixup(c, mode_round, C, k, labels, prev, changed, dmin, c.fix_rows, c.fix_cnt);
+}
+
+// ---------------------------------------------------------------- Lloyd's bounds
+// Between Lloyd iterations every center c moves by delta_c = ||c_new - c_old||.
+// A row labelled a with u >= d(x, c_a) and l <= d(x, c) for every other c keeps
+// u + delta_a and l - max_{c != a} delta_c as bounds for the moved centers (the
+// triangle inequality); if the first is below the second, a is still strictly the
+// nearest center, by more than the FP32 tie window (both bounds carry it), so the
+// exact FP32 argmin takes a again and only d^2(x, c_a) needs computing.
+
+// delta_c in FP64 from the FP32 centers, rounded up to FP32 (one warp per center)
+__global__ void lloyd_drift_kernel(const float *__restrict__ Cn, const float *__restrict__ Co, int k, int d,
+                                   float *__restrict__ drift) {
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= k) return;
+    double s = 0.0;
+    for (int q = lane; q < d; q += 32) {
+        const double t = (double)Cn[(size_t)c * d + q] - (double)Co[(size_t)c * d + q];
+        s = __fma_rn(t, t, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) drift[c] = __double2float_ru(sqrt(s));
+}
+
+// for every center, the largest drift among the other centers (one block)
+__global__ void __launch_bounds__(1024) lloyd_drift_other_kernel(const float *__restrict__ drift, int k,
+                                                                 float *__restrict__ other) {
+    __shared__ float s1[32], s2[32];
+    __shared__ int si[32];
+    float m1 = 0.f, m2 = 0.f;
+    int i1 = -1;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        const float v = drift[c];
+        if (v > m1) { m2 = m1; m1 = v; i1 = c; }
+        else if (v > m2) m2 = v;
+    }
+    // merge the top two of the warp, then of the block
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float a1 = __shfl_xor_sync(0xffffffffu, m1, o), a2 = __shfl_xor_sync(0xffffffffu, m2, o);
+        const int ai = __shfl_xor_sync(0xffffffffu, i1, o);
+        if (a1 > m1 || (a1 == m1 && ai < i1)) { m2 = fmaxf(m1, a2); m1 = a1; i1 = ai; }
+        else m2 = fmaxf(m2, a1);
+    }
+    if (lane == 0) { s1[wid] = m1; s2[wid] = m2; si[wid] = i1; }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        m1 = lane < nw ? s1[lane] : 0.f;
+        m2 = lane < nw ? s2[lane] : 0.f;
+        i1 = lane < nw ? si[lane] : -1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float a1 = __shfl_xor_sync(0xffffffffu, m1, o), a2 = __shfl_xor_sync(0xffffffffu, m2, o);
+            const int ai = __shfl_xor_sync(0xffffffffu, i1, o);
+            if (a1 > m1 || (a1 == m1 && ai < i1)) { m2 = fmaxf(m1, a2); m1 = a1; i1 = ai; }
+            else m2 = fmaxf(m2, a1);
+        }
+        if (lane == 0) { s1[0] = m1; s2[0] = m2; si[0] = i1; }
+    }
+    __syncthreads();
+    m1 = s1[0]; m2 = s2[0]; i1 = si[0];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) other[c] = c == i1 ? m2 : m1;
+}
+
+// The bounds test for every row (in the order given: rows sorted by their previous
+// label, so neighbouring threads read the same center row).  A row it settles gets
+// its label, the exact FP32 d^2 to the moved center (bit-identical to the refine's
+// chains) and fresh bounds; the others are listed for the compact pass (with l = 0
+// until that pass certifies them again).
+__global__ void __launch_bounds__(256) lloyd_bounds_kernel(const float *__restrict__ X, int64_t n, int d,
+                                                           const float *__restrict__ C,
+                                                           const int32_t *__restrict__ prev,
+                                                           const int32_t *__restrict__ order, int32_t *labels,
+                                                           float *dmin, float *ubd, float *lbd,
+                                                           const float *__restrict__ drift,
+                                                           const float *__restrict__ other, int32_t *rows, int *cnt,
+                                                           unsigned long long *settled) {
+    const int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = T < n;
+    const int64_t R = order && valid ? (int64_t)order[T] : T;
+    const int lane = threadIdx.x & 31;
+    bool keep = false;
+    if (valid) {
+        const int a = prev[R];
+        const float u = ubd[R] + drift[a];
+        const float l = lbd[R] - other[a];
+        keep = l > 0.f && u < l;
+        if (keep) {
+            const float4 *x4 = reinterpret_cast<const float4 *>(X + R * d);
+            const float4 *c4 = reinterpret_cast<const float4 *>(C + (int64_t)a * d);
+            float v = 0.f;
+#pragma unroll 4
+            for (int p = 0; p < (d >> 2); ++p) {
+                const float4 x = __ldg(x4 + p), c = __ldg(c4 + p);
+                float t;
+                t = __fsub_rn(x.x, c.x); v = __fmaf_rn(t, t, v);
+                t = __fsub_rn(x.y, c.y); v = __fmaf_rn(t, t, v);
+                t = __fsub_rn(x.z, c.z); v = __fmaf_rn(t, t, v);
+                t = __fsub_rn(x.w, c.w); v = __fmaf_rn(t, t, v);
+            }
+            labels[R] = a;
+            dmin[R] = v;
+            ubd[R] = bound_upper(v, fp32_tie_window(d));
+            lbd[R] = l;
+        } else {
+            lbd[R] = 0.f;
+        }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, valid && !keep);
+    if (m) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(cnt, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (valid && !keep) rows[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)R;
+    }
+    const unsigned kp = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0 && kp) atomicAdd(settled, (unsigned long long)__popc(kp));
+}
+
+bool lloyd_bounds_usable(const Ctx &c, const float *C) {
+    if (c.precision == KMPAR_FP32 || !c.ll_lb || !c.tc_cimg) return false;
+    const ResidentPlan rp = resident_plan(c.k, c.d);
+    return rp.parts == 0 && (c.d & 3) == 0 && tc::tc_norms_in_epilogue(c.tc_fmt) &&
+           ((reinterpret_cast<uintptr_t>(c.X) | reinterpret_cast<uintptr_t>(C)) & 15u) == 0;
+}
+
+// one Lloyd assignment after a centroid update, using the bounds: the rows they
+// settle, then a compact tensor pass over the rest
+cudaError_t launch_lloyd_bounded_pass(Ctx &c, const float *C, int32_t *labels, const int32_t *prev, int *changed,
+                                      float *dmin) {
+    cudaError_t e;
+    const int k = c.k;
+    lloyd_drift_kernel<<<(k + 7) / 8, 256, 0, c.stream>>>(C, c.ll_cold, k, c.d, c.ll_drift);
+    lloyd_drift_other_kernel<<<1, 1024, 0, c.stream>>>(c.ll_drift, k, c.ll_other);
+    count_launches(2);
+    if ((e = cudaMemsetAsync(c.ll_cnt, 0, sizeof(int), c.stream)) != cudaSuccess) return e;
+    lloyd_bounds_kernel<<<(int)((c.n + 255) / 256), 256, 0, c.stream>>>(
+        c.X, c.n, c.d, C, prev, c.perm, labels, dmin, c.ll_ub, c.ll_lb, c.ll_drift, c.ll_other, c.ll_rows, c.ll_cnt,
+        &c.st->lloyd_settled);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_tc_pass(c, 0, C, k, labels, prev, changed, dmin, -1, c.ll_rows, c.ll_cnt);
 }
 
 }  // namespace kmp

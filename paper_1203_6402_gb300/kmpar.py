@@ -42,7 +42,7 @@ class kmpar_stats(ctypes.Structure):
                 ("kernel_ms", ctypes.c_double * 2), ("kernel_launches", ctypes.c_int64 * 2),
                 ("screen_rows", ctypes.c_int64), ("screen_fallback", ctypes.c_int64),
                 ("screen_exact", ctypes.c_int64), ("screen_listed", ctypes.c_int64),
-                ("recluster_snapshots", ctypes.c_int64)]
+                ("recluster_snapshots", ctypes.c_int64), ("lloyd_settled", ctypes.c_int64)]
 
     def to_dict(self) -> dict:
         r = self.rounds_done
@@ -54,7 +54,8 @@ class kmpar_stats(ctypes.Structure):
                     recluster_warn=self.recluster_warn, kernel_ms=list(self.kernel_ms),
                     kernel_launches=list(self.kernel_launches), screen_rows=self.screen_rows,
                     screen_fallback=self.screen_fallback, screen_exact=self.screen_exact,
-                    screen_listed=self.screen_listed, recluster_snapshots=self.recluster_snapshots)
+                    screen_listed=self.screen_listed, recluster_snapshots=self.recluster_snapshots,
+                    lloyd_settled=self.lloyd_settled)
 
 
 class kmpar_problem(ctypes.Structure):

@@ -193,8 +193,10 @@ def test_large_k_wide_rows(km):
     # plain BF16 (error ~2^-6 of ||x'|| ||c'||) leaves many rows of the rounds to the
     # exact fix-up: their candidates are data points, about two per true cluster,
     # so the two nearest are often near ties; every row is decided exactly all the same
-    # screened rows: 5 round passes and 4 Lloyd assignments (updates 0..3)
-    assert stats["screen_rows"] == (5 + 4) * n and 0 < stats["screen_fallback"] < stats["screen_rows"]
+    # rows: 5 round passes and 4 Lloyd assignments (updates 0..3), each row of an
+    # assignment after the first either screened or settled by Lloyd's bounds
+    assert stats["screen_rows"] + stats["lloyd_settled"] == (5 + 4) * n
+    assert stats["lloyd_settled"] > 0 and 0 < stats["screen_fallback"] < stats["screen_rows"]
 
 
 def test_full_size_exact_rounds(km):

@@ -454,6 +454,34 @@ def test_lloyd_from_fixed_centers_matches_oracle(km, orc, k, d, precision):
     g.close()
 
 
+def test_lloyd_bounds_settle_rows_and_match_oracle(km, orc):
+    """Lloyd in BF16 at d = 128 (norms in the screening epilogue, direct refine):
+    after the first assignment, rows whose bounds (upper bound to their center plus
+    its drift below the lower bound to every other center minus their largest drift)
+    prove the center unchanged skip the tensor pass.  The trajectory equals the
+    oracle's, and the labels and centers equal the FP32 path's bit for bit."""
+    X = datagen.gauss_mixture(30000, 128, 60, 100.0, seed=91)
+    k = 60
+    C0 = np.ascontiguousarray(X[::499][:k])
+    res = {}
+    for prec in ("bf16", "fp32"):
+        g = km.KMeansPar(_dev(X), k, 2.0 * k, 1, 5, precision=prec)
+        C = _dev(C0)
+        out = g.lloyd(C, 15, labels=True, hist=True)
+        res[prec] = (C.cpu().numpy(), out["labels"].cpu().numpy(), out["iters"], out["final_cost"], g.stats())
+        g.close()
+    Cb, lb, itb, fcb, stb = res["bf16"]
+    Cf, lf, itf, fcf, stf = res["fp32"]
+    assert stb["lloyd_settled"] > 0 and stf["lloyd_settled"] == 0
+    assert itb == itf and np.array_equal(lb, lf) and np.array_equal(Cb, Cf) and fcb == fcf
+    oC, olab, oit, ofc, ohist, onear = orc.lloyd(X, C0.astype(np.float64), 15)
+    if itb == oit and np.array_equal(lb, olab):
+        assert math.isclose(fcb, ofc, rel_tol=1e-4)
+        np.testing.assert_allclose(Cb, oC, rtol=1e-5, atol=1e-5 * (np.abs(oC).max() + 1))
+    else:
+        assert onear.any() or stb["argmin_fp64"] > 0
+
+
 # ------------------------------------------------------------------ edge cases
 def test_single_point(km, orc):
     X = np.array([[1.5, -2.0, 3.0]], np.float32)

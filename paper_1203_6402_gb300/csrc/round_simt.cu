@@ -1769,8 +1769,10 @@ cudaError_t launch_lloyd_bounded_pass(Ctx &c, const float *C, int32_t *labels, c
     lloyd_drift_other_kernel<<<1, 1024, 0, c.stream>>>(c.ll_drift, k, c.ll_other);
     count_launches(2);
     if ((e = cudaMemsetAsync(c.ll_cnt, 0, sizeof(int), c.stream)) != cudaSuccess) return e;
+    // rows in storage order: X streams from HBM, the settled rows' center rows (k x d,
+    // a few MB) come from L2
     lloyd_bounds_kernel<<<(int)((c.n + 255) / 256), 256, 0, c.stream>>>(
-        c.X, c.n, c.d, C, prev, c.perm, labels, dmin, c.ll_ub, c.ll_lb, c.ll_drift, c.ll_other, c.ll_rows, c.ll_cnt,
+        c.X, c.n, c.d, C, prev, nullptr, labels, dmin, c.ll_ub, c.ll_lb, c.ll_drift, c.ll_other, c.ll_rows, c.ll_cnt,
         &c.st->lloyd_settled);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -401,6 +401,34 @@ def test_recluster_batched_matches_oracle(km, orc, batch):
     assert diag["recluster_snapshots"] >= -(-79 // batch)
 
 
+def test_set_recluster_validates_and_both_forms_run_on_one_context(km, orc):
+    """kmpar_set_recluster: batches outside 0..64 are refused (KMPAR_ERR_ARG); one
+    context reclusters in both forms, each equal to its oracle function."""
+    X = datagen.gauss_mixture(3000, 8, 12, 10.0, seed=3)
+    k, seed = 12, 19
+    g = km.KMeansPar(_dev(X), k, 24.0, 3, seed)
+    for b in (-1, 65):
+        with pytest.raises(km.KmparError) as ei:
+            km.kmpar_set_recluster(g.ctx, b)
+        assert ei.value.status == km.KMPAR_ERR_ARG
+    for r in range(1, 4):
+        g.round(r)
+    g.weight()
+    cand, w = g.candidates()
+    cand, w = cand.cpu().numpy(), w.cpu().numpy()
+    rows = X[cand].astype(np.float64)
+    for b in (0, 5, 0):
+        km.kmpar_set_recluster(g.ctx, b)
+        C, _ = g.recluster()
+        if b:
+            ch, near, _, _ = orc.recluster_rejection(rows, w, k, seed, b)
+        else:
+            ch, near, _ = orc.recluster(rows, w, k, seed)
+        if not near.any():
+            assert np.array_equal(C.cpu().numpy(), X[cand[ch]]), b
+    g.close()
+
+
 def test_recluster_batched_many_snapshots(km, orc):
     """~20,000 candidates, k = 1,500, 64 draws per snapshot: the reclustering alone
     (on the GPU's own candidate set) against the oracle, draw by draw up to the

@@ -420,6 +420,11 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
             // EPI_LIST: the row's threshold (pad rows list nothing)
             float thr = -INF;
             if (EPI != EPI_PAIR && R < n) thr = p.thr[R];
+            // EPI_PAIRLIST: the same threshold for the groups' minimum keys (a key
+            // differs from its value by less than 2^-17 relative: widened by 2^-16, a
+            // group that holds a value <= thr always passes; its values are then tested
+            // exactly); -inf once the list has overflowed
+            float thrk = thr == -INF ? -INF : thr + fabsf(thr) * 1.52587890625e-5f;
             int lcount = 0;
             float K1 = INF, K2 = INF;
             int T1 = 0;
@@ -494,7 +499,10 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
                                     const uint32_t gc = (uint32_t)(((c + cc) * 32 + q) >> 2);
                                     const float m0 = fminf(min3f(v[0], v[1], v[2]), v[3]);
                                     const float m1 = fminf(min3f(v[4], v[5], v[6]), v[7]);
-                                    if (PLIST && lcount <= kListSlots && fminf(m0, m1) <= thr) {
+                                    const float a = __uint_as_float((__float_as_uint(m0) & vmask) | gc);
+                                    const float b = __uint_as_float((__float_as_uint(m1) & vmask) | (gc + 1));
+                                    const float lo = fminf(a, b), hi = fmaxf(a, b);
+                                    if (PLIST && lo <= thrk) {
                                         // (rarely) list the centers at or below the row's threshold;
                                         // an overflowed list stops here (its row takes the list pass)
                                         const int col0 = t * BN + grp * C::GW + (c + cc) * 32 + q;
@@ -505,10 +513,8 @@ __global__ void __launch_bounds__(kThreads, 1) nearest_tc_kernel(TcParams p, int
                                                 ++lcount;
                                             }
                                         }
+                                        if (lcount > kListSlots) thrk = -INF;
                                     }
-                                    const float a = __uint_as_float((__float_as_uint(m0) & vmask) | gc);
-                                    const float b = __uint_as_float((__float_as_uint(m1) & vmask) | (gc + 1));
-                                    const float lo = fminf(a, b), hi = fmaxf(a, b);
                                     if ((q >> 3) & 1) {
                                         k2b = min3f(fmaxf(k1b, lo), k2b, hi);
                                         k1b = fminf(k1b, lo);

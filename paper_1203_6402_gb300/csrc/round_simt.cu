@@ -1102,16 +1102,17 @@ int refine_warps(int d) {
 size_t refine_smem_bytes(int d) { return sizeof(float) * refine_warps(d) * 96 * (size_t)refine_stride(d); }
 
 // Rows the screening could not settle, scanned exactly against every center of the
-// pass.  A CTA takes tiles of 8 listed rows, one warp per row; the centers stream
+// pass.  A CTA takes tiles of 32 listed rows, four per warp; the centers stream
 // through shared memory in chunks of 64 (asynchronous copies, double-buffered) and
-// lane l sums centers l and l + 32 of each chunk in the exact FP32 difference form
-// in ascending coordinates (bit-identical to dist2_fp32): per coordinate pair one
-// broadcast and two conflict-free 8-byte shared loads (row stride 2 mod 4) feed
-// eight FP32 operations.  Small tiles keep every SM busy when only a few thousand
-// rows need the scan.  A lexicographic top-2 per row is merged across the warp,
-// then the same decision as nearest_kernel (decide_top2).  Persistent: the row
-// count is read on the device.
-constexpr int kFxRows = 8;
+// lane l sums centers l and l + 32 of each chunk for the warp's four rows in the
+// exact FP32 difference form in ascending coordinates (bit-identical to
+// dist2_fp32): per coordinate pair four broadcast and two conflict-free 8-byte
+// shared loads (row stride 2 mod 4) feed 32 FP32 operations, and every center chunk
+// serves 32 rows.  A lexicographic top-2 per row is merged across the warp, then the
+// same decision as nearest_kernel (decide_top2).  Persistent: the row count is read
+// on the device.
+constexpr int kFxWarpRows = 4;
+constexpr int kFxRows = 8 * kFxWarpRows;
 constexpr int kFxCent = 64;
 
 template <int MODE>
@@ -1123,7 +1124,7 @@ __global__ void __launch_bounds__(256) fixup_kernel(const float *__restrict__ X,
                                                    unsigned long long *wide_cnt) {
     extern __shared__ __align__(16) float fsm[];
     const int ds = refine_stride(d);
-    float *xs = fsm;                   // kFxRows x ds point rows
+    float *xs = fsm;                   // kFxRows x ds point rows (row wid + 8 r of the tile: xs + (wid + 8 r) ds)
     float *cs = fsm + kFxRows * ds;    // 2 x kFxCent x ds center rows
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nrows = *rows_cnt;
@@ -1145,15 +1146,20 @@ __global__ void __launch_bounds__(256) fixup_kernel(const float *__restrict__ X,
     for (int t0 = blockIdx.x * kFxRows; t0 < nrows; t0 += gridDim.x * kFxRows) {   // uniform per block
         const int nr = min(kFxRows, nrows - t0);
         __syncthreads();   // the previous tile's readers are done with xs and cs
-        if (wid < nr) {
-            const float *src = X + (int64_t)rows[t0 + wid] * d;
-            for (int q = lane; q < d; q += 32) xs[wid * ds + q] = __ldg(src + q);
+#pragma unroll
+        for (int r = 0; r < kFxWarpRows; ++r) {
+            const int tr = wid + 8 * r;
+            if (tr < nr) {
+                const float *src = X + (int64_t)rows[t0 + tr] * d;
+                for (int q = lane; q < d; q += 32) xs[tr * ds + q] = __ldg(src + q);
+            }
         }
         if (nchunk > 0) issue(0);
         cp_async_commit();
-        float b1 = FMAX, b2 = FMAX;
-        int i1 = INT_MAX, i2 = INT_MAX;
-        const float *xa = xs + wid * ds;
+        float b1[kFxWarpRows], b2[kFxWarpRows];
+        int i1[kFxWarpRows], i2[kFxWarpRows];
+#pragma unroll
+        for (int r = 0; r < kFxWarpRows; ++r) { b1[r] = FMAX; b2[r] = FMAX; i1[r] = INT_MAX; i2[r] = INT_MAX; }
         for (int ch = 0; ch < nchunk; ++ch) {
             if (ch + 1 < nchunk) issue(ch + 1);
             cp_async_commit();
@@ -1161,53 +1167,76 @@ __global__ void __launch_bounds__(256) fixup_kernel(const float *__restrict__ X,
             __syncthreads();   // chunk ch and the point rows are visible
             const float *cb = cs + (ch & 1) * kFxCent * ds;
             const float *c0 = cb + lane * ds, *c1 = cb + (lane + 32) * ds;
-            float a0 = 0.f, a1 = 0.f;
-            const float2 *x2 = reinterpret_cast<const float2 *>(xa);
+            float a0[kFxWarpRows], a1[kFxWarpRows];
+#pragma unroll
+            for (int r = 0; r < kFxWarpRows; ++r) { a0[r] = 0.f; a1[r] = 0.f; }
             const float2 *p0 = reinterpret_cast<const float2 *>(c0);
             const float2 *p1 = reinterpret_cast<const float2 *>(c1);
-#pragma unroll 4
+#pragma unroll 2
             for (int p = 0; p < (d >> 1); ++p) {
-                const float2 x = x2[p], u = p0[p], v = p1[p];
-                float t = __fsub_rn(x.x, u.x);
-                a0 = __fmaf_rn(t, t, a0);
-                t = __fsub_rn(x.y, u.y);
-                a0 = __fmaf_rn(t, t, a0);
-                t = __fsub_rn(x.x, v.x);
-                a1 = __fmaf_rn(t, t, a1);
-                t = __fsub_rn(x.y, v.y);
-                a1 = __fmaf_rn(t, t, a1);
+                const float2 u = p0[p], v = p1[p];
+#pragma unroll
+                for (int r = 0; r < kFxWarpRows; ++r) {
+                    const float2 x = reinterpret_cast<const float2 *>(xs + (wid + 8 * r) * ds)[p];
+                    float t = __fsub_rn(x.x, u.x);
+                    a0[r] = __fmaf_rn(t, t, a0[r]);
+                    t = __fsub_rn(x.y, u.y);
+                    a0[r] = __fmaf_rn(t, t, a0[r]);
+                    t = __fsub_rn(x.x, v.x);
+                    a1[r] = __fmaf_rn(t, t, a1[r]);
+                    t = __fsub_rn(x.y, v.y);
+                    a1[r] = __fmaf_rn(t, t, a1[r]);
+                }
             }
             if (d & 1) {
-                const float xe = xa[d - 1];
-                float t = __fsub_rn(xe, c0[d - 1]);
-                a0 = __fmaf_rn(t, t, a0);
-                t = __fsub_rn(xe, c1[d - 1]);
-                a1 = __fmaf_rn(t, t, a1);
+#pragma unroll
+                for (int r = 0; r < kFxWarpRows; ++r) {
+                    const float xe = xs[(wid + 8 * r) * ds + d - 1];
+                    float t = __fsub_rn(xe, c0[d - 1]);
+                    a0[r] = __fmaf_rn(t, t, a0[r]);
+                    t = __fsub_rn(xe, c1[d - 1]);
+                    a1[r] = __fmaf_rn(t, t, a1[r]);
+                }
             }
             const int jl0 = ch * kFxCent + lane, jl1 = jl0 + 32;
-            if (jl0 < cnt && lex_lt(a0, begin + jl0, b2, i2)) {
-                if (lex_lt(a0, begin + jl0, b1, i1)) { b2 = b1; i2 = i1; b1 = a0; i1 = begin + jl0; }
-                else { b2 = a0; i2 = begin + jl0; }
-            }
-            if (jl1 < cnt && lex_lt(a1, begin + jl1, b2, i2)) {
-                if (lex_lt(a1, begin + jl1, b1, i1)) { b2 = b1; i2 = i1; b1 = a1; i1 = begin + jl1; }
-                else { b2 = a1; i2 = begin + jl1; }
+#pragma unroll
+            for (int r = 0; r < kFxWarpRows; ++r) {
+                if (jl0 < cnt && lex_lt(a0[r], begin + jl0, b2[r], i2[r])) {
+                    if (lex_lt(a0[r], begin + jl0, b1[r], i1[r])) {
+                        b2[r] = b1[r]; i2[r] = i1[r]; b1[r] = a0[r]; i1[r] = begin + jl0;
+                    } else {
+                        b2[r] = a0[r]; i2[r] = begin + jl0;
+                    }
+                }
+                if (jl1 < cnt && lex_lt(a1[r], begin + jl1, b2[r], i2[r])) {
+                    if (lex_lt(a1[r], begin + jl1, b1[r], i1[r])) {
+                        b2[r] = b1[r]; i2[r] = i1[r]; b1[r] = a1[r]; i1[r] = begin + jl1;
+                    } else {
+                        b2[r] = a1[r]; i2[r] = begin + jl1;
+                    }
+                }
             }
             __syncthreads();   // every reader is done with this buffer before it is refilled
         }
         cp_async_wait<0>();
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float c1 = __shfl_xor_sync(0xffffffffu, b1, o), c2 = __shfl_xor_sync(0xffffffffu, b2, o);
-            const int j1 = __shfl_xor_sync(0xffffffffu, i1, o), j2 = __shfl_xor_sync(0xffffffffu, i2, o);
-            top2_merge(b1, i1, b2, i2, c1, j1, c2, j2);
-        }
-        if (lane == 0 && wid < nr) {
-            const int64_t R = rows[t0 + wid];
-            if (i2 == INT_MAX) { i2 = -1; b2 = FMAX; }
-            if (decide_top2<MODE>(X, d, C, R, b1, i1, b2, i2, D2, idx, labels, prev, dmin, fp64_cnt, wide_cnt) &&
-                changed)
-                atomicAdd(changed, 1);
+        for (int r = 0; r < kFxWarpRows; ++r) {
+            float v1 = b1[r], v2 = b2[r];
+            int j1 = i1[r], j2 = i2[r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float c1v = __shfl_xor_sync(0xffffffffu, v1, o), c2v = __shfl_xor_sync(0xffffffffu, v2, o);
+                const int k1 = __shfl_xor_sync(0xffffffffu, j1, o), k2 = __shfl_xor_sync(0xffffffffu, j2, o);
+                top2_merge(v1, j1, v2, j2, c1v, k1, c2v, k2);
+            }
+            const int tr = wid + 8 * r;
+            if (lane == 0 && tr < nr) {
+                const int64_t R = rows[t0 + tr];
+                if (j2 == INT_MAX) { j2 = -1; v2 = FMAX; }
+                if (decide_top2<MODE>(X, d, C, R, v1, j1, v2, j2, D2, idx, labels, prev, dmin, fp64_cnt, wide_cnt) &&
+                    changed)
+                    atomicAdd(changed, 1);
+            }
         }
     }
 }

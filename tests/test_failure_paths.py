@@ -1,5 +1,5 @@
-"""Error paths of the C ABI, made to happen on the host (SURVEY: failure
-detection): a round that draws more than its capacity (KMPAR_ERR_CAPACITY), a
+"""Error paths of the C ABI, made to happen on the host (failure detection
+without a GPU fault): a round that draws more than its capacity (KMPAR_ERR_CAPACITY), a
 context whose allocations pass a memory limit (KMPAR_ERR_OOM), and a grid
 barrier of the cooperative reclustering kernel whose wait budget runs out
 (KMPAR_ERR_TIMEOUT).  No GPU fault is involved: the capacity check, the memory

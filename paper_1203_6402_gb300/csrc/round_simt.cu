@@ -1429,45 +1429,56 @@ __global__ void __launch_bounds__(256) refine_list_kernel(
     const float *__restrict__ thr, ScreenBound sb, int32_t *rows2, int *cnt2, float *D2, int32_t *idx,
     int32_t *labels, const int32_t *prev, int *changed, float *dmin, unsigned long long *fp64_cnt,
     unsigned long long *wide_cnt) {
+    // four listed rows per warp, eight lanes per row (a row's lists usually hold a
+    // few centers): lane sl of a row's group takes its list entries sl, sl + 8, ...
     constexpr int S = tc::kListSlots;
     const int lane = threadIdx.x & 31;
+    const int sub = lane >> 3, sl = lane & 7;
+    const unsigned gmask = 0xFFu << (8 * sub);   // the lanes of this row's group
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int nrows = *rows_cnt;
     const int begin = MODE == MODE_ROUND ? sb.st->batch_begin : 0;
     const int cnt = MODE == MODE_ROUND ? sb.st->batch_cnt : c_cnt;
     const float FMAX = FLT_MAX;
-    for (int64_t i = gw; i < nrows; i += W) {   // uniform per warp
-        const int64_t R = rows[i];
+    for (int64_t i0 = gw * 4; i0 < nrows; i0 += W * 4) {   // uniform per warp
+        const int64_t i = i0 + sub;
+        const bool valid = i < nrows;
+        const int64_t R = valid ? rows[i] : 0;
         const int64_t li = BYROW ? R : i;   // the row's lists and threshold: by row, or by list position
-        const int cg = lane < 4 ? lcnt[li * 4 + lane] : 0;
-        const bool over = __any_sync(0xffffffffu, cg > S);
-        const int c0 = __shfl_sync(0xffffffffu, cg, 0), c1 = __shfl_sync(0xffffffffu, cg, 1);
-        const int c2 = __shfl_sync(0xffffffffu, cg, 2), c3 = __shfl_sync(0xffffffffu, cg, 3);
+        const int cg = valid && sl < 4 ? lcnt[li * 4 + sl] : 0;
+        const bool over = (__ballot_sync(0xffffffffu, cg > S) & gmask) != 0;
+        const int c0 = __shfl_sync(0xffffffffu, cg, 8 * sub), c1 = __shfl_sync(0xffffffffu, cg, 8 * sub + 1);
+        const int c2 = __shfl_sync(0xffffffffu, cg, 8 * sub + 2), c3 = __shfl_sync(0xffffffffu, cg, 8 * sub + 3);
         float b1 = FMAX, b2 = FMAX;
         int i1 = INT_MAX, i2 = INT_MAX;
-        if (!over) {
-            int g = -1, sidx = lane;
-            if (sidx < c0) g = 0;
-            else if ((sidx -= c0) < c1) g = 1;
-            else if ((sidx -= c1) < c2) g = 2;
-            else if ((sidx -= c2) < c3) g = 3;
-            if (g >= 0) {
+        if (valid && !over) {
+            const int total = c0 + c1 + c2 + c3;
+            for (int e = sl; e < total; e += 8) {
+                int g, sidx = e;
+                if (sidx < c0) g = 0;
+                else if ((sidx -= c0) < c1) g = 1;
+                else if ((sidx -= c1) < c2) g = 2;
+                else { sidx -= c2; g = 3; }
                 const int col = lst[(li * 4 + g) * S + sidx];
                 if (col >= 0 && col < cnt) {
                     const int j = begin + col;
-                    b1 = dist2_fp32_v4(X + R * d, C + (int64_t)j * d, d);
-                    i1 = j;
+                    const float v = dist2_fp32_v4(X + R * d, C + (int64_t)j * d, d);
+                    if (lex_lt(v, j, b2, i2)) {
+                        if (lex_lt(v, j, b1, i1)) { b2 = b1; i2 = i1; b1 = v; i1 = j; }
+                        else { b2 = v; i2 = j; }
+                    }
                 }
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float u1 = __shfl_xor_sync(0xffffffffu, b1, o), u2 = __shfl_xor_sync(0xffffffffu, b2, o);
-                const int j1 = __shfl_xor_sync(0xffffffffu, i1, o), j2 = __shfl_xor_sync(0xffffffffu, i2, o);
-                top2_merge(b1, i1, b2, i2, u1, j1, u2, j2);
-            }
         }
-        if (lane == 0) {
+        // top-2 of the row's group (xor offsets below 8 stay within the group)
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            const float u1 = __shfl_xor_sync(0xffffffffu, b1, o), u2 = __shfl_xor_sync(0xffffffffu, b2, o);
+            const int j1 = __shfl_xor_sync(0xffffffffu, i1, o), j2 = __shfl_xor_sync(0xffffffffu, i2, o);
+            top2_merge(b1, i1, b2, i2, u1, j1, u2, j2);
+        }
+        if (sl == 0 && valid) {
             bool certain = false;
             if (!over) {
                 const float m = deciding<MODE>(D2, R, i1 != INT_MAX ? b1 : FMAX);

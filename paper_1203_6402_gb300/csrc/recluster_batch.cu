@@ -12,14 +12,15 @@
 // keeps up to B draws, so k draws take about k / B snapshots instead of k
 // dependent steps.
 //
-// Per snapshot, four launches on the context's stream and no wait between CTAs:
+// Per snapshot, five launches on the context's stream and no wait between CTAs:
 //   rs_update_kernel   D^2 of every candidate against the centers kept in the last
 //                      snapshot (a sum stops once it reaches D^2: sums of
 //                      non-negative terms never decrease), masses w D^2 as double
-//                      floats, chunk (32) and block (256 candidates) totals;
+//                      floats, the total of each chunk of 32 candidates;
+//   rs_scan_kernel     one block: the chunk totals' inclusive prefix sums (ascending);
 //   rs_propose_kernel  one warp per proposal i: u from counter (p + i, 0, 0, 5),
-//                      target u * total, then the block, the chunk and the candidate
-//                      by prefix sums in ascending order;
+//                      target u * total, then the chunk from the prefix sums and the
+//                      candidate from the chunk's masses;
 //   rs_pair_kernel     squared distances between the proposals (each pair once);
 //   rs_accept_kernel   one warp walks the proposals in order, v from counter
 //                      (p + i, 1, 0, 5), and appends the kept ones to the chosen list.

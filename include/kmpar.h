@@ -170,7 +170,8 @@ KMPAR_API kmpar_status kmpar_weight(kmpar_ctx *ctx, int64_t *m_out, const int32_
  * thread-block cluster's shared memory run in a cluster kernel, larger ones in a
  * cooperative grid kernel; setting the environment variable KMPAR_RECLUSTER_GRID
  * to 1 selects the grid kernel for every size (same draws up to reported near
- * ties).
+ * ties).  After kmpar_set_recluster(ctx, B) with B > 0, the same law is drawn in
+ * batches of up to B draws per D^2 snapshot instead (see kmpar_set_recluster).
  */
 KMPAR_API kmpar_status kmpar_recluster(kmpar_ctx *ctx, float *centers_dev);
 
@@ -197,8 +198,12 @@ KMPAR_API kmpar_status kmpar_weighted_lloyd(kmpar_ctx *ctx, float *centers_dev, 
  * At most max_iter center updates.  labels_dev (device, n int32, nullable)
  * receives the final assignment; *iters (host, nullable) the number of updates;
  * *final_cost (host, nullable) the cost of the final centers; cost_hist (host,
- * nullable, max_iter+1 doubles) the cost of each assignment.  Synchronises once
- * per iteration.
+ * nullable, max_iter+1 doubles) the cost of each assignment.  In the tensor modes
+ * whose screening adds the center norms in the epilogue (BF16, FP8) with d a
+ * multiple of 4, the assignments after the first skip the rows whose distance
+ * bounds prove their center unchanged (counted in kmpar_stats.lloyd_settled);
+ * every label, distance and center is the one the full assignment gives.
+ * Synchronises once per batch of iterations (4, then 8).
  */
 KMPAR_API kmpar_status kmpar_lloyd(kmpar_ctx *ctx, float *centers_dev, int32_t max_iter,
                          int32_t *labels_dev, int32_t *iters, double *final_cost,

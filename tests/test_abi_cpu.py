@@ -54,6 +54,9 @@ def test_argument_errors_need_no_gpu(lib):
     assert kmpar._lib.kmpar_status_string(kmpar.KMPAR_ERR_CAPACITY) == b"round drew more points than its capacity"
     with pytest.raises(kmpar.KmparError):
         kmpar.kmpar_init(1, 10, 0, 2, 4.0, 2, 0, kmpar.KMPAR_FP32)
+    # setters refuse a missing context before touching the device
+    assert kmpar._lib.kmpar_set_recluster(None, 8) == kmpar.KMPAR_ERR_ARG
+    assert kmpar._lib.kmpar_set_sampling(None, kmpar.KMPAR_SAMPLE_EXACT) == kmpar.KMPAR_ERR_ARG
     # no context has allocated, so there is no pool to trim
     assert kmpar._lib.kmpar_release_cached_memory() == kmpar.KMPAR_OK
 

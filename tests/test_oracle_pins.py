@@ -354,6 +354,25 @@ def test_recluster_rejection_joint_law(orc, batch):
     assert snaps >= trials * -(-2 // batch)
 
 
+def test_recluster_rejection_same_law_for_longer_sequences(orc):
+    # both forms sample weighted k-means++: beyond the first three draws (pinned exactly
+    # above), the cost of the k = 6 chosen centers has the same distribution whether
+    # the draws come one at a time or in batches of 2 (rejections and snapshot
+    # refreshes both occur); two-sample Kolmogorov-Smirnov over 3,000 seeds each
+    rng = np.random.default_rng(11)
+    cand = np.concatenate([rng.normal(c, 1.0, size=(6, 2)) for c in ([0, 0], [8, 0], [0, 8], [8, 8], [4, 4])])
+    w = rng.integers(1, 6, size=len(cand)).astype(np.int64)
+    k = 6
+
+    def cost(ch):
+        d2 = cdist(cand, cand[ch], "sqeuclidean").min(1)
+        return float((w * d2).sum())
+
+    seq = [cost(orc.recluster(cand, w, k, seed=s)[0]) for s in range(3000)]
+    bat = [cost(orc.recluster_rejection(cand, w, k, seed=s, batch=2)[0]) for s in range(3000)]
+    assert stats.ks_2samp(seq, bat).pvalue > 1e-4
+
+
 def test_recluster_rejection_first_draw_is_the_sequential_one(orc):
     # draw 0 uses the same counter and rule as the one-at-a-time form
     rng = np.random.default_rng(8)
